@@ -1,0 +1,188 @@
+"""CPU oracle for checkerboard Metropolis and population annealing.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package. It shares no code with the CUDA library (``paper_1709_04394_gb300``)
+and never imports it.
+
+The arithmetic lives in ``gbmc_oracle.c`` (plain C, one site at a time, in the
+order of the paper's algorithms; see that file's header for the passages it
+follows and the readings it takes). This module compiles it with the host C
+compiler on first use and marshals numpy arrays through ctypes. The schedule
+helpers of Sec. 5.4 that the paper leaves open (histogram overlap, bisection)
+live in ``schedule.py``; the MLP reference lives in ``mlp.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gbmc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PURPOSE_METRO, PURPOSE_INIT, PURPOSE_RESAMPLE, PURPOSE_COUPLING = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile gbmc_oracle.c into _build/liboracle.so (host C compiler, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        p = C.c_void_p
+        u32, u64, i32, i64, dbl = C.c_uint32, C.c_uint64, C.c_int, C.c_int64, C.c_double
+        lib.orc_philox_batch.argtypes = [i64, p, p, p]
+        lib.orc_thresholds.argtypes = [dbl, i32, p]
+        lib.orc_init_spins.argtypes = [i32, i32, u64, u32, u32, i32, p]
+        lib.orc_couplings.argtypes = [i32, u64, u32, p]
+        lib.orc_halfsweep.argtypes = [i32, i32, p, p, p, u64, u32, u32, u32, i32]
+        lib.orc_sweeps.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, u32, u32]
+        lib.orc_observables.argtypes = [i32, i32, p, p, p, p]
+        lib.orc_resample.argtypes = [u32, p, dbl, u64, u32, u32, p]
+        lib.orc_resample.restype = dbl
+        lib.orc_children_order.argtypes = [u32, p, p]
+        lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
+                                   p, p, p, p, p, p, p, p, p]
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of counters ``ctr`` (shape [n,4] uint32) under ``key`` (2 uint32)."""
+    lib = _load()
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty_like(ctr)
+    lib.orc_philox_batch(ctr.shape[0], _ptr(ctr), _ptr(key), _ptr(out))
+    return out
+
+
+def thresholds(beta: float, ndE: int) -> np.ndarray:
+    """int64 T(4), T(8), ... : accept a positive dE iff the 32-bit word u <= T(dE)."""
+    lib = _load()
+    out = np.empty(ndE, dtype=np.int64)
+    lib.orc_thresholds(float(beta), ndE, _ptr(out))
+    return out
+
+
+def n_sites(dim: int, L: int) -> int:
+    return L ** dim
+
+
+def init_spins(dim: int, L: int, seed: int, instance: int, replica: int, random_start: bool) -> np.ndarray:
+    lib = _load()
+    s = np.empty(n_sites(dim, L), dtype=np.int8)
+    lib.orc_init_spins(dim, L, seed, instance, replica, int(bool(random_start)), _ptr(s))
+    return s
+
+
+def couplings(L: int, seed: int, instance: int) -> np.ndarray:
+    """Bimodal couplings of a dim-3 lattice, int8 [N, 3] (forward x, y, z bonds)."""
+    lib = _load()
+    J = np.empty(n_sites(3, L) * 3, dtype=np.int8)
+    lib.orc_couplings(L, seed, instance, _ptr(J))
+    return J.reshape(-1, 3)
+
+
+def _check_spins(s, dim, L):
+    assert s.dtype == np.int8 and s.flags.c_contiguous and s.size == n_sites(dim, L)
+
+
+def halfsweep(dim, L, s, J, thr, seed, instance, replica, t, colour):
+    lib = _load()
+    _check_spins(s, dim, L)
+    thr = np.ascontiguousarray(thr, dtype=np.int64)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    lib.orc_halfsweep(dim, L, _ptr(s), _ptr(Jc), _ptr(thr), seed, instance, replica, t, colour)
+
+
+def sweeps(dim, L, s, J, beta, seed, instance, replica, t0, n):
+    """n checkerboard sweeps of spins ``s`` (int8, in place) at ``beta``."""
+    lib = _load()
+    _check_spins(s, dim, L)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    lib.orc_sweeps(dim, L, _ptr(s), _ptr(Jc), float(beta), seed, instance, replica, t0, n)
+
+
+def observables(dim, L, s, J=None):
+    lib = _load()
+    _check_spins(s, dim, L)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    E = np.zeros(1, dtype=np.int64)
+    M = np.zeros(1, dtype=np.int64)
+    lib.orc_observables(dim, L, _ptr(s), _ptr(Jc), _ptr(E), _ptr(M))
+    return int(E[0]), int(M[0])
+
+
+def resample(E, dbeta, seed, instance, step):
+    """Multinomial resampling counts and ln Q of one annealing step."""
+    lib = _load()
+    E = np.ascontiguousarray(E, dtype=np.int64)
+    counts = np.empty(E.size, dtype=np.uint32)
+    lnQ = lib.orc_resample(E.size, _ptr(E), float(dbeta), seed, instance, step, _ptr(counts))
+    return counts, lnQ
+
+
+def children_order(counts):
+    lib = _load()
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    parent = np.empty(counts.size, dtype=np.uint32)
+    lib.orc_children_order(counts.size, _ptr(counts), _ptr(parent))
+    return parent
+
+
+def linear_betas(beta_f: float, S: int) -> np.ndarray:
+    """beta_i = (beta_f * i) / S, i = 0..S, evaluated in that order in fp64."""
+    return np.array([(float(beta_f) * float(i)) / float(S) for i in range(S + 1)], dtype=np.float64)
+
+
+def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None):
+    """Population annealing for one instance (Sec. 5.4). Returns a dict of per-step
+    arrays (index 0 = beta_0 = 0) and the final population."""
+    lib = _load()
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    S = betas.size - 1
+    N = n_sites(dim, L)
+    init = spins is None
+    if init:
+        spins = np.empty(R * N, dtype=np.int8)
+    else:
+        spins = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1).copy()
+        assert spins.size == R * N
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    out = {k: np.zeros(S + 1, dtype=np.float64) for k in ("lnQ", "lnZ", "sumE2", "sumM2")}
+    sumE = np.zeros(S + 1, dtype=np.int64)
+    sumAbsM = np.zeros(S + 1, dtype=np.int64)
+    hashes = np.zeros(S + 1, dtype=np.uint64)
+    E = np.zeros(R, dtype=np.int64)
+    M = np.zeros(R, dtype=np.int64)
+    lib.orc_pa_run(dim, L, _ptr(Jc), seed, instance, R, S, _ptr(betas), theta, _ptr(spins),
+                   int(init), _ptr(out["lnQ"]), _ptr(out["lnZ"]), _ptr(sumE), _ptr(out["sumE2"]),
+                   _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M))
+    out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M,
+               spins=spins.reshape(R, N), betas=betas)
+    return out

@@ -1,0 +1,419 @@
+/*
+ * gbmc_oracle.c -- plain, slow CPU oracle for checkerboard Metropolis sweeps of
+ * Ising-type lattices and population annealing (Weigel, "Monte Carlo methods for
+ * massively parallel computers", arXiv:1709.04394).
+ *
+ * TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline leg may load or call this code. It shares no code, header,
+ * table or constant with the CUDA library and includes nothing from it.
+ *
+ * Every routine follows the paper's steps in the paper's order, one site (or
+ * one replica) at a time, with no blocking, fusion or reordering:
+ *   - Ising Hamiltonian, Eq. (7), with h_i = 0 and periodic boundaries (Sec. 3).
+ *   - Single-spin-flip Metropolis rule, the four-step list of Sec. 3.1 and
+ *     Eq. (8): flip if dE <= 0 or r < exp(-beta dE), r uniform in [0,1).
+ *   - Checkerboard order: the even sub-lattice, then the odd one (Sec. 3.1,
+ *     Fig. 5; the offset 0 / offset 1 kernel calls described there).
+ *   - Philox4x32-10 counter-based generator: the mulhi/mullo round of Sec. 4
+ *     with the constants of Salmon et al. (2011), ten rounds.
+ *   - Population annealing, the five-step algorithm of Sec. 5.4 with the
+ *     normaliser Q_i of Eq. (13).
+ *   - Bimodal +-J couplings of the Edwards-Anderson spin glass (Sec. 6).
+ *
+ * Readings where the paper is silent (all of them are conventions shared with
+ * the CUDA path only through their written definition):
+ *   R1 key = (seed lo, seed hi); Metropolis counter = (q, t, r, c3) with
+ *      k = rank of the site among colour-c sites in row-major order, q = k>>2,
+ *      word k&3; t = global sweep counter; r = replica slot;
+ *      c3 = purpose<<28 | colour<<27 | instance.
+ *      Purposes: METRO 0, INIT 1 (q = site>>2, word site&3, t = 0),
+ *      RESAMPLE 2 (draw k: q = k>>1, t = step, r = 0, 64-bit word k&1),
+ *      COUPLING 3 (bond b = 3 site + mu: q = b>>2, word b&3, t = r = 0).
+ *   R2 r = u 2^-32 with u the 32-bit word, so "r < p" is "u <= ceil(p 2^32) - 1".
+ *   R3 dE = 0 is accepted (the rule says dE <= 0).
+ *   R4 colour(x,y[,z]) = (x+y[+z]) mod 2; colour 0 first.
+ *   R5 PA step order: resample to beta_i, theta sweeps at beta_i, measure.
+ *   R6 constant population R, multinomial resampling with integer weights
+ *      W(E) = floor(2^s exp(-dbeta (E - Emin))), s = 63 - ceil(log2 R); the
+ *      cumulative sums C_j are taken in replica order; draw k picks the least
+ *      j with C_j > floor(U64_k C_R / 2^64); children of parent j are placed
+ *      contiguously, parents in increasing order.
+ *   R7 ln Q_i = -dbeta Emin + ln sum_E h(E) exp(-dbeta (E - Emin)) - ln R,
+ *      summed over energy levels in increasing E.
+ *   R9 J_{i,mu} = +1 if the top bit of its COUPLING word is 0, else -1.
+ *  R10 ln Z(beta_0 = 0) = N ln 2; ln Z_i = ln Z_{i-1} + ln Q_i.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PURPOSE_METRO 0u
+#define ORC_PURPOSE_INIT 1u
+#define ORC_PURPOSE_RESAMPLE 2u
+#define ORC_PURPOSE_COUPLING 3u
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Sec. 4, counter-based generators).                         */
+/* One round: the two 64-bit products R*M give L' = mullo and                 */
+/* R' = mulhi xor key xor L for the two word pairs, with the pair            */
+/* permutation of the 4x32 variant; the key is advanced by the Weyl           */
+/* increments between rounds.                                                 */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t orc_word(uint64_t seed, uint32_t q, uint32_t t, uint32_t r, uint32_t c3,
+                         unsigned lane)
+{
+    uint32_t ctr[4] = {q, t, r, c3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[lane & 3u];
+}
+
+static uint32_t orc_c3(uint32_t purpose, uint32_t colour, uint32_t instance)
+{
+    return (purpose << 28) | (colour << 27) | instance;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattice geometry: N = L^dim sites, x fastest, periodic boundaries.        */
+/* ------------------------------------------------------------------------ */
+static int64_t orc_nsites(int dim, int L)
+{
+    int64_t n = 1;
+    for (int d = 0; d < dim; ++d) n *= L;
+    return n;
+}
+
+static void orc_coords(int dim, int L, int64_t site, int *x, int *y, int *z)
+{
+    *x = (int)(site % L);
+    *y = (int)((site / L) % L);
+    *z = dim == 3 ? (int)(site / ((int64_t)L * L)) : 0;
+}
+
+static int64_t orc_site(int dim, int L, int x, int y, int z)
+{
+    x = ((x % L) + L) % L;
+    y = ((y % L) + L) % L;
+    z = ((z % L) + L) % L;
+    return dim == 3 ? ((int64_t)z * L + y) * L + x : (int64_t)y * L + x;
+}
+
+/* Neighbour n (0..2*dim-1) of a site: even n = forward along axis n/2, odd n =
+ * backward. The coupling of that bond, J_{i,mu} of the forward bond leaving
+ * site i along mu (stored as J[3*i+mu] for dim 3; all +1 when J == NULL). */
+static int64_t orc_neighbour(int dim, int L, int64_t site, int n, const int8_t *J, int *Jn)
+{
+    int x, y, z;
+    orc_coords(dim, L, site, &x, &y, &z);
+    int axis = n / 2, fwd = (n % 2) == 0;
+    int dx = axis == 0 ? 1 : 0, dy = axis == 1 ? 1 : 0, dz = axis == 2 ? 1 : 0;
+    int64_t nb;
+    if (fwd) {
+        nb = orc_site(dim, L, x + dx, y + dy, z + dz);
+        *Jn = J ? J[3 * site + axis] : 1;
+    } else {
+        nb = orc_site(dim, L, x - dx, y - dy, z - dz);
+        *Jn = J ? J[3 * nb + axis] : 1;
+    }
+    return nb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thresholds (reading R2): T(dE) = ceil(exp(-beta dE) 2^32) - 1, so that a   */
+/* 32-bit word u satisfies u 2^-32 < exp(-beta dE)  <=>  u <= T(dE).          */
+/* out[m] = T(4(m+1)) for m = 0 .. ndE-1.                                     */
+/* ------------------------------------------------------------------------ */
+void orc_thresholds(double beta, int ndE, int64_t *out)
+{
+    for (int m = 0; m < ndE; ++m) {
+        double dE = 4.0 * (double)(m + 1);
+        double p = exp(-(beta * dE));
+        double scaled = ldexp(p, 32);
+        out[m] = (int64_t)ceil(scaled) - 1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 1 of the Sec. 3.1 list: initial configuration (all up, or uniformly   */
+/* random from the INIT purpose: s = +1 if the word's top bit is 0).          */
+/* ------------------------------------------------------------------------ */
+void orc_init_spins(int dim, int L, uint64_t seed, uint32_t instance, uint32_t replica,
+                    int random_start, int8_t *s)
+{
+    int64_t N = orc_nsites(dim, L);
+    for (int64_t i = 0; i < N; ++i) {
+        if (!random_start) {
+            s[i] = 1;
+        } else {
+            uint32_t u = orc_word(seed, (uint32_t)(i >> 2), 0u, replica,
+                                  orc_c3(ORC_PURPOSE_INIT, 0u, instance), (unsigned)(i & 3));
+            s[i] = (u >> 31) ? -1 : 1;
+        }
+    }
+}
+
+/* Bimodal couplings P(J = +1) = P(J = -1) = 1/2 (Sec. 6), three forward bonds
+ * per site of a dim-3 lattice, J[3*site + mu]. */
+void orc_couplings(int L, uint64_t seed, uint32_t instance, int8_t *J)
+{
+    int64_t N = orc_nsites(3, L);
+    for (int64_t i = 0; i < N; ++i) {
+        for (int mu = 0; mu < 3; ++mu) {
+            int64_t b = 3 * i + mu;
+            uint32_t u = orc_word(seed, (uint32_t)(b >> 2), 0u, 0u,
+                                  orc_c3(ORC_PURPOSE_COUPLING, 0u, instance), (unsigned)(b & 3));
+            J[b] = (u >> 31) ? -1 : 1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Steps 2-3 of the Sec. 3.1 list for every site of one sub-lattice.          */
+/* ------------------------------------------------------------------------ */
+void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
+                   uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour)
+{
+    int64_t N = orc_nsites(dim, L);
+    uint32_t c3 = orc_c3(ORC_PURPOSE_METRO, (uint32_t)colour, instance);
+    for (int64_t i = 0; i < N; ++i) {
+        int x, y, z;
+        orc_coords(dim, L, i, &x, &y, &z);
+        if (((x + y + z) & 1) != colour) continue;
+        /* rank among the sites of this colour, row-major */
+        int64_t row = dim == 3 ? (int64_t)z * L + y : (int64_t)y;
+        int64_t k = row * (L / 2) + (x >> 1);
+        /* dE_k = 2 s_k sum_nn J s_j */
+        int h = 0;
+        for (int n = 0; n < 2 * dim; ++n) {
+            int Jn;
+            int64_t nb = orc_neighbour(dim, L, i, n, J, &Jn);
+            h += Jn * s[nb];
+        }
+        int dE = 2 * s[i] * h;
+        int accept;
+        if (dE <= 0) {
+            accept = 1;
+        } else {
+            uint32_t u = orc_word(seed, (uint32_t)(k >> 2), t, replica, c3, (unsigned)(k & 3));
+            accept = (int64_t)u <= thr[dE / 4 - 1];
+        }
+        if (accept) s[i] = (int8_t)(-s[i]);
+    }
+}
+
+/* n full sweeps (even sub-lattice, then odd), sweep counters t0 .. t0+n-1. */
+void orc_sweeps(int dim, int L, int8_t *s, const int8_t *J, double beta, uint64_t seed,
+                uint32_t instance, uint32_t replica, uint32_t t0, uint32_t n)
+{
+    int64_t thr[3];
+    orc_thresholds(beta, dim, thr);
+    for (uint32_t m = 0; m < n; ++m) {
+        orc_halfsweep(dim, L, s, J, thr, seed, instance, replica, t0 + m, 0);
+        orc_halfsweep(dim, L, s, J, thr, seed, instance, replica, t0 + m, 1);
+    }
+}
+
+/* Eq. (7): E = -sum_<ij> J_ij s_i s_j over the forward bonds; M = sum_i s_i. */
+void orc_observables(int dim, int L, const int8_t *s, const int8_t *J, int64_t *E, int64_t *M)
+{
+    int64_t N = orc_nsites(dim, L);
+    int64_t e = 0, m = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        for (int axis = 0; axis < dim; ++axis) {
+            int Jn;
+            int64_t nb = orc_neighbour(dim, L, i, 2 * axis, J, &Jn);
+            e -= (int64_t)Jn * s[i] * s[nb];
+        }
+        m += s[i];
+    }
+    *E = e;
+    *M = m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 5.4, step 2: resampling from beta_{i-1} to beta_i = beta_{i-1}+dbeta. */
+/* E[R]: the replicas' energies. Writes counts[R] (number of copies of each   */
+/* replica) and returns ln Q_i (Eq. (13), reading R7). Readings R6, R1.      */
+/* ------------------------------------------------------------------------ */
+static int orc_cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int orc_ceil_log2(uint64_t R)
+{
+    int b = 0;
+    while (((uint64_t)1 << b) < R) ++b;
+    return b;
+}
+
+double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
+                    uint32_t instance, uint32_t step, uint32_t *counts)
+{
+    /* minimum energy of the population */
+    int64_t Emin = E[0];
+    for (uint32_t j = 1; j < R; ++j)
+        if (E[j] < Emin) Emin = E[j];
+
+    /* ln Q_i over energy levels in increasing order: copy, sort, run-length */
+    int64_t *sorted = (int64_t *)malloc(sizeof(int64_t) * R);
+    memcpy(sorted, E, sizeof(int64_t) * R);
+    qsort(sorted, R, sizeof(int64_t), orc_cmp_i64);
+    double sum = 0.0;
+    uint32_t a = 0;
+    while (a < R) {
+        uint32_t b = a;
+        while (b < R && sorted[b] == sorted[a]) ++b;
+        double h = (double)(b - a);
+        sum += h * exp(-(dbeta * (double)(sorted[a] - Emin)));
+        a = b;
+    }
+    free(sorted);
+    double lnQ = -dbeta * (double)Emin + log(sum) - log((double)R);
+
+    /* integer weights and their cumulative sums in replica order */
+    int s = 63 - orc_ceil_log2(R);
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * R);
+    uint64_t acc = 0;
+    for (uint32_t j = 0; j < R; ++j) {
+        double w = exp(-(dbeta * (double)(E[j] - Emin)));
+        uint64_t W = (uint64_t)floor(ldexp(w, s));
+        acc += W;
+        C[j] = acc;
+        counts[j] = 0;
+    }
+    uint64_t total = acc;
+
+    /* R multinomial draws */
+    for (uint32_t k = 0; k < R; ++k) {
+        uint32_t ctr[4] = {k >> 1, step, 0u, orc_c3(ORC_PURPOSE_RESAMPLE, 0u, instance)};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        unsigned l = k & 1u;
+        uint64_t U = ((uint64_t)out[2 * l + 1] << 32) | (uint64_t)out[2 * l];
+        uint64_t x = (uint64_t)(((unsigned __int128)U * (unsigned __int128)total) >> 64);
+        /* least j with C_j > x, by bisection over the increasing C */
+        uint32_t lo = 0, hi = R - 1;
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > x) hi = mid;
+            else lo = mid + 1;
+        }
+        counts[lo] += 1;
+    }
+    free(C);
+    return lnQ;
+}
+
+/* Children of parent j occupy consecutive slots, parents in increasing order. */
+void orc_children_order(uint32_t R, const uint32_t *counts, uint32_t *parent_of_slot)
+{
+    uint32_t m = 0;
+    for (uint32_t j = 0; j < R; ++j)
+        for (uint32_t c = 0; c < counts[j]; ++c) parent_of_slot[m++] = j;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Population annealing, the Sec. 5.4 algorithm, for one instance.            */
+/*   betas[0..S]: beta_0 = 0 (step 1: random start is exact equilibrium),     */
+/*   then for i = 1..S: resample to beta_i, theta sweeps at beta_i with sweep  */
+/*   counters (i-1) theta ... i theta - 1, measure population averages.       */
+/* spins[R*N] in/out: if init != 0 the population is initialised here.       */
+/* Per step outputs (arrays of S+1, index 0 = beta_0): lnQ, lnZ, sum E,      */
+/* sum E^2 (as double of exact int64 sums), sum |M|, sum M^2, and a running   */
+/* FNV-1a hash of the counts for cross-checking.                              */
+/* ------------------------------------------------------------------------ */
+void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R,
+                uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
+                double *lnQ_out, double *lnZ_out, int64_t *sumE_out, double *sumE2_out,
+                int64_t *sumAbsM_out, double *sumM2_out, uint64_t *counts_hash_out,
+                int64_t *E_final, int64_t *M_final)
+{
+    int64_t N = orc_nsites(dim, L);
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * R);
+    int64_t *M = (int64_t *)malloc(sizeof(int64_t) * R);
+    uint32_t *counts = (uint32_t *)malloc(sizeof(uint32_t) * R);
+    uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * R);
+    int8_t *next = (int8_t *)malloc((size_t)R * (size_t)N);
+
+    if (init)
+        for (uint32_t r = 0; r < R; ++r)
+            orc_init_spins(dim, L, seed, instance, r, 1, spins + (size_t)r * N);
+
+    double lnZ = (double)N * log(2.0);
+    uint64_t hash = 1469598103934665603ull;
+    for (uint32_t i = 0; i <= S; ++i) {
+        double lnQ = 0.0;
+        if (i > 0) {
+            double dbeta = betas[i] - betas[i - 1];
+            lnQ = orc_resample(R, E, dbeta, seed, instance, i, counts);
+            for (uint32_t j = 0; j < R; ++j) {
+                hash ^= counts[j];
+                hash *= 1099511628211ull;
+            }
+            orc_children_order(R, counts, parent);
+            for (uint32_t m = 0; m < R; ++m)
+                memcpy(next + (size_t)m * N, spins + (size_t)parent[m] * N, (size_t)N);
+            memcpy(spins, next, (size_t)R * (size_t)N);
+            for (uint32_t r = 0; r < R; ++r)
+                orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                           (i - 1) * theta, theta);
+            lnZ += lnQ;
+        }
+        int64_t sE = 0, sAM = 0;
+        double sE2 = 0.0, sM2 = 0.0;
+        for (uint32_t r = 0; r < R; ++r) {
+            orc_observables(dim, L, spins + (size_t)r * N, J, &E[r], &M[r]);
+            sE += E[r];
+            sE2 += (double)E[r] * (double)E[r];
+            sAM += M[r] < 0 ? -M[r] : M[r];
+            sM2 += (double)M[r] * (double)M[r];
+        }
+        if (lnQ_out) lnQ_out[i] = lnQ;
+        if (lnZ_out) lnZ_out[i] = lnZ;
+        if (sumE_out) sumE_out[i] = sE;
+        if (sumE2_out) sumE2_out[i] = sE2;
+        if (sumAbsM_out) sumAbsM_out[i] = sAM;
+        if (sumM2_out) sumM2_out[i] = sM2;
+        if (counts_hash_out) counts_hash_out[i] = hash;
+    }
+    if (E_final) memcpy(E_final, E, sizeof(int64_t) * R);
+    if (M_final) memcpy(M_final, M, sizeof(int64_t) * R);
+    free(E);
+    free(M);
+    free(counts);
+    free(parent);
+    free(next);
+}
+
+/* Batch form of the generator for tests: n counters, one key. */
+void orc_philox_batch(int64_t n, const uint32_t *ctr, const uint32_t key[2], uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
