@@ -1,0 +1,369 @@
+"""Benchmark: population annealing of 2D Ising lattices on one GB300 (and N ranks).
+
+Default workload: population annealing of the 2D Ising ferromagnet, L = 64,
+R = 10^5 replicas, beta linear 0 -> 1 over 101 temperatures (100 resampling
+steps), theta = 10 checkerboard Metropolis sweeps per temperature, multinomial
+resampling with fp64 weights. One benchmark step = one complete annealing run
+(Sec. 5.4 steps 1-5: random start, 100 x [resample, 10 sweeps, measure]) with a
+fresh Philox seed. The population (2 x 409.6 MB int8 buffers) is larger than
+L2, so no explicit flush is needed between steps.
+
+Other workloads (--workload): ising2d-L4096 (one L = 4096 lattice, 1000 sweeps
+per step, the single-lattice throughput case).
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+N_SMS = 152
+SM_MAX_MHZ = 2070.0
+# Philox4x32-10 per call: 10 rounds x (2 wide products = 4 32-bit multiply
+# halves + 2 three-way xors = 4 xor ops) = 80 integer ops for 4 sites.
+ALG_INT_OPS_PER_SITE_UPDATE = 20.0
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.err = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception as e:  # nvidia-smi missing
+            self.err = str(e)
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err or "no nvidia-smi"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, ws):
+    if ws > 1:
+        dist.barrier()
+
+
+def max_over_ranks(dist, ws, value, device=None):
+    if ws == 1:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+WORKLOADS = {
+    "pa-ising2d-L64": dict(kind="pa", dim=2, L=64, R=100000, S=100, theta=10, beta_f=1.0),
+    "ising2d-L4096": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868),
+}
+
+
+def site_updates_per_step(w):
+    if w["kind"] == "pa":
+        return w["R"] * w["L"] ** w["dim"] * w["theta"] * w["S"]
+    return w["L"] ** w["dim"] * w["sweeps"]
+
+
+def run_gpu(args, w, ws, rank, local):
+    import torch
+
+    from paper_1709_04394_gb300 import build as gbuild
+    from paper_1709_04394_gb300 import gbmc
+
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, "nccl")
+    gbuild.build()
+    stream = torch.cuda.current_stream()
+    ctx = gbmc.gbmc_create(local, stream.cuda_stream)
+    N = w["L"] ** w["dim"]
+    seed0 = 1000003 * (rank + 1)
+    result = {}
+    if w["kind"] == "pa":
+        R = w["R"]
+        spins = torch.empty(R * N, dtype=torch.int8, device="cuda")
+        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=R, seed=seed0, instance_base=rank, spins=spins)
+        pa = gbmc.pa_create(ctx, [lat], w["theta"], w["S"], beta_f=w["beta_f"], init=True)
+
+        def step(k):
+            gbmc.pa_reset(ctx, pa, True, seed0 + k)
+            gbmc.pa_run(ctx, pa)
+    else:
+        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0)
+
+        def step(k):
+            gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = gbmc.gbmc_kernel_launches()
+    gbmc.gbmc_profile(ctx, True)
+    barrier(dist, ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, ws)
+    ms_local = e0.elapsed_time(e1)
+    prof = gbmc.gbmc_profile_read(ctx)
+    gbmc.gbmc_profile(ctx, False)
+    launches = gbmc.gbmc_kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = max_over_ranks(dist, ws, ms_local, device="cuda")
+    result.update(ms=ms, prof=prof, launches=launches, clocks=clocks)
+
+    # end-to-end through the C ABI with host buffers: host population in,
+    # annealing run, host population and statistics out, every step.
+    if w["kind"] == "pa":
+        R = w["R"]
+        host_in = torch.empty(R * N, dtype=torch.int8, pin_memory=True)
+        host_out = torch.empty(R * N, dtype=torch.int8, pin_memory=True)
+        from paper_1709_04394_gb300 import inputs
+
+        host_in.numpy()[:] = inputs.random_spins(R * N, seed=seed0 + 77)
+        n_e2e = max(1, min(args.steps, 3))
+        stats_bytes = 0
+        barrier(dist, ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            gbmc.lattice_copy_in(ctx, lat, host_in)
+            gbmc.pa_reset(ctx, pa, False, seed0 + 500 + k)
+            stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
+            gbmc.lattice_copy_out(ctx, lat, host_out)
+            stats_bytes = stats.nbytes
+        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
+        result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=R * N, d2h=R * N + stats_bytes, steps=n_e2e)
+        gbmc.pa_free(pa)
+    else:
+        host = torch.empty(N, dtype=torch.int8, pin_memory=True)
+        host.numpy()[:] = __import__("paper_1709_04394_gb300.inputs", fromlist=["x"]).random_spins(N, seed=seed0)
+        n_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            gbmc.lattice_copy_in(ctx, lat, host)
+            gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
+            gbmc.lattice_copy_out(ctx, lat, host)
+        t_e2e = (time.perf_counter() - t0)
+        t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
+        result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=N, d2h=N, steps=n_e2e)
+    gbmc.lattice_free(lat)
+    gbmc.gbmc_destroy(ctx)
+    return result
+
+
+def cpu_oracle_sample(w, target_s=12.0):
+    """Time the CPU oracle (single thread, as it stands) on a bounded sample of
+    the workload; returns (site updates per ns, description, seconds)."""
+    import oracle
+
+    oracle.build()
+    if w["kind"] == "pa":
+        R, steps = 1000, 3
+        betas = oracle.linear_betas(w["beta_f"], w["S"])[: steps + 1]
+        t0 = time.perf_counter()
+        oracle.pa_run(w["dim"], w["L"], 1, 0, R, betas, w["theta"])
+        dt = time.perf_counter() - t0
+        upd = R * w["L"] ** w["dim"] * w["theta"] * steps
+        desc = "oracle pa_run: L=%d, R=%d replicas (of %d), first %d of %d temperature steps, theta=%d" % (
+            w["L"], R, w["R"], steps, w["S"], w["theta"])
+    else:
+        n = 2
+        s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
+        t0 = time.perf_counter()
+        oracle.sweeps(w["dim"], w["L"], s, None, w["beta"], 1, 0, 0, 0, n)
+        dt = time.perf_counter() - t0
+        upd = w["L"] ** w["dim"] * n
+        desc = "oracle sweeps: L=%d, %d of %d sweeps" % (w["L"], n, w["sweeps"])
+    return upd / (dt * 1e9), desc, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
+    ap.add_argument("--workload", default="pa-ising2d-L64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+    metric = "spin-flips/ns (checkerboard Metropolis site updates per ns, whole annealing runs incl. resampling)" \
+        if w["kind"] == "pa" else "spin-flips/ns (checkerboard Metropolis site updates per ns)"
+    upd = site_updates_per_step(w)
+    config = {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
+              "l2_flush": "inputs larger than L2 (2 x 409.6 MB population)" if w["kind"] == "pa"
+              else "none: 16 MiB lattice is L2-resident (single-lattice case)",
+              "parallelism": "replicas only: independent populations per rank" if ws > 1 else "single GPU"}
+
+    if args.impl == "reference":
+        # the CPU oracle as it stands, on the host cores, bounded sample per step
+        if rank != 0:
+            return
+        vals = []
+        for _ in range(args.warmup):
+            cpu_oracle_sample(w)
+        t_total = 0.0
+        for _ in range(args.steps):
+            v, desc, dt = cpu_oracle_sample(w)
+            vals.append(v)
+            t_total += dt
+        value = statistics.mean(vals)
+        line = {"impl": "reference", "metric": metric, "value": value, "unit": "spin-flips/ns", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8/int32/f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": "spin-flips/ns", "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "spin-flips/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    res = run_gpu(args, w, ws, rank, local)
+    if rank != 0:
+        return
+    peaks, peak_src = load_peaks()
+    ms = res["ms"]
+    value = ws * upd * args.steps / (ms * 1e6)  # site updates per ns, all ranks
+    prof = res["prof"]
+    # dominant kernel: the sweep kernel of the workload
+    kname = "sweep_resident" if w["kind"] == "pa" else "halfsweep_global"
+    n_l, t_l = prof.get(kname, (0, 0.0))
+    avg_ms = t_l / n_l if n_l else float("nan")
+    if w["kind"] == "pa":
+        upd_per_launch = w["R"] * w["L"] ** w["dim"] * w["theta"]
+        hbm_bytes_per_launch = 2 * w["R"] * w["L"] ** w["dim"] + 12 * w["R"]
+    else:
+        upd_per_launch = w["L"] ** w["dim"] // 2
+        hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 2
+    ops = ALG_INT_OPS_PER_SITE_UPDATE * upd_per_launch
+    achieved = ops / (avg_ms * 1e-3) / 1e9  # Gop/s
+    clk = res["clocks"]
+    peak_alu = N_SMS * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e9  # Gop/s: one warp instruction per SMSP per cycle
+    hbm_gbs = hbm_bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    total_ms = sum(t for _, t in prof.values())
+    line = {
+        "metric": metric, "value": value, "unit": "spin-flips/ns", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8 spins / int32 energies / f64 weights", "data": "synthetic",
+        "config": config,
+        "replica_sweeps_per_s": (ws * w["R"] * w["theta"] * w["S"] * args.steps / (ms * 1e-3)) if w["kind"] == "pa" else None,
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction "
+                                    "per SMSP per cycle)",
+                     "alg_ops_per_site_update": ALG_INT_OPS_PER_SITE_UPDATE,
+                     "avg_launch_ms": avg_ms, "launches": n_l,
+                     "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
+                     "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,
+                     "kernel_share": t_l / total_ms if total_ms else None},
+        "kernels": {k: {"launches": n, "total_ms": t} for k, (n, t) in prof.items()},
+        "gpu_launches": res["launches"],
+        "clocks": clk,
+    }
+    e = res["e2e"]
+    if w["kind"] == "pa":
+        e2e_upd = w["R"] * w["L"] ** w["dim"] * w["theta"] * w["S"]
+    else:
+        e2e_upd = upd
+    line["e2e"] = {"value": ws * e2e_upd / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
+                   "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"]}
+    if not args.no_cpu_baseline:
+        v, desc, dt = cpu_oracle_sample(w)
+        line["cpu_baseline"] = {"value": v, "unit": "spin-flips/ns", "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * gbmc.h -- C ABI of the GB300 library for checkerboard Metropolis sweeps of
+ * Ising-type lattices and population annealing (arXiv:1709.04394).
+ *
+ * Conventions (apply to every entry point):
+ *  - Every call returns a gbmc_status: 0 on success, a negative code on error.
+ *    No exception crosses the ABI. gbmc_last_error() returns a message for the
+ *    calling host thread's last failed call.
+ *  - Work is enqueued asynchronously on the context's CUDA stream unless the
+ *    entry point says it synchronises. Device pointers passed in are owned by
+ *    the caller and must stay valid until the enqueued work has completed.
+ *  - Handles (gbmc_ctx, gbmc_lattice, gbmc_pa) are owned by the library and
+ *    released with gbmc_destroy / lattice_free / pa_free.
+ *  - Spin layout ("int8 layout"): int8 values +1 / -1, one byte per site,
+ *    [instance][replica][site], site index row-major with x fastest:
+ *    2D site = y*L + x, 3D site = (z*L + y)*L + x. Periodic boundaries.
+ *  - Random numbers: Philox4x32-10 (Sec. 4, counter-based generators) with
+ *    key = (seed & 0xffffffff, seed >> 32) and counter (q, t, r, c3), where
+ *    c3 = purpose<<28 | colour<<27 | instance. Metropolis (purpose 0): for the
+ *    k-th site of colour c in row-major order, q = k>>2 and the site uses
+ *    output word k&3; t = the lattice's sweep counter; r = replica index
+ *    within its instance. Random start (purpose 1): q = site>>2, word site&3,
+ *    t = 0, s = +1 if the word's top bit is 0. Resampling draw k (purpose 2):
+ *    q = k>>1, t = annealing step, r = 0, 64-bit value (w[2l+1]<<32)|w[2l],
+ *    l = k&1. Couplings (purpose 3): bond b = 3*site + mu, q = b>>2, word b&3,
+ *    t = r = 0, J = +1 if the top bit is 0. These numbers depend only on these
+ *    indices, never on how the work is spread over the GPU (Sec. 4).
+ *  - Metropolis acceptance (Sec. 3.1, Eq. (8)): a site with dE <= 0 flips;
+ *    otherwise it flips iff its 32-bit word u satisfies u <= T(dE), with
+ *    T(dE) = ceil(exp(-beta dE) * 2^32) - 1 computed in fp64 on the host, i.e.
+ *    r = u 2^-32 < exp(-beta dE). Even sub-lattice ((x+y[+z]) even) first.
+ */
+#ifndef GBMC_H
+#define GBMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBMC_OK = 0,
+    GBMC_ERR_ARG = -1,     /* invalid argument, size or layout */
+    GBMC_ERR_OOM = -2,     /* device or host allocation failed */
+    GBMC_ERR_CUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    GBMC_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up; results are invalid */
+    GBMC_ERR_STATE = -5    /* call not valid in the handle's current state */
+} gbmc_status;
+
+enum { GBMC_ISING_FM = 0, GBMC_EA_PMJ = 1 };            /* model */
+enum { GBMC_INT8 = 0, GBMC_BITPACK = 1 };               /* storage layout */
+enum { GBMC_START_ALL_UP = 0, GBMC_START_RANDOM = 1 };  /* initial state */
+
+typedef struct gbmc_ctx gbmc_ctx;
+typedef struct gbmc_lattice gbmc_lattice;
+typedef struct gbmc_pa gbmc_pa;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int gbmc_version(void);
+
+/* Message of the calling thread's last failed call ("" if none). The pointer
+ * stays valid until the thread's next gbmc call. */
+const char *gbmc_last_error(void);
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). The stream is borrowed. */
+gbmc_status gbmc_create(gbmc_ctx **out, int device, void *cuda_stream);
+gbmc_status gbmc_set_stream(gbmc_ctx *ctx, void *cuda_stream);
+/* Synchronise the context's stream and report any device-side error flag
+ * (GBMC_ERR_TIMEOUT) raised by a bounded wait since the last check. */
+gbmc_status gbmc_sync(gbmc_ctx *ctx);
+gbmc_status gbmc_destroy(gbmc_ctx *ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every launch the library enqueues (off by default). gbmc_profile(ctx, 1)
+ * clears the counters and starts recording; 0 stops. gbmc_profile_read
+ * synchronises the stream and fills up to `capacity` entries (one per kernel
+ * kind that ran), *n_out = their number. Times are device times between the
+ * events bracketing the launches of that kind, in milliseconds. */
+typedef struct {
+    char name[32];
+    uint64_t launches;  /* kernels of this kind enqueued while recording */
+    double total_ms;    /* summed event-to-event device time */
+} gbmc_kernel_time;
+gbmc_status gbmc_profile(gbmc_ctx *ctx, int32_t enable);
+gbmc_status gbmc_profile_read(gbmc_ctx *ctx, gbmc_kernel_time *out, uint32_t capacity, uint32_t *n_out);
+/* Number of kernels this library has enqueued in this process so far. */
+uint64_t gbmc_kernel_launches(void);
+
+/* ------------------------------------------------------------------------ */
+/* Lattices: one or more independent copies of an L^dim periodic lattice.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t dim;            /* 2 or 3 */
+    int32_t L;              /* linear size, even, 2 <= L <= 32768 (dim 2) / 1024 (dim 3) */
+    int32_t model;          /* GBMC_ISING_FM (J = 1) or GBMC_EA_PMJ (bimodal +-J, Sec. 6) */
+    int32_t layout;         /* GBMC_INT8 or GBMC_BITPACK (dim 2, FM, L % 64 == 0) */
+    int32_t start;          /* GBMC_START_ALL_UP or GBMC_START_RANDOM */
+    uint32_t n_instances;   /* disorder instances (independent couplings), >= 1 */
+    uint32_t n_replicas;    /* replicas per instance, >= 1 */
+    uint32_t instance_base; /* Philox instance id of the first instance (< 2^27) */
+    uint64_t seed;          /* Philox key */
+} gbmc_lattice_desc;
+
+typedef struct {
+    int64_t n_sites;        /* N = L^dim */
+    int64_t n_copies;       /* n_instances * n_replicas */
+    int64_t spin_bytes;     /* bytes of one configuration buffer in the lattice's layout */
+    uint32_t sweep_counter; /* t of the next sweep */
+    uint32_t pad;
+    void *spins_dev;        /* buffer that holds the current configuration */
+} gbmc_lattice_info;
+
+/* Create a lattice and write its initial state (Sec. 3.1, step 1).
+ * spins_dev: caller-owned device buffer of at least info.spin_bytes bytes
+ * (int8 layout: n_instances*n_replicas*N bytes; bit-packed: N/8 bytes per
+ * copy), 16-byte aligned; NULL lets the library allocate it. For GBMC_EA_PMJ
+ * the couplings of every instance are drawn here from the seed (purpose 3)
+ * and kept in library memory. Enqueued on the context stream. */
+gbmc_status lattice_init(gbmc_ctx *ctx, const gbmc_lattice_desc *desc, void *spins_dev,
+                         size_t spins_bytes, gbmc_lattice **out);
+gbmc_status lattice_free(gbmc_lattice *lat);
+gbmc_status lattice_info(const gbmc_lattice *lat, gbmc_lattice_info *out);
+gbmc_status lattice_set_sweep_counter(gbmc_lattice *lat, uint32_t t);
+
+/* Copy the current configuration out in the int8 layout (bytes must equal
+ * n_copies*N). dst may be host (pageable or pinned) or device memory. For a
+ * bit-packed lattice the copy is unpacked on the device first. Synchronises
+ * the context stream when dst is host memory. */
+gbmc_status lattice_copy_out(gbmc_ctx *ctx, const gbmc_lattice *lat, int8_t *dst, size_t bytes);
+/* Overwrite the configuration from an int8-layout buffer (host or device);
+ * values must be +1/-1 (others give undefined dynamics). */
+gbmc_status lattice_copy_in(gbmc_ctx *ctx, gbmc_lattice *lat, const int8_t *src, size_t bytes);
+/* Couplings of a GBMC_EA_PMJ lattice as int8 +-1, [instance][site][mu], mu = x,y,z
+ * forward bonds (bytes = n_instances*N*3). */
+gbmc_status lattice_couplings_out(gbmc_ctx *ctx, const gbmc_lattice *lat, int8_t *dst, size_t bytes);
+
+/* n_sweeps checkerboard Metropolis sweeps at inverse temperature beta of every
+ * copy (Sec. 3.1; Eq. (8)), sweep counters t .. t+n_sweeps-1; the lattice's
+ * counter advances by n_sweeps. 0 <= beta*4*dim <= 700.
+ * E_series_dev / M_series_dev: NULL, or device int32 [n_sweeps][n_copies]
+ * receiving E (Eq. (7)) and M = sum_i s_i after every sweep. */
+gbmc_status metropolis_sweeps(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_sweeps,
+                              int32_t *E_series_dev, int32_t *M_series_dev);
+
+/* Energy E = -sum_<ij> J_ij s_i s_j (Eq. (7), forward bonds) and magnetisation
+ * M = sum_i s_i of every copy, into device int32 arrays [n_copies]. */
+gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, int32_t *M_dev);
+
+/* ------------------------------------------------------------------------ */
+/* Population annealing (Sec. 5.4): every (lattice, instance) pair is one     */
+/* population of n_replicas replicas annealed from beta_0 = 0.               */
+/* ------------------------------------------------------------------------ */
+enum {
+    GBMC_SCHED_LINEAR = 0,    /* beta_i = (beta_f * i) / n_steps, i = 0..n_steps */
+    GBMC_SCHED_LIST = 1,      /* beta_i = betas[i], i = 0..n_steps, betas[0] = 0 */
+    GBMC_SCHED_BISECTION = 2, /* per lattice: dbeta from histogram overlap bisection */
+    GBMC_SCHED_MLP = 3        /* per lattice: MLP proposal, judged by the overlap */
+};
+
+typedef struct {
+    uint32_t theta;          /* Metropolis sweeps per temperature step */
+    uint32_t n_steps;        /* resampling steps S (LINEAR, LIST); step cap (adaptive) */
+    int32_t schedule;        /* GBMC_SCHED_* */
+    int32_t init;            /* 1: random start of every replica (exact at beta_0 = 0);
+                                0: keep the lattices' current spins (taken as beta_0 = 0 samples) */
+    double beta_f;           /* final inverse temperature */
+    const double *betas;     /* host [n_steps+1] for GBMC_SCHED_LIST (copied) */
+    double target_overlap;   /* adaptive schedules: histogram overlap to aim at (0.85) */
+    double dbeta_max;        /* adaptive schedules: largest step */
+    const float *mlp_params; /* GBMC_SCHED_MLP: host fp32 parameters, gbmc_mlp_param_count() */
+    double overlap_lo;       /* GBMC_SCHED_MLP: accept a proposal if lo <= overlap <= hi */
+    double overlap_hi;
+} gbmc_pa_config;
+
+/* Per-population record of one annealing step (after its sweeps). */
+typedef struct {
+    double beta;             /* beta_i */
+    double dbeta;            /* beta_i - beta_{i-1} (0 at i = 0) */
+    double lnQ;              /* ln Q_i, Eq. (13) */
+    double lnZ;              /* N ln 2 + sum_{k<=i} ln Q_k */
+    int64_t sumE, sumE2;     /* exact sums over the population of E and E^2 */
+    int64_t sumAbsM, sumM2;  /* exact sums of |M| and M^2 */
+    int32_t Emin, Emax;      /* population energy range */
+    uint32_t step;           /* i */
+    uint32_t n_replicas;     /* R */
+    double overlap;          /* adaptive schedules: realised histogram overlap, else 0 */
+    int32_t proposal_kind;   /* 0 fixed, 1 bisection, 2 accepted MLP proposal */
+    int32_t pad;
+} gbmc_pa_stats;
+
+/* Create an annealing run over n_lattices lattices advanced together (one
+ * sweep launch covers all of them). Library-owned device workspace: a second
+ * configuration buffer per lattice, energies, histograms, resampling scratch,
+ * and the fp64 weight tables. If cfg->init, every replica is randomised and
+ * step 0 (beta_0 = 0) is recorded. Lattices must outlive the run. */
+gbmc_status pa_create(gbmc_ctx *ctx, gbmc_lattice *const *lattices, uint32_t n_lattices,
+                      const gbmc_pa_config *cfg, gbmc_pa **out);
+gbmc_status pa_free(gbmc_pa *pa);
+/* Start the run over from beta_0 = 0 without reallocating: step counter, ln Z
+ * and accumulators are reset, the sweep counters return to their values at
+ * pa_create, and step 0 is measured again. seed != 0 replaces every lattice's
+ * Philox seed first. init != 0 draws a fresh random start from the (new)
+ * seed; init == 0 keeps the current spins as the beta_0 = 0 population. */
+gbmc_status pa_reset(gbmc_ctx *ctx, gbmc_pa *pa, int32_t init, uint64_t seed);
+/* Number of populations (sum over lattices of n_instances); stats arrays are
+ * indexed [step][population], lattices in creation order, instances within. */
+gbmc_status pa_populations(const gbmc_pa *pa, uint32_t *n_populations);
+
+/* One annealing step (Sec. 5.4 steps 2-4): resample every population to its
+ * next inverse temperature, theta sweeps there, population measurements.
+ * beta_next: NULL = the schedule's next value; else host [n_lattices]
+ * (must exceed the current beta). out_host: NULL or host [n_populations].
+ * Synchronises when out_host != NULL or the schedule is adaptive.
+ * Returns GBMC_ERR_STATE once every lattice has reached beta_f. */
+gbmc_status pa_step(gbmc_ctx *ctx, gbmc_pa *pa, const double *beta_next, gbmc_pa_stats *out_host);
+
+/* All remaining steps; stats_host: NULL or host [n_steps_max+1][n_populations]
+ * (record of step 0 included); n_steps_done: number of steps taken by the run
+ * so far. Synchronises. */
+gbmc_status pa_run(gbmc_ctx *ctx, gbmc_pa *pa, gbmc_pa_stats *stats_host, uint32_t stats_capacity,
+                   uint32_t *n_steps_done);
+
+/* Replica each slot was copied from in the last resampling (device or host
+ * dst, uint32 [n_copies] of that lattice; indices within the instance). */
+gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, uint32_t *dst,
+                           size_t count);
+/* Energies and magnetisations of the current population of a lattice
+ * (device or host int32 [n_copies]). */
+gbmc_status pa_energies_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, int32_t *E_dst,
+                            int32_t *M_dst, size_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMC_H */

@@ -62,7 +62,7 @@ def _load():
         lib.orc_resample.restype = dbl
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
-                                   p, p, p, p, p, p, p, p, p]
+                                   p, p, p, p, p, p, p, p, p, p]
         _lib = lib
         return lib
 
@@ -180,9 +180,10 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None):
     hashes = np.zeros(S + 1, dtype=np.uint64)
     E = np.zeros(R, dtype=np.int64)
     M = np.zeros(R, dtype=np.int64)
+    parents = np.arange(R, dtype=np.uint32)
     lib.orc_pa_run(dim, L, _ptr(Jc), seed, instance, R, S, _ptr(betas), theta, _ptr(spins),
                    int(init), _ptr(out["lnQ"]), _ptr(out["lnZ"]), _ptr(sumE), _ptr(out["sumE2"]),
-                   _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M))
-    out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M,
+                   _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M), _ptr(parents))
+    out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents,
                spins=spins.reshape(R, N), betas=betas)
     return out

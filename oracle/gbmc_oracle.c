@@ -347,13 +347,13 @@ void orc_children_order(uint32_t R, const uint32_t *counts, uint32_t *parent_of_
 /* spins[R*N] in/out: if init != 0 the population is initialised here.       */
 /* Per step outputs (arrays of S+1, index 0 = beta_0): lnQ, lnZ, sum E,      */
 /* sum E^2 (as double of exact int64 sums), sum |M|, sum M^2, and a running   */
-/* FNV-1a hash of the counts for cross-checking.                              */
+/* FNV-1a hash of the counts; optionally the last step's slot -> parent map.   */
 /* ------------------------------------------------------------------------ */
 void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R,
                 uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                 double *lnQ_out, double *lnZ_out, int64_t *sumE_out, double *sumE2_out,
                 int64_t *sumAbsM_out, double *sumM2_out, uint64_t *counts_hash_out,
-                int64_t *E_final, int64_t *M_final)
+                int64_t *E_final, int64_t *M_final, uint32_t *parents_last)
 {
     int64_t N = orc_nsites(dim, L);
     int64_t *E = (int64_t *)malloc(sizeof(int64_t) * R);
@@ -378,6 +378,7 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
                 hash *= 1099511628211ull;
             }
             orc_children_order(R, counts, parent);
+            if (parents_last) memcpy(parents_last, parent, sizeof(uint32_t) * R);
             for (uint32_t m = 0; m < R; ++m)
                 memcpy(next + (size_t)m * N, spins + (size_t)parent[m] * N, (size_t)N);
             memcpy(spins, next, (size_t)R * (size_t)N);

@@ -1,0 +1,903 @@
+// api.cu -- the C ABI declared in include/gbmc.h: contexts, lattices, sweeps,
+// observables and population annealing runs. Host code here only validates,
+// sizes launches, computes the per-beta tables (thresholds of Eq. (8), fp64
+// resampling weights of Eq. (13)) and enqueues the kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gbmc.h"
+#include "internal.h"
+
+using namespace gbmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+gbmc_status fail(gbmc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? GBMC_ERR_OOM : GBMC_ERR_CUDA,       \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+std::atomic<uint64_t> g_launches{0};
+
+enum ProfKind {
+    PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
+    PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_COUNT
+};
+const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
+                                          "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
+                                          "pa_record", "pa_reset"};
+
+}  // namespace
+
+namespace gbmc {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace gbmc
+
+struct gbmc_ctx {
+    int device;
+    cudaStream_t stream;
+    int sm_count;
+    bool prof = false;
+    struct Pending {
+        int kind;
+        uint64_t launches;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[PK_COUNT] = {};
+    uint64_t launches[PK_COUNT] = {};
+
+    cudaEvent_t event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+namespace {
+// Brackets one launcher call with CUDA events when profiling is on.
+struct ProfScope {
+    gbmc_ctx* c;
+    int kind;
+    uint64_t n0;
+    cudaEvent_t a = nullptr;
+    ProfScope(gbmc_ctx* ctx, int k) : c(ctx), kind(k), n0(g_launches.load()) {
+        if (c->prof) {
+            a = c->event();
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~ProfScope() {
+        const uint64_t n = g_launches.load() - n0;
+        if (c->prof) {
+            cudaEvent_t b = c->event();
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({kind, n, a, b});
+        }
+    }
+};
+}  // namespace
+
+struct gbmc_lattice {
+    gbmc_ctx* ctx;
+    gbmc_lattice_desc d;
+    uint64_t N;
+    uint64_t ncopies;
+    int8_t* spins;     // caller's (or library-allocated) buffer
+    bool owns_spins;
+    int8_t* cur;       // buffer holding the current configuration
+    uint8_t* jbits;    // +-J bond planes [inst][3][N]
+    uint32_t t;        // sweep counter
+    gbmc_pa* run;      // annealing run using this lattice
+};
+
+namespace {
+
+struct PaLat {
+    gbmc_lattice* lat = nullptr;
+    int8_t* alt = nullptr;
+    int32_t *E = nullptr, *M = nullptr;
+    uint32_t* hist = nullptr;
+    int32_t *emin = nullptr, *emax = nullptr;
+    unsigned long long* sums = nullptr;
+    double* lnZ = nullptr;  // [2*n_inst]: lnZ, then lnQ of the last step
+    unsigned long long *cloc = nullptr, *ctot = nullptr, *cpre = nullptr;
+    uint32_t *counts = nullptr, *sloc = nullptr, *ntot = nullptr, *parent = nullptr;
+    double* wexp = nullptr;                // [n_tables][nbins]
+    unsigned long long* wint = nullptr;    // [n_tables][nbins]
+    std::vector<double> betas;             // beta_0 .. beta_S
+    std::vector<uint32_t> thr;             // [S+1][3]
+    uint32_t nbins = 0, nchunks = 0;
+    int32_t e_lo = 0;
+    int s_bits = 0;
+    uint32_t pop0 = 0;                     // first population index
+    uint32_t t_start = 0;
+};
+
+}  // namespace
+
+struct gbmc_pa {
+    gbmc_ctx* ctx;
+    gbmc_pa_config cfg;
+    std::vector<PaLat> lats;
+    uint32_t P = 0;
+    uint32_t S = 0;        // steps of the schedule
+    uint32_t step = 0;     // steps done
+    gbmc_pa_stats* stats = nullptr;  // device [S+1][P]
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// T(dE) = ceil(exp(-beta dE) 2^32) - 1 (Eq. (8) as an integer comparison).
+void thresholds(double beta, uint32_t out[3]) {
+    for (int m = 0; m < 3; ++m) {
+        const double dE = 4.0 * (double)(m + 1);
+        const double p = std::exp(-(beta * dE));
+        const double scaled = std::ldexp(p, 32);
+        const int64_t t = (int64_t)std::ceil(scaled) - 1;
+        out[m] = (uint32_t)(t < 0 ? 0 : (t > 0xFFFFFFFFll ? 0xFFFFFFFFll : t));
+    }
+}
+
+bool beta_ok(double beta, int dim) { return std::isfinite(beta) && beta >= 0.0 && beta * 4.0 * dim <= 700.0; }
+
+struct Tuning {
+    bool resident;
+    uint32_t tpr, rpc, threads;
+    size_t smem;
+};
+
+// Launch shape of the resident sweep for one lattice: threads per copy `tpr`
+// (a power of two covering the copy's units, at most 256), copies per CTA rpc.
+Tuning tune(const gbmc_lattice* l) {
+    Tuning t{};
+    const uint64_t N = l->N;
+    const bool ea = l->d.model == GBMC_EA_PMJ;
+    const uint64_t stride = (N + 15) & ~15ull;
+    const uint64_t units = (l->d.L % 8 == 0) ? N / 8 : ((N / 2) + 3) / 4;
+    const size_t one = stride + (ea ? 3 * N : 0);
+    if (one > kSmemLimit || N > (1ull << 31)) {
+        t.resident = false;
+        return t;
+    }
+    uint32_t tpr = 8;
+    while (tpr < units && tpr < 256) tpr <<= 1;
+    uint32_t rpc = 256 / tpr;
+    if (rpc > l->d.n_replicas) rpc = l->d.n_replicas;
+    if (rpc < 1) rpc = 1;
+    while (rpc > 1 && rpc * stride + (ea ? 3 * N : 0) > kSmemLimit) --rpc;
+    t.resident = true;
+    t.tpr = tpr;
+    t.rpc = rpc;
+    t.threads = tpr * rpc;
+    if (t.threads < 32) t.threads = 32, t.tpr = 32 / rpc;
+    t.smem = rpc * stride + (ea ? 3 * N : 0);
+    return t;
+}
+
+SweepJob base_job(const gbmc_lattice* l, const Tuning& tu) {
+    SweepJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.src = l->cur;
+    J.dst = l->cur;
+    J.jbits = l->jbits;
+    J.seed = l->d.seed;
+    J.L = (uint32_t)l->d.L;
+    J.N = (uint32_t)l->N;
+    J.R = l->d.n_replicas;
+    J.n_inst = l->d.n_instances;
+    J.inst_base = l->d.instance_base;
+    J.t0 = l->t;
+    J.rpc = tu.rpc;
+    J.ctas_per_inst = (J.R + tu.rpc - 1) / tu.rpc;
+    J.e_lo = -(int32_t)(l->d.dim * l->N);
+    J.nbins = (uint32_t)(l->d.dim * l->N / 2 + 1);
+    return J;
+}
+
+gbmc_status launch_jobs(gbmc_ctx* ctx, SweepLaunch& P, const std::vector<Tuning>& tu) {
+    uint32_t total = 0, threads = 0;
+    for (int j = 0; j < P.njobs; ++j) {
+        P.cta_begin[j] = total;
+        total += P.jobs[j].n_inst * P.jobs[j].ctas_per_inst;
+        if (tu[j].threads > threads) threads = tu[j].threads;
+    }
+    P.cta_begin[P.njobs] = total;
+    // every job must use the same thread count: copies per CTA scale with it
+    for (int j = 0; j < P.njobs; ++j)
+        if (tu[j].threads != threads)
+            return fail(GBMC_ERR_ARG, "lattices of one launch need equal CTA shapes");
+    const size_t smem = resident_smem_bytes(P);
+    ProfScope ps_(ctx, PK_SWEEP_RES);
+    CUDA_TRY(launch_sweep_resident(P, total, threads, smem, ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status dalloc(gbmc_pa* pa, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(GBMC_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    pa->allocs.push_back(*p);
+    return GBMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbmc_version(void) { return 100; }
+
+const char* gbmc_last_error(void) { return g_err.c_str(); }
+
+gbmc_status gbmc_create(gbmc_ctx** out, int device, void* cuda_stream) {
+    if (!out) return fail(GBMC_ERR_ARG, "out is NULL");
+    int n = 0;
+    CUDA_TRY(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(GBMC_ERR_ARG, "device %d out of range (%d devices)", device, n);
+    CUDA_TRY(cudaSetDevice(device));
+    gbmc_ctx* c = new (std::nothrow) gbmc_ctx();
+    if (!c) return fail(GBMC_ERR_OOM, "host allocation");
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    *out = c;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_set_stream(gbmc_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_sync(gbmc_ctx* ctx) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_destroy(gbmc_ctx* ctx) {
+    if (!ctx) return GBMC_OK;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_profile(gbmc_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->pending) {
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    if (enable)
+        for (int k = 0; k < PK_COUNT; ++k) ctx->ms[k] = 0.0, ctx->launches[k] = 0;
+    ctx->prof = enable != 0;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_profile_read(gbmc_ctx* ctx, gbmc_kernel_time* out, uint32_t capacity, uint32_t* n_out) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+        ctx->ms[p.kind] += ms;
+        ctx->launches[p.kind] += p.launches;
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    uint32_t n = 0;
+    for (int k = 0; k < PK_COUNT; ++k) {
+        if (ctx->launches[k] == 0) continue;
+        if (out && n < capacity) {
+            std::memset(&out[n], 0, sizeof(out[n]));
+            std::snprintf(out[n].name, sizeof(out[n].name), "%s", kProfNames[k]);
+            out[n].launches = ctx->launches[k];
+            out[n].total_ms = ctx->ms[k];
+        }
+        ++n;
+    }
+    if (n_out) *n_out = n;
+    return GBMC_OK;
+}
+
+uint64_t gbmc_kernel_launches(void) { return g_launches.load(); }
+
+gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_dev, size_t spins_bytes,
+                         gbmc_lattice** out) {
+    if (!ctx || !d || !out) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (d->dim != 2 && d->dim != 3) return fail(GBMC_ERR_ARG, "dim must be 2 or 3 (got %d)", d->dim);
+    if (d->L < 2 || (d->L & 1)) return fail(GBMC_ERR_ARG, "L must be even and >= 2 (got %d)", d->L);
+    if ((d->dim == 2 && d->L > 32768) || (d->dim == 3 && d->L > 1024))
+        return fail(GBMC_ERR_ARG, "L too large");
+    if (d->model != GBMC_ISING_FM && d->model != GBMC_EA_PMJ) return fail(GBMC_ERR_ARG, "unknown model");
+    if (d->model == GBMC_EA_PMJ && d->dim != 3) return fail(GBMC_ERR_ARG, "the +-J model is three-dimensional");
+    if (d->layout != GBMC_INT8) return fail(GBMC_ERR_ARG, "layout %d not supported by this build", d->layout);
+    if (d->start != GBMC_START_ALL_UP && d->start != GBMC_START_RANDOM) return fail(GBMC_ERR_ARG, "unknown start");
+    if (d->n_instances == 0 || d->n_replicas == 0) return fail(GBMC_ERR_ARG, "empty lattice set");
+    if ((uint64_t)d->instance_base + d->n_instances > (1ull << 27)) return fail(GBMC_ERR_ARG, "instance ids exceed 2^27");
+    uint64_t N = 1;
+    for (int i = 0; i < d->dim; ++i) N *= (uint64_t)d->L;
+    const uint64_t ncopies = (uint64_t)d->n_instances * d->n_replicas;
+    if (d->n_replicas > 0xFFFFFFFFull || N * (uint64_t)d->dim > 0x7FFFFFFFull)
+        return fail(GBMC_ERR_ARG, "lattice too large for 32-bit energies");
+    const uint64_t bytes = ncopies * N;
+    if (spins_dev) {
+        if (spins_bytes < bytes) return fail(GBMC_ERR_ARG, "spins buffer has %zu bytes, need %llu", spins_bytes, (unsigned long long)bytes);
+        if (((uintptr_t)spins_dev & 15) != 0) return fail(GBMC_ERR_ARG, "spins buffer must be 16-byte aligned");
+        if (!is_device_ptr(spins_dev)) return fail(GBMC_ERR_ARG, "spins buffer is not device memory");
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    gbmc_lattice* l = new (std::nothrow) gbmc_lattice;
+    if (!l) return fail(GBMC_ERR_OOM, "host allocation");
+    std::memset(l, 0, sizeof(*l));
+    l->ctx = ctx;
+    l->d = *d;
+    l->N = N;
+    l->ncopies = ncopies;
+    if (spins_dev) {
+        l->spins = (int8_t*)spins_dev;
+    } else {
+        cudaError_t e = cudaMalloc(&l->spins, bytes);
+        if (e != cudaSuccess) {
+            delete l;
+            return fail(GBMC_ERR_OOM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+        }
+        l->owns_spins = true;
+    }
+    l->cur = l->spins;
+    if (d->model == GBMC_EA_PMJ) {
+        cudaError_t e = cudaMalloc(&l->jbits, 3 * N * d->n_instances);
+        if (e != cudaSuccess) {
+            if (l->owns_spins) cudaFree(l->spins);
+            delete l;
+            return fail(GBMC_ERR_OOM, "cudaMalloc(couplings): %s", cudaGetErrorString(e));
+        }
+        ProfScope ps_(ctx, PK_COUPLINGS);
+        CUDA_TRY(launch_couplings(l->jbits, (uint32_t)d->L, d->n_instances, d->instance_base, d->seed, ctx->stream));
+    }
+    {
+        ProfScope ps_(ctx, PK_INIT);
+        CUDA_TRY(launch_init_spins(l->spins, d->dim, (uint32_t)d->L, d->n_instances, d->n_replicas, d->instance_base,
+                                   d->seed, d->start == GBMC_START_RANDOM, ctx->stream));
+    }
+    *out = l;
+    return GBMC_OK;
+}
+
+gbmc_status lattice_free(gbmc_lattice* l) {
+    if (!l) return GBMC_OK;
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice still used by an annealing run");
+    if (l->owns_spins) cudaFree(l->spins);
+    if (l->jbits) cudaFree(l->jbits);
+    delete l;
+    return GBMC_OK;
+}
+
+gbmc_status lattice_info(const gbmc_lattice* l, gbmc_lattice_info* out) {
+    if (!l || !out) return fail(GBMC_ERR_ARG, "NULL argument");
+    out->n_sites = (int64_t)l->N;
+    out->n_copies = (int64_t)l->ncopies;
+    out->spin_bytes = (int64_t)(l->N * l->ncopies);
+    out->sweep_counter = l->t;
+    out->pad = 0;
+    out->spins_dev = l->cur;
+    return GBMC_OK;
+}
+
+gbmc_status lattice_set_sweep_counter(gbmc_lattice* l, uint32_t t) {
+    if (!l) return fail(GBMC_ERR_ARG, "NULL lattice");
+    l->t = t;
+    return GBMC_OK;
+}
+
+gbmc_status lattice_copy_out(gbmc_ctx* ctx, const gbmc_lattice* l, int8_t* dst, size_t bytes) {
+    if (!ctx || !l || !dst) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (bytes != l->N * l->ncopies) return fail(GBMC_ERR_ARG, "bytes must be %llu", (unsigned long long)(l->N * l->ncopies));
+    CUDA_TRY(cudaMemcpyAsync(dst, l->cur, bytes, cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(dst)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status lattice_copy_in(gbmc_ctx* ctx, gbmc_lattice* l, const int8_t* src, size_t bytes) {
+    if (!ctx || !l || !src) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (bytes != l->N * l->ncopies) return fail(GBMC_ERR_ARG, "bytes must be %llu", (unsigned long long)(l->N * l->ncopies));
+    CUDA_TRY(cudaMemcpyAsync(l->cur, src, bytes, cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(src)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status lattice_couplings_out(gbmc_ctx* ctx, const gbmc_lattice* l, int8_t* dst, size_t bytes) {
+    if (!ctx || !l || !dst) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!l->jbits) return fail(GBMC_ERR_STATE, "lattice has no couplings (ferromagnet)");
+    const size_t need = 3 * l->N * l->d.n_instances;
+    if (bytes != need) return fail(GBMC_ERR_ARG, "bytes must be %zu", need);
+    int8_t* tmp = dst;
+    const bool dev = is_device_ptr(dst);
+    if (!dev) CUDA_TRY(cudaMallocAsync((void**)&tmp, need, ctx->stream));
+    CUDA_TRY(launch_jbits_to_int8(l->jbits, tmp, (uint32_t)l->N, l->d.n_instances, ctx->stream));
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(cudaFreeAsync(tmp, ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return GBMC_OK;
+}
+
+gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t n_sweeps, int32_t* E_series,
+                              int32_t* M_series) {
+    if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!beta_ok(beta, l->d.dim)) return fail(GBMC_ERR_ARG, "beta must satisfy 0 <= 4*dim*beta <= 700 (got %g)", beta);
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice is owned by an annealing run");
+    if (n_sweeps == 0) return GBMC_OK;
+    if ((uint64_t)l->t + n_sweeps > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "sweep counter would wrap");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const Tuning tu = tune(l);
+    SweepJob J = base_job(l, tu);
+    thresholds(beta, J.thr);
+    if (tu.resident) {
+        SweepLaunch P;
+        std::memset(&P, 0, sizeof(P));
+        J.nsweeps = n_sweeps;
+        J.Eser = E_series;
+        J.Mser = M_series;
+        P.jobs[0] = J;
+        P.njobs = 1;
+        P.dim = l->d.dim;
+        P.ea = l->d.model == GBMC_EA_PMJ;
+        P.swar = (l->d.L % 8) == 0;
+        gbmc_status st = launch_jobs(ctx, P, std::vector<Tuning>{tu});
+        if (st != GBMC_OK) return st;
+    } else {
+        for (uint32_t s = 0; s < n_sweeps; ++s) {
+            for (int colour = 0; colour < 2; ++colour) {
+                ProfScope ps_(ctx, PK_HALFSWEEP);
+                CUDA_TRY(launch_halfsweep_global(J, l->d.dim, colour, l->t + s, ctx->stream));
+            }
+            ProfScope ps_(ctx, PK_OBS);
+            if (E_series || M_series)
+                CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances,
+                                            l->d.n_replicas, E_series ? E_series + (uint64_t)s * l->ncopies : nullptr,
+                                            M_series ? M_series + (uint64_t)s * l->ncopies : nullptr, ctx->stream));
+        }
+    }
+    l->t += n_sweeps;
+    return GBMC_OK;
+}
+
+gbmc_status observables(gbmc_ctx* ctx, const gbmc_lattice* l, int32_t* E, int32_t* M) {
+    if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!E && !M) return GBMC_OK;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    ProfScope ps_(ctx, PK_OBS);
+    CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances, l->d.n_replicas, E, M,
+                                ctx->stream));
+    return GBMC_OK;
+}
+
+// ------------------------------------------------------------------------
+// Population annealing
+// ------------------------------------------------------------------------
+
+static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
+    PaLattice P;
+    std::memset(&P, 0, sizeof(P));
+    gbmc_lattice* l = pl.lat;
+    P.E = pl.E;
+    P.hist = pl.hist;
+    P.emin = pl.emin;
+    P.emax = pl.emax;
+    P.sums = pl.sums;
+    P.cloc = pl.cloc;
+    P.ctot = pl.ctot;
+    P.cpre = pl.cpre;
+    P.counts = pl.counts;
+    P.sloc = pl.sloc;
+    P.ntot = pl.ntot;
+    P.parent = pl.parent;
+    P.stats = pa->stats + (uint64_t)step * pa->P + pl.pop0;
+    P.beta = pl.betas[step];
+    P.dbeta = step == 0 ? 0.0 : pl.betas[step] - pl.betas[step - 1];
+    if (step > 0) {
+        P.wexp = pl.wexp + (uint64_t)(step - 1) * pl.nbins;
+        P.wint = pl.wint + (uint64_t)(step - 1) * pl.nbins;
+    }
+    P.log_R = std::log((double)l->d.n_replicas);
+    P.seed = l->d.seed;
+    P.R = l->d.n_replicas;
+    P.n_inst = l->d.n_instances;
+    P.inst_base = l->d.instance_base;
+    P.nbins = pl.nbins;
+    P.nchunks = pl.nchunks;
+    P.step = step;
+    P.e_lo = pl.e_lo;
+    return P;
+}
+
+// Sweep launch over every lattice of the run: nsweeps = theta with the
+// resampling gather (step > 0), or a measurement-only pass (step 0).
+static gbmc_status pa_sweep_launch(gbmc_pa* pa, uint32_t step) {
+    SweepLaunch P;
+    std::memset(&P, 0, sizeof(P));
+    std::vector<Tuning> tus;
+    const gbmc_lattice* l0 = pa->lats[0].lat;
+    P.dim = l0->d.dim;
+    P.ea = l0->d.model == GBMC_EA_PMJ;
+    P.swar = 1;
+    for (auto& pl : pa->lats) {
+        gbmc_lattice* l = pl.lat;
+        const Tuning tu = tune(l);
+        tus.push_back(tu);
+        SweepJob J = base_job(l, tu);
+        if (l->d.L % 8) P.swar = 0;
+        thresholds(pl.betas[step], J.thr);
+        J.E = pl.E;
+        J.M = pl.M;
+        J.hist = pl.hist;
+        J.emin = pl.emin;
+        J.emax = pl.emax;
+        J.sums = pl.sums;
+        if (step == 0) {
+            J.nsweeps = 0;
+            J.src = J.dst = l->cur;
+        } else {
+            J.nsweeps = pa->cfg.theta;
+            J.t0 = pl.t_start + (step - 1) * pa->cfg.theta;
+            J.src = l->cur;
+            J.dst = (l->cur == l->spins) ? pl.alt : l->spins;
+            J.parent = pl.parent;
+        }
+        P.jobs[P.njobs++] = J;
+    }
+    gbmc_status st = launch_jobs(pa->ctx, P, tus);
+    if (st != GBMC_OK) return st;
+    if (step > 0) {
+        for (int j = 0; j < P.njobs; ++j) {
+            gbmc_lattice* l = pa->lats[j].lat;
+            l->cur = P.jobs[j].dst;
+            l->t = pa->lats[j].t_start + step * pa->cfg.theta;
+        }
+    }
+    return GBMC_OK;
+}
+
+static gbmc_status pa_record(gbmc_pa* pa, uint32_t step) {
+    for (auto& pl : pa->lats) {
+        PaLattice P = pa_params(pa, pl, step);
+        ProfScope ps_(pa->ctx, PK_PA_RECORD);
+        CUDA_TRY(launch_pa_record(P, pl.lnZ, 0.0, pa->ctx->stream));
+    }
+    return GBMC_OK;
+}
+
+// Step 0: random start (exact equilibrium at beta_0 = 0, Sec. 5.4 step 1)
+// and its measurement.
+static gbmc_status pa_begin(gbmc_pa* pa, int init) {
+    cudaStream_t s = pa->ctx->stream;
+    for (auto& pl : pa->lats) {
+        gbmc_lattice* l = pl.lat;
+        if (init) {
+            l->cur = l->spins;
+            ProfScope ps_(pa->ctx, PK_INIT);
+            CUDA_TRY(launch_init_spins(l->spins, l->d.dim, (uint32_t)l->d.L, l->d.n_instances, l->d.n_replicas,
+                                       l->d.instance_base, l->d.seed, 1, s));
+        }
+        l->t = pl.t_start;
+        std::vector<double> z(2 * l->d.n_instances, 0.0);
+        for (uint32_t k = 0; k < l->d.n_instances; ++k) z[k] = (double)l->N * std::log(2.0);
+        CUDA_TRY(cudaMemcpyAsync(pl.lnZ, z.data(), z.size() * 8, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));  // z is a host temporary
+        PaLattice P = pa_params(pa, pl, 0);
+        ProfScope ps_(pa->ctx, PK_PA_RESET);
+        CUDA_TRY(launch_pa_reset(P, s));
+    }
+    pa->step = 0;
+    gbmc_status st = pa_sweep_launch(pa, 0);
+    if (st != GBMC_OK) return st;
+    return pa_record(pa, 0);
+}
+
+gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_lattices, const gbmc_pa_config* cfg,
+                      gbmc_pa** out) {
+    if (!ctx || !lattices || !cfg || !out) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (n_lattices == 0 || n_lattices > (uint32_t)kMaxJobs) return fail(GBMC_ERR_ARG, "1..%d lattices per run", kMaxJobs);
+    if (cfg->schedule != GBMC_SCHED_LINEAR && cfg->schedule != GBMC_SCHED_LIST)
+        return fail(GBMC_ERR_ARG, "schedule %d not supported by this build", cfg->schedule);
+    if (cfg->n_steps == 0) return fail(GBMC_ERR_ARG, "n_steps must be >= 1");
+    if (cfg->schedule == GBMC_SCHED_LIST && !cfg->betas) return fail(GBMC_ERR_ARG, "betas required for a list schedule");
+    const gbmc_lattice* l0 = lattices[0];
+    if (!l0) return fail(GBMC_ERR_ARG, "NULL lattice");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::vector<Tuning> tus;
+    for (uint32_t i = 0; i < n_lattices; ++i) {
+        const gbmc_lattice* l = lattices[i];
+        if (!l) return fail(GBMC_ERR_ARG, "NULL lattice");
+        if (l->run) return fail(GBMC_ERR_STATE, "lattice %u already in an annealing run", i);
+        if (l->d.dim != l0->d.dim || l->d.model != l0->d.model)
+            return fail(GBMC_ERR_ARG, "lattices of one run share dim and model");
+        for (uint32_t k = 0; k < i; ++k)
+            if (lattices[k] == l) return fail(GBMC_ERR_ARG, "lattice %u listed twice", i);
+        const Tuning tu = tune(l);
+        if (!tu.resident) return fail(GBMC_ERR_ARG, "lattice %u too large for shared-memory resident annealing", i);
+        if (i > 0 && tu.threads != tus[0].threads)
+            return fail(GBMC_ERR_ARG, "lattices of one run need the same CTA shape");
+        tus.push_back(tu);
+    }
+    gbmc_pa* pa = new (std::nothrow) gbmc_pa;
+    if (!pa) return fail(GBMC_ERR_OOM, "host allocation");
+    pa->ctx = ctx;
+    pa->cfg = *cfg;
+    pa->cfg.betas = nullptr;
+    pa->S = cfg->n_steps;
+    pa->lats.resize(n_lattices);
+    gbmc_status st = GBMC_OK;
+    uint32_t pop = 0;
+    for (uint32_t i = 0; i < n_lattices && st == GBMC_OK; ++i) {
+        PaLat& pl = pa->lats[i];
+        gbmc_lattice* l = lattices[i];
+        pl.lat = l;
+        pl.pop0 = pop;
+        pop += l->d.n_instances;
+        pl.t_start = l->t;
+        const uint32_t I = l->d.n_instances, R = l->d.n_replicas;
+        const uint64_t C = (uint64_t)I * R;
+        pl.nbins = (uint32_t)(l->d.dim * l->N / 2 + 1);
+        pl.e_lo = -(int32_t)(l->d.dim * l->N);
+        pl.nchunks = (R + kScanChunk - 1) / kScanChunk;
+        int lg = 0;
+        while ((1ull << lg) < R) ++lg;
+        pl.s_bits = 63 - lg;
+        // schedule
+        pl.betas.resize(pa->S + 1);
+        for (uint32_t k = 0; k <= pa->S; ++k)
+            pl.betas[k] = cfg->schedule == GBMC_SCHED_LIST ? cfg->betas[k]
+                                                           : (cfg->beta_f * (double)k) / (double)pa->S;
+        if (pl.betas[0] != 0.0) st = fail(GBMC_ERR_ARG, "beta_0 must be 0");
+        for (uint32_t k = 1; k <= pa->S && st == GBMC_OK; ++k) {
+            if (!(pl.betas[k] >= pl.betas[k - 1]) || !beta_ok(pl.betas[k], l->d.dim))
+                st = fail(GBMC_ERR_ARG, "schedule must be non-decreasing with 0 <= 4*dim*beta <= 700");
+        }
+        if (st != GBMC_OK) break;
+        void* p;
+        if ((st = dalloc(pa, &p, C * l->N)) != GBMC_OK) break;
+        pl.alt = (int8_t*)p;
+        if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
+        pl.E = (int32_t*)p;
+        if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
+        pl.M = (int32_t*)p;
+        if ((st = dalloc(pa, &p, (uint64_t)I * pl.nbins * 4)) != GBMC_OK) break;
+        pl.hist = (uint32_t*)p;
+        if ((st = dalloc(pa, &p, I * 4)) != GBMC_OK) break;
+        pl.emin = (int32_t*)p;
+        if ((st = dalloc(pa, &p, I * 4)) != GBMC_OK) break;
+        pl.emax = (int32_t*)p;
+        if ((st = dalloc(pa, &p, I * 32)) != GBMC_OK) break;
+        pl.sums = (unsigned long long*)p;
+        if ((st = dalloc(pa, &p, I * 16)) != GBMC_OK) break;
+        pl.lnZ = (double*)p;
+        if ((st = dalloc(pa, &p, C * 8)) != GBMC_OK) break;
+        pl.cloc = (unsigned long long*)p;
+        if ((st = dalloc(pa, &p, (uint64_t)I * pl.nchunks * 8)) != GBMC_OK) break;
+        pl.ctot = (unsigned long long*)p;
+        if ((st = dalloc(pa, &p, (uint64_t)I * (pl.nchunks + 1) * 8)) != GBMC_OK) break;
+        pl.cpre = (unsigned long long*)p;
+        if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
+        pl.counts = (uint32_t*)p;
+        if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
+        pl.sloc = (uint32_t*)p;
+        if ((st = dalloc(pa, &p, (uint64_t)I * pl.nchunks * 4)) != GBMC_OK) break;
+        pl.ntot = (uint32_t*)p;
+        if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
+        pl.parent = (uint32_t*)p;
+        cudaError_t ce = cudaMemsetAsync(pl.counts, 0, C * 4, ctx->stream);
+        if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "memset: %s", cudaGetErrorString(ce)); break; }
+        // fp64 weight tables of every step (Eq. (13)), host libm exp
+        const uint64_t tb = (uint64_t)pa->S * pl.nbins;
+        if ((st = dalloc(pa, &p, tb * 8)) != GBMC_OK) break;
+        pl.wexp = (double*)p;
+        if ((st = dalloc(pa, &p, tb * 8)) != GBMC_OK) break;
+        pl.wint = (unsigned long long*)p;
+        std::vector<double> we(tb);
+        std::vector<unsigned long long> wi(tb);
+        for (uint32_t k = 1; k <= pa->S; ++k) {
+            const double dbeta = pl.betas[k] - pl.betas[k - 1];
+            double* row = we.data() + (uint64_t)(k - 1) * pl.nbins;
+            unsigned long long* irow = wi.data() + (uint64_t)(k - 1) * pl.nbins;
+            for (uint32_t b = 0; b < pl.nbins; ++b) {
+                const double w = std::exp(-(dbeta * (double)(4ll * b)));
+                row[b] = w;
+                irow[b] = (unsigned long long)std::floor(std::ldexp(w, pl.s_bits));
+            }
+        }
+        ce = cudaMemcpy(pl.wexp, we.data(), tb * 8, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(pl.wint, wi.data(), tb * 8, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "table upload: %s", cudaGetErrorString(ce)); break; }
+    }
+    if (st == GBMC_OK) {
+        pa->P = pop;
+        void* p;
+        st = dalloc(pa, &p, (uint64_t)(pa->S + 1) * pa->P * sizeof(gbmc_pa_stats));
+        if (st == GBMC_OK) pa->stats = (gbmc_pa_stats*)p;
+    }
+    if (st != GBMC_OK) {
+        for (void* p : pa->allocs) cudaFree(p);
+        delete pa;
+        return st;
+    }
+    for (auto& pl : pa->lats) pl.lat->run = pa;
+    st = pa_begin(pa, cfg->init);
+    if (st != GBMC_OK) return st;
+    *out = pa;
+    return GBMC_OK;
+}
+
+gbmc_status pa_free(gbmc_pa* pa) {
+    if (!pa) return GBMC_OK;
+    cudaStreamSynchronize(pa->ctx->stream);
+    for (auto& pl : pa->lats) {
+        // leave the current configuration in the lattice's own buffer
+        gbmc_lattice* l = pl.lat;
+        if (l->cur != l->spins) {
+            cudaMemcpy(l->spins, l->cur, l->N * l->ncopies, cudaMemcpyDeviceToDevice);
+            l->cur = l->spins;
+        }
+        l->run = nullptr;
+    }
+    for (void* p : pa->allocs) cudaFree(p);
+    delete pa;
+    return GBMC_OK;
+}
+
+gbmc_status pa_reset(gbmc_ctx* ctx, gbmc_pa* pa, int32_t init, uint64_t seed) {
+    if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    pa->ctx = ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (seed != 0)
+        for (auto& pl : pa->lats) pl.lat->d.seed = seed;
+    return pa_begin(pa, init);
+}
+
+gbmc_status pa_populations(const gbmc_pa* pa, uint32_t* n) {
+    if (!pa || !n) return fail(GBMC_ERR_ARG, "NULL argument");
+    *n = pa->P;
+    return GBMC_OK;
+}
+
+static gbmc_status pa_enqueue_step(gbmc_pa* pa) {
+    const uint32_t i = pa->step + 1;
+    cudaStream_t s = pa->ctx->stream;
+    for (auto& pl : pa->lats) {
+        PaLattice P = pa_params(pa, pl, i);
+        {
+            ProfScope ps_(pa->ctx, PK_PA_WEIGHTS);
+            CUDA_TRY(launch_pa_weights(P, s));
+        }
+        {
+            ProfScope ps_(pa->ctx, PK_PA_REDUCE);
+            CUDA_TRY(launch_pa_reduce(P, pl.lnZ, 0, s));
+        }
+        {
+            ProfScope ps_(pa->ctx, PK_PA_DRAWS);
+            CUDA_TRY(launch_pa_draws(P, s));
+        }
+        {
+            ProfScope ps_(pa->ctx, PK_PA_PLACE);
+            CUDA_TRY(launch_pa_place(P, s));
+        }
+    }
+    gbmc_status st = pa_sweep_launch(pa, i);
+    if (st != GBMC_OK) return st;
+    st = pa_record(pa, i);
+    if (st != GBMC_OK) return st;
+    pa->step = i;
+    return GBMC_OK;
+}
+
+gbmc_status pa_step(gbmc_ctx* ctx, gbmc_pa* pa, const double* beta_next, gbmc_pa_stats* out_host) {
+    if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (pa->step >= pa->S) return fail(GBMC_ERR_STATE, "schedule finished after %u steps", pa->S);
+    if (beta_next) return fail(GBMC_ERR_ARG, "explicit beta_next needs an adaptive schedule");
+    pa->ctx = ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    gbmc_status st = pa_enqueue_step(pa);
+    if (st != GBMC_OK) return st;
+    if (out_host) {
+        CUDA_TRY(cudaMemcpyAsync(out_host, pa->stats + (uint64_t)pa->step * pa->P, pa->P * sizeof(gbmc_pa_stats),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return GBMC_OK;
+}
+
+gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32_t capacity, uint32_t* n_done) {
+    if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    pa->ctx = ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    while (pa->step < pa->S) {
+        gbmc_status st = pa_enqueue_step(pa);
+        if (st != GBMC_OK) return st;
+    }
+    if (stats_host) {
+        const uint32_t rows = capacity < pa->step + 1 ? capacity : pa->step + 1;
+        CUDA_TRY(cudaMemcpyAsync(stats_host, pa->stats, (uint64_t)rows * pa->P * sizeof(gbmc_pa_stats),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (n_done) *n_done = pa->step;
+    return GBMC_OK;
+}
+
+gbmc_status pa_parents_out(gbmc_ctx* ctx, const gbmc_pa* pa, uint32_t lattice, uint32_t* dst, size_t count) {
+    if (!ctx || !pa || !dst) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (lattice >= pa->lats.size()) return fail(GBMC_ERR_ARG, "lattice index out of range");
+    const PaLat& pl = pa->lats[lattice];
+    if (count != pl.lat->ncopies) return fail(GBMC_ERR_ARG, "count must be %llu", (unsigned long long)pl.lat->ncopies);
+    CUDA_TRY(cudaMemcpyAsync(dst, pl.parent, count * 4, cudaMemcpyDefault, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status pa_energies_out(gbmc_ctx* ctx, const gbmc_pa* pa, uint32_t lattice, int32_t* E_dst, int32_t* M_dst,
+                            size_t count) {
+    if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (lattice >= pa->lats.size()) return fail(GBMC_ERR_ARG, "lattice index out of range");
+    const PaLat& pl = pa->lats[lattice];
+    if (count != pl.lat->ncopies) return fail(GBMC_ERR_ARG, "count must be %llu", (unsigned long long)pl.lat->ncopies);
+    if (E_dst) CUDA_TRY(cudaMemcpyAsync(E_dst, pl.E, count * 4, cudaMemcpyDefault, ctx->stream));
+    if (M_dst) CUDA_TRY(cudaMemcpyAsync(M_dst, pl.M, count * 4, cudaMemcpyDefault, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+}  // extern "C"

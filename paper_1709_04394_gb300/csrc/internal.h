@@ -1,0 +1,100 @@
+// internal.h -- host/device shared structures of the library and the host-side
+// launchers of its kernels (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace gbmc {
+
+// Kernels enqueued by this library in this process (every <<<>>> adds one).
+void count_launch();
+
+constexpr int kMaxJobs = 8;
+
+// One lattice's share of a sweep launch (Sec. 3.1 checkerboard sweeps of all
+// copies of one lattice; with PA, the resampling gather of Sec. 5.4 on load).
+struct SweepJob {
+    const int8_t* src;        // configuration read: copy c from src + parent(c)*N (or c*N)
+    int8_t* dst;              // configuration written: copy c to dst + c*N (may be src if no parent)
+    const uint32_t* parent;   // [n_inst*R] source replica (within its instance) of each slot, or null
+    const uint8_t* jbits;     // +-J bonds: [n_inst][3][N], byte 1 where J = -1; null for J = 1
+    int32_t* E;               // [n_inst*R] energy after the last sweep, or null
+    int32_t* M;               // [n_inst*R] magnetisation after the last sweep, or null
+    int32_t* Eser;            // [nsweeps][n_inst*R] per-sweep energy, or null
+    int32_t* Mser;            // [nsweeps][n_inst*R] per-sweep magnetisation, or null
+    uint32_t* hist;           // [n_inst][nbins] energy histogram accumulated, or null (PA)
+    int32_t* emin;            // [n_inst] atomic min of E (PA), or null
+    int32_t* emax;            // [n_inst] atomic max of E (PA), or null
+    unsigned long long* sums; // [n_inst][4] sum E, E^2, |M|, M^2 (two's complement), or null
+    uint64_t seed;
+    uint32_t thr[3];          // thresholds T(4), T(8), T(12)
+    uint32_t L, N, R, n_inst, inst_base;
+    uint32_t t0, nsweeps;
+    int32_t e_lo;             // histogram bin b = (E - e_lo) >> 2
+    uint32_t nbins;
+    uint32_t rpc;             // replicas per CTA (CTAs never straddle instances)
+    uint32_t ctas_per_inst;
+};
+
+struct SweepLaunch {
+    SweepJob jobs[kMaxJobs];
+    uint32_t cta_begin[kMaxJobs + 1];  // job j owns CTAs [cta_begin[j], cta_begin[j+1])
+    int32_t njobs;
+    int32_t dim;
+    int32_t ea;
+    int32_t swar;                      // 1: every job has L % 8 == 0 (8-byte row chunks)
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_init_spins(int8_t* spins, int dim, uint32_t L, uint32_t n_inst, uint32_t R,
+                              uint32_t inst_base, uint64_t seed, int random_start, cudaStream_t s);
+cudaError_t launch_couplings(uint8_t* jbits, uint32_t L, uint32_t n_inst, uint32_t inst_base,
+                             uint64_t seed, cudaStream_t s);
+cudaError_t launch_jbits_to_int8(const uint8_t* jbits, int8_t* out, uint32_t N, uint32_t n_inst,
+                                 cudaStream_t s);
+cudaError_t launch_observables(const int8_t* spins, const uint8_t* jbits, int dim, uint32_t L,
+                               uint32_t n_inst, uint32_t R, int32_t* E, int32_t* M, cudaStream_t s);
+
+// Resident sweep: every copy fits in one CTA's shared memory.
+size_t resident_smem_bytes(const SweepLaunch& P);
+cudaError_t launch_sweep_resident(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads,
+                                  size_t smem, cudaStream_t s);
+// Global-memory half-sweep over one job (large lattices); colour 0 or 1.
+cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
+                                    cudaStream_t s);
+
+// ---- population annealing resampling (Sec. 5.4, Eq. (13)) ----
+struct PaLattice {
+    const int32_t* E;         // [n_inst*R] current energies
+    uint32_t* hist;           // [n_inst][nbins]
+    int32_t* emin;            // [n_inst]
+    int32_t* emax;            // [n_inst]
+    unsigned long long* sums; // [n_inst][4]
+    const double* wexp;       // [nbins] exp(-dbeta*4k) of this step
+    const unsigned long long* wint;  // [nbins] floor(2^s exp(-dbeta*4k))
+    unsigned long long* cloc; // [n_inst*R] inclusive weight sums within each chunk
+    unsigned long long* ctot; // [n_inst][nchunks] chunk totals
+    unsigned long long* cpre; // [n_inst][nchunks+1] exclusive chunk prefix (last = total)
+    uint32_t* counts;         // [n_inst*R] copies of each replica
+    uint32_t* sloc;           // [n_inst*R] exclusive count prefix within the chunk
+    uint32_t* ntot;           // [n_inst][nchunks] chunk count totals
+    uint32_t* parent;         // [n_inst*R] out: source replica of each slot
+    void* stats;              // gbmc_pa_stats [n_inst] record of this step (device)
+    double dbeta, beta, log_R, lnZ0;
+    uint64_t seed;
+    uint32_t R, n_inst, inst_base, nbins, nchunks, step;
+    int32_t e_lo;
+};
+
+constexpr uint32_t kScanChunk = 2048;  // replicas per resampling chunk (512 threads x 4)
+
+cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s);
+cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int first_step, cudaStream_t s);
+cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s);
+cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s);
+cudaError_t launch_pa_record(const PaLattice& P, const double* lnZ, double lnQ_unused, cudaStream_t s);
+cudaError_t launch_pa_reset(const PaLattice& P, cudaStream_t s);
+
+}  // namespace gbmc

@@ -1,0 +1,267 @@
+// pa.cu -- population-annealing resampling (Sec. 5.4, step 2; Eq. (13)).
+//
+// Per population (one instance of one lattice, R replicas), from the energies
+// left by the previous sweep launch and its histogram/min/max accumulators:
+//   k_pa_weights : integer weight W_j = floor(2^s exp(-dbeta (E_j - Emin))) from
+//                  the host-computed table; inclusive sums within 2048-replica
+//                  chunks, chunk totals.
+//   k_pa_reduce  : ln Q_i = -dbeta Emin + ln sum_E h(E) exp(-dbeta (E-Emin)) - ln R
+//                  over the histogram (fixed-order fp64 tree), ln Z += ln Q;
+//                  exclusive scan of the chunk totals -> the cumulative weights
+//                  C_j = cpre[chunk] + cloc[j] in replica order; reset of the
+//                  accumulators for the next sweep.
+//   k_pa_draws   : R multinomial draws x_k = floor(U64_k C_R / 2^64) (Philox,
+//                  purpose 2), parent = least j with C_j > x_k (two-level
+//                  bisection), counts[parent] += 1 (integer atomics: the result
+//                  does not depend on their order).
+//   k_pa_count_scan, k_pa_place : exclusive scan of the counts; parent j fills
+//                  slots [S_j, S_j + n_j): children contiguous, parents in order.
+// The sweep kernel then gathers slot c from parent[c] while loading.
+#include <climits>
+
+#include "../../include/gbmc.h"
+#include "device.cuh"
+#include "internal.h"
+
+namespace gbmc {
+
+constexpr int kScanThreads = 512;
+constexpr int kPerThread = kScanChunk / kScanThreads;  // 4
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_weights(const __grid_constant__ PaLattice P) {
+    __shared__ unsigned long long sh[32];
+    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+    const uint64_t base = (uint64_t)inst * P.R;
+    const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
+    const int32_t emin = P.emin[inst];
+    unsigned long long w[kPerThread];
+    unsigned long long run = 0;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const uint32_t j = j0 + i;
+        unsigned long long v = 0;
+        if (j < P.R) v = P.wint[(uint32_t)(P.E[base + j] - emin) >> 2];
+        run += v;
+        w[i] = run;
+    }
+    unsigned long long total;
+    const unsigned long long incl = block_inclusive_scan<unsigned long long>(run, sh, &total);
+    const unsigned long long excl = incl - run;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const uint32_t j = j0 + i;
+        if (j < P.R) P.cloc[base + j] = excl + w[i];
+    }
+    if (threadIdx.x == 0) P.ctot[(uint64_t)inst * P.nchunks + chunk] = total;
+}
+
+cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s) {
+    dim3 grid(P.nchunks, P.n_inst);
+    k_pa_weights<<<grid, kScanThreads, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// One CTA per population.
+__global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLattice P, double* lnZ,
+                                                    double* lnQ_out) {
+    __shared__ double sd[32];
+    __shared__ unsigned long long su[32];
+    const uint32_t inst = blockIdx.x;
+    const int32_t emin = P.emin[inst], emax = P.emax[inst];
+    const uint32_t bmin = (uint32_t)(emin - P.e_lo) >> 2, bmax = (uint32_t)(emax - P.e_lo) >> 2;
+    uint32_t* h = P.hist + (uint64_t)inst * P.nbins;
+    double acc = 0.0;
+    for (uint32_t b = bmin + threadIdx.x; b <= bmax; b += blockDim.x) {
+        const uint32_t hb = h[b];
+        if (hb) acc += (double)hb * P.wexp[b - bmin];
+        h[b] = 0u;
+    }
+    // fixed-order tree: warp butterfly, then over warps
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0) sd[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double v = lane < nwarps ? sd[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) {
+            const double lnQ = -P.dbeta * (double)emin + log(v) - P.log_R;
+            lnQ_out[inst] = lnQ;
+            lnZ[inst] += lnQ;
+        }
+    }
+    // exclusive scan of the chunk totals (nchunks may exceed blockDim)
+    const unsigned long long* ct = P.ctot + (uint64_t)inst * P.nchunks;
+    unsigned long long* cp = P.cpre + (uint64_t)inst * (P.nchunks + 1);
+    unsigned long long carry = 0;
+    for (uint32_t c0 = 0; c0 < P.nchunks; c0 += blockDim.x) {
+        const uint32_t c = c0 + threadIdx.x;
+        const unsigned long long v = c < P.nchunks ? ct[c] : 0ull;
+        unsigned long long tot;
+        const unsigned long long incl = block_inclusive_scan<unsigned long long>(v, su, &tot);
+        if (c < P.nchunks) cp[c] = carry + incl - v;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        cp[P.nchunks] = carry;
+        P.emin[inst] = INT_MAX;
+        P.emax[inst] = INT_MIN;
+        unsigned long long* sums = P.sums + (uint64_t)inst * 4;
+        sums[0] = sums[1] = sums[2] = sums[3] = 0ull;
+    }
+}
+
+cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int /*first_step*/, cudaStream_t s) {
+    // lnQ of the step is kept next to lnZ: lnZ[n_inst .. 2 n_inst)
+    k_pa_reduce<<<P.n_inst, 1024, 0, s>>>(P, lnZ, lnZ + P.n_inst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_pa_draws(const __grid_constant__ PaLattice P) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t total_draws = (uint64_t)P.n_inst * P.R;
+    if (g >= total_draws) return;
+    const uint32_t inst = (uint32_t)(g / P.R), k = (uint32_t)(g - (uint64_t)inst * P.R);
+    const uint4 w = philox4x32_10(
+        make_uint4(k >> 1, P.step, 0u, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
+        (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    const unsigned long long U = (k & 1u) ? (((unsigned long long)w.w << 32) | w.z)
+                                          : (((unsigned long long)w.y << 32) | w.x);
+    const unsigned long long* cp = P.cpre + (uint64_t)inst * (P.nchunks + 1);
+    const unsigned long long x = __umul64hi(U, cp[P.nchunks]);
+    // least chunk c with cp[c+1] > x
+    uint32_t lo = 0, hi = P.nchunks - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cp[mid + 1] > x) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint32_t c = lo;
+    const unsigned long long xr = x - cp[c];  // cumulative within the chunk: least j with cloc[j] > xr
+    const uint64_t base = (uint64_t)inst * P.R;
+    uint32_t a = c * kScanChunk, b = min(P.R, (c + 1) * kScanChunk) - 1;
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (P.cloc[base + mid] > xr) b = mid;
+        else a = mid + 1;
+    }
+    atomicAdd(&P.counts[base + a], 1u);
+}
+
+cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s) {
+    const uint64_t total = (uint64_t)P.n_inst * P.R;
+    k_pa_draws<<<(uint32_t)((total + 255) / 256), 256, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_count_scan(const __grid_constant__ PaLattice P) {
+    __shared__ uint32_t sh[32];
+    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+    const uint64_t base = (uint64_t)inst * P.R;
+    const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
+    uint32_t v[kPerThread];
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const uint32_t j = j0 + i;
+        v[i] = run;  // exclusive within the thread
+        if (j < P.R) run += P.counts[base + j];
+    }
+    uint32_t total;
+    const uint32_t incl = block_inclusive_scan<uint32_t>(run, sh, &total);
+    const uint32_t excl = incl - run;
+#pragma unroll
+    for (int i = 0; i < kPerThread; ++i) {
+        const uint32_t j = j0 + i;
+        if (j < P.R) P.sloc[base + j] = excl + v[i];
+    }
+    if (threadIdx.x == 0) P.ntot[(uint64_t)inst * P.nchunks + chunk] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_place(const __grid_constant__ PaLattice P) {
+    __shared__ uint32_t prefix;
+    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+    const uint64_t base = (uint64_t)inst * P.R;
+    if (threadIdx.x < 32) {
+        uint32_t acc = 0;
+        for (uint32_t c = threadIdx.x; c < chunk; c += 32) acc += P.ntot[(uint64_t)inst * P.nchunks + c];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) prefix = acc;
+    }
+    __syncthreads();
+    const uint32_t pre = prefix;
+    for (uint32_t i = threadIdx.x; i < kScanChunk; i += blockDim.x) {
+        const uint32_t j = chunk * kScanChunk + i;
+        if (j >= P.R) break;
+        const uint32_t n = P.counts[base + j];
+        if (n) {
+            const uint32_t S = pre + P.sloc[base + j];
+            for (uint32_t m = 0; m < n; ++m) P.parent[base + S + m] = j;
+            P.counts[base + j] = 0u;
+        }
+    }
+}
+
+cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s) {
+    dim3 grid(P.nchunks, P.n_inst);
+    k_pa_count_scan<<<grid, kScanThreads, 0, s>>>(P);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pa_place<<<grid, kScanThreads, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Record of one step for every population of a lattice, after its sweeps.
+__global__ void k_pa_record(const __grid_constant__ PaLattice P, const double* lnZ) {
+    const uint32_t inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= P.n_inst) return;
+    gbmc_pa_stats* st = reinterpret_cast<gbmc_pa_stats*>(P.stats) + inst;
+    const unsigned long long* su = P.sums + (uint64_t)inst * 4;
+    st->beta = P.beta;
+    st->dbeta = P.dbeta;
+    st->lnQ = P.step == 0 ? 0.0 : lnZ[P.n_inst + inst];
+    st->lnZ = lnZ[inst];
+    st->sumE = (int64_t)su[0];
+    st->sumE2 = (int64_t)su[1];
+    st->sumAbsM = (int64_t)su[2];
+    st->sumM2 = (int64_t)su[3];
+    st->Emin = P.emin[inst];
+    st->Emax = P.emax[inst];
+    st->step = P.step;
+    st->n_replicas = P.R;
+    st->overlap = 0.0;
+    st->proposal_kind = 0;
+    st->pad = 0;
+}
+
+cudaError_t launch_pa_record(const PaLattice& P, const double* lnZ, double, cudaStream_t s) {
+    k_pa_record<<<(P.n_inst + 127) / 128, 128, 0, s>>>(P, lnZ);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Reset of the accumulators before the first measurement (step 0).
+__global__ void k_pa_reset(const __grid_constant__ PaLattice P) {
+    const uint32_t inst = blockIdx.x;
+    uint32_t* h = P.hist + (uint64_t)inst * P.nbins;
+    for (uint32_t b = threadIdx.x; b < P.nbins; b += blockDim.x) h[b] = 0u;
+    if (threadIdx.x == 0) {
+        P.emin[inst] = INT_MAX;
+        P.emax[inst] = INT_MIN;
+        unsigned long long* sums = P.sums + (uint64_t)inst * 4;
+        sums[0] = sums[1] = sums[2] = sums[3] = 0ull;
+    }
+}
+
+cudaError_t launch_pa_reset(const PaLattice& P, cudaStream_t s) {
+    k_pa_reset<<<P.n_inst, 256, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

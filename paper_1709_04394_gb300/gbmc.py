@@ -1,0 +1,298 @@
+"""ctypes binding of libgbmc.so, the C ABI declared in include/gbmc.h.
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name. Device buffers are torch CUDA tensors (their data_ptr is passed);
+host buffers are numpy arrays. Streams are raw cudaStream_t handles (an int,
+e.g. ``torch.cuda.current_stream().cuda_stream``) or None for the default
+stream. A missing or unloadable library raises immediately: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbmc.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "gbmc.h")
+
+GBMC_OK, GBMC_ERR_ARG, GBMC_ERR_OOM, GBMC_ERR_CUDA, GBMC_ERR_TIMEOUT, GBMC_ERR_STATE = 0, -1, -2, -3, -4, -5
+GBMC_ISING_FM, GBMC_EA_PMJ = 0, 1
+GBMC_INT8, GBMC_BITPACK = 0, 1
+GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
+GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
+
+
+class GbmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("gbmc status %d: %s" % (status, msg))
+        self.status = status
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("L", C.c_int32), ("model", C.c_int32), ("layout", C.c_int32),
+                ("start", C.c_int32), ("n_instances", C.c_uint32), ("n_replicas", C.c_uint32),
+                ("instance_base", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class LatticeInfo(C.Structure):
+    _fields_ = [("n_sites", C.c_int64), ("n_copies", C.c_int64), ("spin_bytes", C.c_int64),
+                ("sweep_counter", C.c_uint32), ("pad", C.c_uint32), ("spins_dev", C.c_void_p)]
+
+
+class PaConfig(C.Structure):
+    _fields_ = [("theta", C.c_uint32), ("n_steps", C.c_uint32), ("schedule", C.c_int32), ("init", C.c_int32),
+                ("beta_f", C.c_double), ("betas", C.c_void_p), ("target_overlap", C.c_double),
+                ("dbeta_max", C.c_double), ("mlp_params", C.c_void_p), ("overlap_lo", C.c_double),
+                ("overlap_hi", C.c_double)]
+
+
+class PaStats(C.Structure):
+    _fields_ = [("beta", C.c_double), ("dbeta", C.c_double), ("lnQ", C.c_double), ("lnZ", C.c_double),
+                ("sumE", C.c_int64), ("sumE2", C.c_int64), ("sumAbsM", C.c_int64), ("sumM2", C.c_int64),
+                ("Emin", C.c_int32), ("Emax", C.c_int32), ("step", C.c_uint32), ("n_replicas", C.c_uint32),
+                ("overlap", C.c_double), ("proposal_kind", C.c_int32), ("pad", C.c_int32)]
+
+
+PA_STATS_DTYPE = np.dtype([("beta", "<f8"), ("dbeta", "<f8"), ("lnQ", "<f8"), ("lnZ", "<f8"),
+                           ("sumE", "<i8"), ("sumE2", "<i8"), ("sumAbsM", "<i8"), ("sumM2", "<i8"),
+                           ("Emin", "<i4"), ("Emax", "<i4"), ("step", "<u4"), ("n_replicas", "<u4"),
+                           ("overlap", "<f8"), ("proposal_kind", "<i4"), ("pad", "<i4")])
+assert PA_STATS_DTYPE.itemsize == C.sizeof(PaStats)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libgbmc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgbmc.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        lib = C.CDLL(LIB_PATH)
+        p, st = C.c_void_p, C.c_int
+        sig = {
+            "gbmc_version": ([], C.c_int),
+            "gbmc_last_error": ([], C.c_char_p),
+            "gbmc_create": ([C.POINTER(C.c_void_p), C.c_int, p], st),
+            "gbmc_set_stream": ([p, p], st),
+            "gbmc_sync": ([p], st),
+            "gbmc_destroy": ([p], st),
+            "gbmc_profile": ([p, C.c_int32], st),
+            "gbmc_profile_read": ([p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
+            "gbmc_kernel_launches": ([], C.c_uint64),
+            "lattice_init": ([p, C.POINTER(LatticeDesc), p, C.c_size_t, C.POINTER(C.c_void_p)], st),
+            "lattice_free": ([p], st),
+            "lattice_info": ([p, C.POINTER(LatticeInfo)], st),
+            "lattice_set_sweep_counter": ([p, C.c_uint32], st),
+            "lattice_copy_out": ([p, p, p, C.c_size_t], st),
+            "lattice_copy_in": ([p, p, p, C.c_size_t], st),
+            "lattice_couplings_out": ([p, p, p, C.c_size_t], st),
+            "metropolis_sweeps": ([p, p, C.c_double, C.c_uint32, p, p], st),
+            "observables": ([p, p, p, p], st),
+            "pa_create": ([p, C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(PaConfig), C.POINTER(C.c_void_p)], st),
+            "pa_free": ([p], st),
+            "pa_reset": ([p, p, C.c_int32, C.c_uint64], st),
+            "pa_populations": ([p, C.POINTER(C.c_uint32)], st),
+            "pa_step": ([p, p, p, p], st),
+            "pa_run": ([p, p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
+            "pa_parents_out": ([p, p, C.c_uint32, p, C.c_size_t], st),
+            "pa_energies_out": ([p, p, C.c_uint32, p, p, C.c_size_t], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != GBMC_OK:
+        raise GbmcError(status, load().gbmc_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _nbytes(x):
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    return x.numel() * x.element_size()
+
+
+def gbmc_version() -> int:
+    return load().gbmc_version()
+
+
+def gbmc_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    _check(load().gbmc_create(C.byref(h), device, stream))
+    return h
+
+
+def gbmc_set_stream(ctx, stream):
+    _check(load().gbmc_set_stream(ctx, stream))
+
+
+def gbmc_sync(ctx):
+    _check(load().gbmc_sync(ctx))
+
+
+def gbmc_destroy(ctx):
+    _check(load().gbmc_destroy(ctx))
+
+
+def gbmc_profile(ctx, enable=True):
+    _check(load().gbmc_profile(ctx, int(bool(enable))))
+
+
+def gbmc_profile_read(ctx) -> dict:
+    """{kernel name: (launches, total_ms)} recorded since gbmc_profile(ctx, True)."""
+    arr = (KernelTime * 32)()
+    n = C.c_uint32()
+    _check(load().gbmc_profile_read(ctx, C.cast(arr, C.c_void_p), 32, C.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def gbmc_kernel_launches() -> int:
+    return int(load().gbmc_kernel_launches())
+
+
+def lattice_init(ctx, dim, L, model=GBMC_ISING_FM, start=GBMC_START_RANDOM, n_instances=1, n_replicas=1,
+                 seed=1, instance_base=0, layout=GBMC_INT8, spins=None):
+    d = LatticeDesc(dim, L, model, layout, start, n_instances, n_replicas, instance_base, seed)
+    h = C.c_void_p()
+    _check(load().lattice_init(ctx, C.byref(d), _ptr(spins), 0 if spins is None else _nbytes(spins), C.byref(h)))
+    return h
+
+
+def lattice_free(lat):
+    _check(load().lattice_free(lat))
+
+
+def lattice_info(lat) -> LatticeInfo:
+    info = LatticeInfo()
+    _check(load().lattice_info(lat, C.byref(info)))
+    return info
+
+
+def lattice_set_sweep_counter(lat, t: int):
+    _check(load().lattice_set_sweep_counter(lat, t))
+
+
+def lattice_copy_out(ctx, lat, dst):
+    _check(load().lattice_copy_out(ctx, lat, _ptr(dst), _nbytes(dst)))
+    return dst
+
+
+def lattice_copy_in(ctx, lat, src):
+    _check(load().lattice_copy_in(ctx, lat, _ptr(src), _nbytes(src)))
+
+
+def lattice_couplings_out(ctx, lat, dst):
+    _check(load().lattice_couplings_out(ctx, lat, _ptr(dst), _nbytes(dst)))
+    return dst
+
+
+def metropolis_sweeps(ctx, lat, beta: float, n_sweeps: int, E_series=None, M_series=None):
+    _check(load().metropolis_sweeps(ctx, lat, float(beta), n_sweeps, _ptr(E_series), _ptr(M_series)))
+
+
+def observables(ctx, lat, E=None, M=None):
+    _check(load().observables(ctx, lat, _ptr(E), _ptr(M)))
+
+
+def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=1.0, betas=None, init=True,
+              target_overlap=0.85, dbeta_max=0.05, mlp_params=None, overlap_lo=0.83, overlap_hi=0.90):
+    arr = (C.c_void_p * len(lattices))(*[l.value if isinstance(l, C.c_void_p) else l for l in lattices])
+    keep = []
+    bptr = None
+    if betas is not None:
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        keep.append(b)
+        bptr = b.ctypes.data
+    mptr = None
+    if mlp_params is not None:
+        m = np.ascontiguousarray(mlp_params, dtype=np.float32)
+        keep.append(m)
+        mptr = m.ctypes.data
+    cfg = PaConfig(theta, n_steps, schedule, int(bool(init)), beta_f, bptr, target_overlap, dbeta_max, mptr,
+                   overlap_lo, overlap_hi)
+    h = C.c_void_p()
+    _check(load().pa_create(ctx, arr, len(lattices), C.byref(cfg), C.byref(h)))
+    return h
+
+
+def pa_free(pa):
+    _check(load().pa_free(pa))
+
+
+def pa_reset(ctx, pa, init=True, seed=0):
+    _check(load().pa_reset(ctx, pa, int(bool(init)), seed))
+
+
+def pa_populations(pa) -> int:
+    n = C.c_uint32()
+    _check(load().pa_populations(pa, C.byref(n)))
+    return n.value
+
+
+def pa_step(ctx, pa, beta_next=None, want_stats=True):
+    out = None
+    if want_stats:
+        out = np.zeros(pa_populations(pa), dtype=PA_STATS_DTYPE)
+    bn = None
+    if beta_next is not None:
+        bn = np.ascontiguousarray(beta_next, dtype=np.float64)
+    _check(load().pa_step(ctx, pa, _ptr(bn), _ptr(out)))
+    return out
+
+
+def pa_run(ctx, pa, capacity=None):
+    P = pa_populations(pa)
+    out = None
+    cap = 0
+    if capacity is not None:
+        cap = capacity
+        out = np.zeros((capacity, P), dtype=PA_STATS_DTYPE)
+    n = C.c_uint32()
+    _check(load().pa_run(ctx, pa, _ptr(out), cap, C.byref(n)))
+    return (out[: n.value + 1] if out is not None else None), n.value
+
+
+def pa_parents_out(ctx, pa, lattice, dst):
+    _check(load().pa_parents_out(ctx, pa, lattice, _ptr(dst), dst.size if isinstance(dst, np.ndarray) else dst.numel()))
+    return dst
+
+
+def pa_energies_out(ctx, pa, lattice, E_dst=None, M_dst=None):
+    ref = E_dst if E_dst is not None else M_dst
+    n = ref.size if isinstance(ref, np.ndarray) else ref.numel()
+    _check(load().pa_energies_out(ctx, pa, lattice, _ptr(E_dst), _ptr(M_dst), n))
+
+
+def gbmc_last_error() -> str:
+    return load().gbmc_last_error().decode(errors="replace")
