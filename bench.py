@@ -164,6 +164,9 @@ def run_gpu(args, w, ws, rank, local):
         R = w["R"]
         spins = torch.empty(R * N, dtype=torch.int8, device="cuda")
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=R, seed=seed0, instance_base=rank, spins=spins)
+        tuned = gbmc.gbmc_autotune(ctx, lat, 0.5 * w["beta_f"], w["theta"])
+        result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
+                            "row_walk": tuned.row_walk, "candidates": tuned.n_candidates}
         pa = gbmc.pa_create(ctx, [lat], w["theta"], w["S"], beta_f=w["beta_f"], init=True)
 
         def step(k):
@@ -348,6 +351,7 @@ def main():
                      "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,
                      "kernel_share": t_l / total_ms if total_ms else None},
         "kernels": {k: {"launches": n, "total_ms": t} for k, (n, t) in prof.items()},
+        "autotuned_shape": res.get("tuning"),
         "gpu_launches": res["launches"],
         "clocks": clk,
     }

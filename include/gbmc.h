@@ -149,6 +149,31 @@ gbmc_status metropolis_sweeps(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uin
  * M = sum_i s_i of every copy, into device int32 arrays [n_copies]. */
 gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, int32_t *M_dev);
 
+/* Launch-shape autotuner for the shared-memory sweep kernel (lattices whose
+ * copy fits in one CTA's shared memory). Candidate shapes -- threads per copy
+ * (powers of two), copies per CTA, row-wise or flat walk over the words of a
+ * colour plane -- are timed with CUDA events on a scratch copy of up to 32768
+ * replicas of instance 0 (n_sweeps sweeps at beta, the lattice itself is left
+ * unchanged), and the fastest is recorded for the lattice class (dim, model,
+ * L) for the rest of the process. Every shape gives bit-identical results:
+ * the random words depend only on (seed, sweep, replica, site). Synchronises.
+ * out->resident = 0 when the lattice uses the global-memory kernel. */
+typedef struct {
+    int32_t resident;
+    uint32_t threads_per_copy;
+    uint32_t copies_per_cta;
+    int32_t row_walk;
+    double ms_per_sweep;      /* best time of one sweep of the timed replicas */
+    uint32_t n_candidates;
+    uint32_t pad;
+} gbmc_tuning;
+gbmc_status gbmc_autotune(gbmc_ctx *ctx, const gbmc_lattice *lat, double beta, uint32_t n_sweeps,
+                          gbmc_tuning *out);
+/* Force (shape != NULL) or clear (NULL) the shape of a lattice class; used by
+ * tests to check that every shape gives the same spins. threads_per_copy: a
+ * power of two <= 256; copies_per_cta in 1..64 with product <= 256. */
+gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tuning *shape);
+
 /* ------------------------------------------------------------------------ */
 /* Population annealing (Sec. 5.4): every (lattice, instance) pair is one     */
 /* population of n_replicas replicas annealed from beta_0 = 0.               */

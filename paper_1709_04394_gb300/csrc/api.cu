@@ -6,6 +6,8 @@
 
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -118,6 +120,7 @@ struct gbmc_lattice {
     bool owns_spins;
     int8_t* cur;       // buffer holding the current configuration
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
+    uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
     uint32_t t;        // sweep counter
     gbmc_pa* run;      // annealing run using this lattice
 };
@@ -186,33 +189,81 @@ struct Tuning {
     bool resident;
     uint32_t tpr, rpc, threads;
     size_t smem;
+    bool rowwise;  // allow the division-free row walk (needs tpr % (L/8) == 0)
 };
 
-// Launch shape of the resident sweep for one lattice: threads per copy `tpr`
-// (a power of two covering the copy's units, at most 256), copies per CTA rpc.
-Tuning tune(const gbmc_lattice* l) {
+// Launch shapes chosen by gbmc_autotune (or set with gbmc_set_tuning), per
+// lattice class (dim, model, L); every shape gives bit-identical results
+// because the random numbers depend only on (seed, sweep, replica, site).
+struct ShapeKey {
+    int dim, model, L;
+    bool operator<(const ShapeKey& o) const {
+        return dim != o.dim ? dim < o.dim : (model != o.model ? model < o.model : L < o.L);
+    }
+};
+struct Shape {
+    uint32_t tpr, copies_per_cta;
+    bool rowwise;
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, Shape> g_shapes;
+
+size_t bond_bytes(const gbmc_lattice* l) {
+    if (l->d.model != GBMC_EA_PMJ) return 0;
+    return (l->d.L % 8 == 0 ? 6 : 3) * l->N;
+}
+
+uint64_t units_per_copy(const gbmc_lattice* l) {
+    return (l->d.L % 8 == 0) ? l->N / 8 : ((l->N / 2) + 3) / 4;
+}
+
+// Shape for (tpr, copies per CTA): clamp to the replica count and shared memory.
+Tuning make_tuning(const gbmc_lattice* l, uint32_t tpr, uint32_t rpc, bool rowwise) {
     Tuning t{};
-    const uint64_t N = l->N;
-    const bool ea = l->d.model == GBMC_EA_PMJ;
-    const uint64_t stride = (N + 15) & ~15ull;
-    const uint64_t units = (l->d.L % 8 == 0) ? N / 8 : ((N / 2) + 3) / 4;
-    const size_t one = stride + (ea ? 3 * N : 0);
-    if (one > kSmemLimit || N > (1ull << 31)) {
+    const uint64_t stride = (l->N + 15) & ~15ull;
+    const size_t bonds = bond_bytes(l);
+    if (stride + bonds > kSmemLimit || l->N > (1ull << 31)) {
         t.resident = false;
         return t;
     }
-    uint32_t tpr = 8;
-    while (tpr < units && tpr < 256) tpr <<= 1;
-    uint32_t rpc = 256 / tpr;
     if (rpc > l->d.n_replicas) rpc = l->d.n_replicas;
     if (rpc < 1) rpc = 1;
-    while (rpc > 1 && rpc * stride + (ea ? 3 * N : 0) > kSmemLimit) --rpc;
+    while (rpc > 1 && rpc * stride + bonds > kSmemLimit) --rpc;
     t.resident = true;
     t.tpr = tpr;
     t.rpc = rpc;
     t.threads = tpr * rpc;
     if (t.threads < 32) t.threads = 32, t.tpr = 32 / rpc;
-    t.smem = rpc * stride + (ea ? 3 * N : 0);
+    t.smem = rpc * stride + bonds;
+    t.rowwise = rowwise;
+    return t;
+}
+
+// Default shape: threads per copy = the power of two covering the copy's
+// units (at most 256), copies per CTA filling 256 threads; or the tuned one.
+Tuning tune(const gbmc_lattice* l, bool use_table = true) {
+    if (use_table) {
+        std::lock_guard<std::mutex> g(g_shape_mu);
+        auto it = g_shapes.find(ShapeKey{l->d.dim, l->d.model, l->d.L});
+        if (it != g_shapes.end()) return make_tuning(l, it->second.tpr, it->second.copies_per_cta, it->second.rowwise);
+    }
+    const uint64_t units = units_per_copy(l);
+    uint32_t tpr = 8;
+    while (tpr < units && tpr < 256) tpr <<= 1;
+    return make_tuning(l, tpr, 256 / tpr, true);
+}
+
+// Shapes for lattices launched together: they must share the CTA size, so
+// tuned shapes are used only if they agree; otherwise the defaults.
+std::vector<Tuning> tune_batch(const std::vector<const gbmc_lattice*>& ls) {
+    std::vector<Tuning> t;
+    for (auto* l : ls) t.push_back(tune(l));
+    for (auto& x : t)
+        if (x.threads != t[0].threads) {
+            t.clear();
+            for (auto* l : ls) t.push_back(tune(l, false));
+            break;
+        }
     return t;
 }
 
@@ -222,6 +273,7 @@ SweepJob base_job(const gbmc_lattice* l, const Tuning& tu) {
     J.src = l->cur;
     J.dst = l->cur;
     J.jbits = l->jbits;
+    J.jsplit = l->jsplit;
     J.seed = l->d.seed;
     J.L = (uint32_t)l->d.L;
     J.N = (uint32_t)l->N;
@@ -244,6 +296,11 @@ gbmc_status launch_jobs(gbmc_ctx* ctx, SweepLaunch& P, const std::vector<Tuning>
         if (tu[j].threads > threads) threads = tu[j].threads;
     }
     P.cta_begin[P.njobs] = total;
+    P.rowwise = 1;
+    for (int j = 0; j < P.njobs; ++j) {
+        const uint32_t W = P.jobs[j].L / 8, tpr = threads / P.jobs[j].rpc;
+        if (W == 0 || tpr % W != 0 || !tu[j].rowwise) P.rowwise = 0;
+    }
     // every job must use the same thread count: copies per CTA scale with it
     for (int j = 0; j < P.njobs; ++j)
         if (tu[j].threads != threads)
@@ -406,6 +463,16 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
         }
         ProfScope ps_(ctx, PK_COUPLINGS);
         CUDA_TRY(launch_couplings(l->jbits, (uint32_t)d->L, d->n_instances, d->instance_base, d->seed, ctx->stream));
+        if (d->L % 8 == 0) {
+            e = cudaMalloc(&l->jsplit, 6 * N * d->n_instances);
+            if (e != cudaSuccess) {
+                cudaFree(l->jbits);
+                if (l->owns_spins) cudaFree(l->spins);
+                delete l;
+                return fail(GBMC_ERR_OOM, "cudaMalloc(split couplings): %s", cudaGetErrorString(e));
+            }
+            CUDA_TRY(launch_split_bonds(l->jbits, l->jsplit, (uint32_t)d->L, d->n_instances, ctx->stream));
+        }
     }
     {
         ProfScope ps_(ctx, PK_INIT);
@@ -421,6 +488,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->run) return fail(GBMC_ERR_STATE, "lattice still used by an annealing run");
     if (l->owns_spins) cudaFree(l->spins);
     if (l->jbits) cudaFree(l->jbits);
+    if (l->jsplit) cudaFree(l->jsplit);
     delete l;
     return GBMC_OK;
 }
@@ -570,15 +638,17 @@ static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
 static gbmc_status pa_sweep_launch(gbmc_pa* pa, uint32_t step) {
     SweepLaunch P;
     std::memset(&P, 0, sizeof(P));
-    std::vector<Tuning> tus;
+    std::vector<const gbmc_lattice*> ls;
+    for (auto& pl : pa->lats) ls.push_back(pl.lat);
+    const std::vector<Tuning> tus = tune_batch(ls);
     const gbmc_lattice* l0 = pa->lats[0].lat;
     P.dim = l0->d.dim;
     P.ea = l0->d.model == GBMC_EA_PMJ;
     P.swar = 1;
-    for (auto& pl : pa->lats) {
+    for (size_t li = 0; li < pa->lats.size(); ++li) {
+        auto& pl = pa->lats[li];
         gbmc_lattice* l = pl.lat;
-        const Tuning tu = tune(l);
-        tus.push_back(tu);
+        const Tuning& tu = tus[li];
         SweepJob J = base_job(l, tu);
         if (l->d.L % 8) P.swar = 0;
         thresholds(pl.betas[step], J.thr);
@@ -659,7 +729,7 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     const gbmc_lattice* l0 = lattices[0];
     if (!l0) return fail(GBMC_ERR_ARG, "NULL lattice");
     CUDA_TRY(cudaSetDevice(ctx->device));
-    std::vector<Tuning> tus;
+    std::vector<const gbmc_lattice*> ls;
     for (uint32_t i = 0; i < n_lattices; ++i) {
         const gbmc_lattice* l = lattices[i];
         if (!l) return fail(GBMC_ERR_ARG, "NULL lattice");
@@ -668,11 +738,16 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
             return fail(GBMC_ERR_ARG, "lattices of one run share dim and model");
         for (uint32_t k = 0; k < i; ++k)
             if (lattices[k] == l) return fail(GBMC_ERR_ARG, "lattice %u listed twice", i);
-        const Tuning tu = tune(l);
-        if (!tu.resident) return fail(GBMC_ERR_ARG, "lattice %u too large for shared-memory resident annealing", i);
-        if (i > 0 && tu.threads != tus[0].threads)
-            return fail(GBMC_ERR_ARG, "lattices of one run need the same CTA shape");
-        tus.push_back(tu);
+        ls.push_back(l);
+    }
+    {
+        const std::vector<Tuning> tus = tune_batch(ls);
+        for (uint32_t i = 0; i < n_lattices; ++i) {
+            if (!tus[i].resident)
+                return fail(GBMC_ERR_ARG, "lattice %u too large for shared-memory resident annealing", i);
+            if (tus[i].threads != tus[0].threads)
+                return fail(GBMC_ERR_ARG, "lattices of one run need the same CTA size");
+        }
     }
     gbmc_pa* pa = new (std::nothrow) gbmc_pa;
     if (!pa) return fail(GBMC_ERR_OOM, "host allocation");
@@ -897,6 +972,103 @@ gbmc_status pa_energies_out(gbmc_ctx* ctx, const gbmc_pa* pa, uint32_t lattice, 
     if (E_dst) CUDA_TRY(cudaMemcpyAsync(E_dst, pl.E, count * 4, cudaMemcpyDefault, ctx->stream));
     if (M_dst) CUDA_TRY(cudaMemcpyAsync(M_dst, pl.M, count * 4, cudaMemcpyDefault, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tuning* shape) {
+    std::lock_guard<std::mutex> g(g_shape_mu);
+    const ShapeKey k{dim, model, L};
+    if (!shape) {
+        g_shapes.erase(k);
+        return GBMC_OK;
+    }
+    const uint32_t tpr = shape->threads_per_copy, rpc = shape->copies_per_cta;
+    if (tpr == 0 || (tpr & (tpr - 1)) || tpr > 256 || rpc == 0 || rpc > 64 || tpr * rpc > 256)
+        return fail(GBMC_ERR_ARG, "threads_per_copy must be a power of two <= 256, copies_per_cta in 1..64, product <= 256");
+    g_shapes[k] = Shape{tpr, rpc, shape->row_walk != 0};
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uint32_t n_sweeps, gbmc_tuning* out) {
+    if (!ctx || !l || !out) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!beta_ok(beta, l->d.dim)) return fail(GBMC_ERR_ARG, "beta out of range");
+    if (n_sweeps == 0) n_sweeps = 1;
+    std::memset(out, 0, sizeof(*out));
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const Tuning def = tune(l, false);
+    if (!def.resident) return GBMC_OK;
+    // time on instance 0 with at most 32768 of its replicas, on a scratch copy
+    const uint32_t R = l->d.n_replicas < 32768u ? l->d.n_replicas : 32768u;
+    const size_t bytes = (size_t)R * l->N;
+    int8_t* scratch = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&scratch, bytes, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(scratch, l->cur, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    cudaEvent_t e0 = ctx->event(), e1 = ctx->event();
+    const uint32_t W = (uint32_t)l->d.L / 8;
+    const uint64_t units = units_per_copy(l);
+    double best = 1e30;
+    Shape best_shape{def.tpr, def.rpc, true};
+    uint32_t n_cand = 0;
+    gbmc_status st = GBMC_OK;
+    for (uint32_t tpr = 8; tpr <= 256 && st == GBMC_OK; tpr <<= 1) {
+        if (tpr > 2 * units && tpr > 32) break;
+        for (uint32_t threads : {128u, 256u}) {
+            if (tpr > threads) continue;
+            for (int rw = 1; rw >= 0; --rw) {
+                if (rw && (l->d.L % 8 != 0 || tpr % W != 0)) continue;
+                const Tuning tu = make_tuning(l, tpr, threads / tpr, rw != 0);
+                if (!tu.resident || tu.threads != threads) continue;
+                SweepLaunch P;
+                std::memset(&P, 0, sizeof(P));
+                SweepJob J = base_job(l, tu);
+                J.src = J.dst = scratch;
+                J.R = R;
+                J.n_inst = 1;
+                J.ctas_per_inst = (R + tu.rpc - 1) / tu.rpc;
+                J.nsweeps = n_sweeps;
+                J.t0 = 0;
+                thresholds(beta, J.thr);
+                P.jobs[0] = J;
+                P.njobs = 1;
+                P.dim = l->d.dim;
+                P.ea = l->d.model == GBMC_EA_PMJ;
+                P.swar = (l->d.L % 8) == 0;
+                std::vector<Tuning> tv{tu};
+                // warm-up launch, then two timed launches
+                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
+                cudaEventRecord(e0, ctx->stream);
+                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
+                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
+                cudaEventRecord(e1, ctx->stream);
+                cudaError_t ce = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce != cudaSuccess) {
+                    st = fail(GBMC_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
+                    break;
+                }
+                ++n_cand;
+                if (ms < best) {
+                    best = ms;
+                    best_shape = Shape{tu.tpr, tu.rpc, rw != 0};
+                }
+            }
+        }
+    }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    cudaFreeAsync(scratch, ctx->stream);
+    if (st != GBMC_OK) return st;
+    {
+        std::lock_guard<std::mutex> g(g_shape_mu);
+        g_shapes[ShapeKey{l->d.dim, l->d.model, l->d.L}] = best_shape;
+    }
+    out->resident = 1;
+    out->threads_per_copy = best_shape.tpr;
+    out->copies_per_cta = best_shape.copies_per_cta;
+    out->row_walk = best_shape.rowwise ? 1 : 0;
+    out->ms_per_sweep = best / (2.0 * n_sweeps);
+    out->n_candidates = n_cand;
     return GBMC_OK;
 }
 

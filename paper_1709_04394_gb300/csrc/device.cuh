@@ -15,6 +15,13 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
 enum : uint32_t { kPurposeMetro = 0u, kPurposeInit = 1u, kPurposeResample = 2u, kPurposeCoupling = 3u };
 
+// 32 x 32 -> 64-bit product as (hi, lo): one wide multiply.
+__device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
 __device__ __forceinline__ uint32_t c3_word(uint32_t purpose, uint32_t colour, uint32_t instance) {
     return (purpose << 28) | (colour << 27) | instance;
 }
@@ -22,10 +29,9 @@ __device__ __forceinline__ uint32_t c3_word(uint32_t purpose, uint32_t colour, u
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-        const uint32_t lo0 = kPhiloxM0 * c.x;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-        const uint32_t lo1 = kPhiloxM1 * c.z;
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo(kPhiloxM1, c.z, hi1, lo1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += kPhiloxW0;
         k1 += kPhiloxW1;
@@ -61,17 +67,19 @@ __device__ __forceinline__ PhiloxFixed philox_fix(uint32_t t, uint32_t r, uint32
 
 __device__ __forceinline__ uint4 philox_q(const PhiloxFixed& f, uint32_t q) {
     // round 0: words 2, 3 depend on q
-    const uint32_t x = __umulhi(kPhiloxM0, q) ^ f.x0;
-    const uint32_t y = kPhiloxM0 * q;
+    uint32_t x, y;
+    mulhilo(kPhiloxM0, q, x, y);
+    x ^= f.x0;
     // round 1
-    uint4 c = make_uint4(__umulhi(kPhiloxM1, x) ^ f.b1, kPhiloxM1 * x, f.u1 ^ y, f.v1);
+    uint32_t h1, l1;
+    mulhilo(kPhiloxM1, x, h1, l1);
+    uint4 c = make_uint4(h1 ^ f.b1, l1, f.u1 ^ y, f.v1);
     uint32_t k0 = f.k0, k1 = f.k1;
 #pragma unroll
     for (int round = 2; round < 10; ++round) {
-        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-        const uint32_t lo0 = kPhiloxM0 * c.x;
-        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-        const uint32_t lo1 = kPhiloxM1 * c.z;
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo(kPhiloxM1, c.z, hi1, lo1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += kPhiloxW0;
         k1 += kPhiloxW1;

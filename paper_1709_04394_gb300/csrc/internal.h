@@ -20,6 +20,7 @@ struct SweepJob {
     int8_t* dst;              // configuration written: copy c to dst + c*N (may be src if no parent)
     const uint32_t* parent;   // [n_inst*R] source replica (within its instance) of each slot, or null
     const uint8_t* jbits;     // +-J bonds: [n_inst][3][N], byte 1 where J = -1; null for J = 1
+    const uint8_t* jsplit;    // +-J bonds per colour plane: [n_inst][2][6][N/2], byte 4 where J = -1
     int32_t* E;               // [n_inst*R] energy after the last sweep, or null
     int32_t* M;               // [n_inst*R] magnetisation after the last sweep, or null
     int32_t* Eser;            // [nsweeps][n_inst*R] per-sweep energy, or null
@@ -44,7 +45,8 @@ struct SweepLaunch {
     int32_t njobs;
     int32_t dim;
     int32_t ea;
-    int32_t swar;                      // 1: every job has L % 8 == 0 (8-byte row chunks)
+    int32_t swar;                      // 1: every job has L % 8 == 0 (split colour planes)
+    int32_t rowwise;                   // 1: every job's threads per copy are a multiple of L/8
 };
 
 // ---- launchers (return cudaError_t of the launch) ----
@@ -52,6 +54,10 @@ cudaError_t launch_init_spins(int8_t* spins, int dim, uint32_t L, uint32_t n_ins
                               uint32_t inst_base, uint64_t seed, int random_start, cudaStream_t s);
 cudaError_t launch_couplings(uint8_t* jbits, uint32_t L, uint32_t n_inst, uint32_t inst_base,
                              uint64_t seed, cudaStream_t s);
+// Bond planes of the split layout (L % 8 == 0): for colour c and each site of
+// that colour, the bonds to its 6 neighbours in the order used by the sweep.
+cudaError_t launch_split_bonds(const uint8_t* jbits, uint8_t* jsplit, uint32_t L, uint32_t n_inst,
+                               cudaStream_t s);
 cudaError_t launch_jbits_to_int8(const uint8_t* jbits, int8_t* out, uint32_t N, uint32_t n_inst,
                                  cudaStream_t s);
 cudaError_t launch_observables(const int8_t* spins, const uint8_t* jbits, int dim, uint32_t L,

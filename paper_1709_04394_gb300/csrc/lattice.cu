@@ -73,6 +73,51 @@ cudaError_t launch_couplings(uint8_t* jbits, uint32_t L, uint32_t n_inst, uint32
     return cudaGetLastError();
 }
 
+// jsplit[((inst*2 + c)*6 + d)*(N/2) + row*(L/2) + j] = 4 if the bond in
+// direction d of the colour-c site (row, j) has J = -1. Directions: the x
+// neighbour with the same plane index j, the other x neighbour, y-1, y+1,
+// z-1, z+1. The site is x = 2j + o with o = (y+z+c)&1: for o = 0 the same-j
+// neighbour is x+1 and the other x-1; for o = 1 the reverse.
+__global__ void k_split_bonds(const uint8_t* jbits, uint8_t* jsplit, uint32_t L, uint32_t n_inst) {
+    const uint32_t N = L * L * L, H = N / 2;
+    const uint64_t total = (uint64_t)n_inst * N;  // (inst, c, row, j)
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t inst = (uint32_t)(g / N);
+        const uint32_t rem = (uint32_t)(g - (uint64_t)inst * N);
+        const uint32_t c = rem / H, k = rem - c * H;
+        const uint32_t row = k / (L / 2), j = k - row * (L / 2);
+        const uint32_t y = row % L, z = row / L;
+        const uint32_t o = (y + z + c) & 1u;
+        const uint32_t x = 2 * j + o;
+        const uint8_t* Jx = jbits + (uint64_t)inst * 3 * N;
+        const uint8_t* Jy = Jx + N;
+        const uint8_t* Jz = Jx + 2 * N;
+        const uint32_t site = row * L + x;
+        const uint32_t xm = row * L + (x == 0 ? L - 1 : x - 1);
+        const uint32_t ym = (z * L + (y == 0 ? L - 1 : y - 1)) * L + x;
+        const uint32_t zm = ((z == 0 ? L - 1 : z - 1) * L + y) * L + x;
+        const uint8_t fwd_x = Jx[site], bwd_x = Jx[xm];
+        uint8_t b[6];
+        b[0] = o ? bwd_x : fwd_x;
+        b[1] = o ? fwd_x : bwd_x;
+        b[2] = Jy[ym];
+        b[3] = Jy[site];
+        b[4] = Jz[zm];
+        b[5] = Jz[site];
+        uint8_t* dst = jsplit + ((uint64_t)inst * 2 + c) * 6 * H + k;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) dst[(uint64_t)d * H] = b[d] ? 4 : 0;
+    }
+}
+
+cudaError_t launch_split_bonds(const uint8_t* jbits, uint8_t* jsplit, uint32_t L, uint32_t n_inst,
+                               cudaStream_t s) {
+    k_split_bonds<<<152 * 8, 256, 0, s>>>(jbits, jsplit, L, n_inst);
+    count_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_jbits_to_int8(const uint8_t* jbits, int8_t* out, uint32_t N, uint32_t n_inst) {
     const uint64_t total = (uint64_t)n_inst * N * 3;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total;

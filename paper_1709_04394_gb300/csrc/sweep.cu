@@ -15,13 +15,20 @@
 //    lattices too large for shared memory (one launch per half-sweep, the
 //    kernel-boundary synchronisation described in Sec. 3.1).
 //
-// Spins are bytes +1 (0x01) / -1 (0xFF). For L % 8 == 0 each thread updates a
-// row chunk of 8 bytes at a time (the 4 sites of one colour in it use the 4
-// words of one Philox call): the byte-wise "down" bit d = (byte >> 1) & 1 of the
-// chunk and of its neighbour chunks is combined with byte-parallel xor/add to
-// count, per site, the unsatisfied bonds a (s_i J_ij s_j = -1); then
-// dE = 4 (dim - a) and the site flips iff dE <= 0 or u <= T(dE). Other L use a
-// per-site path with the same words.
+// Spins are bytes +1 (0x01) / -1 (0xFF). For L % 8 == 0 the resident kernel
+// keeps each copy in shared memory as two colour planes (the separate
+// sub-lattice storage of Sec. 3.1): plane c, row r = z*L + y, holds the L/2
+// sites of colour c of that row in x order. A thread updates one 32-bit word
+// of a plane = 4 consecutive same-colour sites = the 4 words of one Philox
+// call. Their vertical neighbours are the same word of the other plane in the
+// rows above/below; the horizontal ones are the same word and the word shifted
+// by one byte (funnel shift). Byte-parallel (s_i ^ s_j) & 4 summed over the
+// neighbours gives 4a per site, a = number of unsatisfied bonds
+// (s_i J_ij s_j = -1), so dE = 4 (dim - a); 4a is also the byte offset of the
+// site's threshold in a shared table (dE <= 0 -> 0xffffffff, i.e. always
+// accept), and the site flips iff u <= table[a]. The global-memory kernel
+// works on the row-major layout with 8-byte chunks; L % 8 != 0 uses a per-site
+// path with the same Philox words.
 #include "device.cuh"
 #include "internal.h"
 
@@ -113,6 +120,70 @@ __device__ __forceinline__ void unit_swar(uint8_t* sp, const uint8_t* jb, uint32
     }
 }
 
+__device__ __forceinline__ uint32_t neq4(uint32_t a, uint32_t b) { return (a ^ b) & 0x04040404u; }
+
+// Split-plane unit: word g of row `row` of colour plane `colour`. sp: copy
+// base (plane 0 then plane 1, N/2 bytes each); jb: this colour's 2*DIM bond
+// planes (bytes 0x04 where J = -1; order same-j x, shifted x, y-1, y+1, z-1,
+// z+1); tbl: byte-addressed threshold table (entry a at byte 4a).
+template <int DIM, bool EA, bool MEASURE>
+__device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
+                                           uint32_t row, uint32_t y, uint32_t z, uint32_t g, uint32_t colour,
+                                           const PhiloxFixed& pf, const uint8_t* tbl, bool doflip, int& e_acc,
+                                           int& m_acc) {
+    const uint32_t W = L >> 3, H = N >> 1;
+    const uint32_t o = (y + z + colour) & 1u;
+    uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * H);
+    const uint32_t* oth = reinterpret_cast<const uint32_t*>(sp + (colour ^ 1u) * H);
+    const uint32_t rw = row * W;
+    const uint32_t cur = own[rw + g];
+    const uint32_t same = oth[rw + g];
+    // horizontal neighbour not sharing j: j+1 (odd x) or j-1 (even x)
+    const uint32_t side = o ? __funnelshift_r(same, oth[rw + (g + 1 == W ? 0 : g + 1)], 8)
+                            : __funnelshift_l(oth[rw + (g == 0 ? W - 1 : g - 1)], same, 8);
+    const uint32_t rowu = y == 0 ? row + L - 1 : row - 1;
+    const uint32_t rowd = y + 1 == L ? row + 1 - L : row + 1;
+    const uint32_t up = oth[rowu * W + g], dn = oth[rowd * W + g];
+    uint32_t a4;
+    const uint32_t* b = EA ? reinterpret_cast<const uint32_t*>(jb) + rw + g : nullptr;
+    const uint32_t P = H >> 2;  // words per plane
+    if (EA) {
+        a4 = (neq4(cur, same) ^ b[0]) + (neq4(cur, side) ^ b[P]) + (neq4(cur, up) ^ b[2 * P]) +
+             (neq4(cur, dn) ^ b[3 * P]);
+    } else {
+        a4 = neq4(cur, same) + neq4(cur, side) + neq4(cur, up) + neq4(cur, dn);
+    }
+    if (DIM == 3) {
+        const uint32_t rowb = z == 0 ? row + (L - 1) * L : row - L;
+        const uint32_t rowf = z + 1 == L ? row - (L - 1) * L : row + L;
+        const uint32_t bk = oth[rowb * W + g], fr = oth[rowf * W + g];
+        if (EA) a4 += (neq4(cur, bk) ^ b[4 * P]) + (neq4(cur, fr) ^ b[5 * P]);
+        else a4 += neq4(cur, bk) + neq4(cur, fr);
+    }
+    uint32_t flip = 0;
+    if (doflip) {
+        const uint4 w = philox_q(pf, rw + g);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t am = __byte_perm(a4, 0u, 0x4440u + m);  // 4a of site m
+            const uint32_t thr = *reinterpret_cast<const uint32_t*>(tbl + am);
+            const uint32_t u = m == 0 ? w.x : m == 1 ? w.y : m == 2 ? w.z : w.w;
+            flip |= (u <= thr) ? (0xFEu << (8 * m)) : 0u;
+        }
+    }
+    const uint32_t nw = cur ^ flip;
+    if (doflip) own[rw + g] = nw;
+    if (MEASURE) {
+        // E contribution -sum s_new h = sum_acc s h - sum_rej s h, s h = 2 DIM - (4a)/2
+        const int s_all = (int)__dp4a(a4, 0x01010101u, 0u);
+        const int s_acc = (int)__dp4a(a4 & flip, 0x01010101u, 0u);
+        const int nacc = __popc(flip & 0x02020202u);
+        e_acc += 4 * DIM * nacc - s_acc - 8 * DIM + s_all / 2;
+        // the other plane's word `same` pairs each of its sites with one site here
+        m_acc += 8 - 2 * (__popc(nw & 0x02020202u) + __popc(same & 0x02020202u));
+    }
+}
+
 // Per-site path for any even L: quad q covers colour ranks k = 4q .. 4q+3.
 template <int DIM, bool EA, bool MEASURE>
 __device__ __forceinline__ void unit_scalar(int8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
@@ -167,41 +238,93 @@ __device__ __forceinline__ void unit_scalar(int8_t* sp, const uint8_t* jb, uint3
     }
 }
 
-template <int DIM, bool EA, bool SWAR>
-__device__ __forceinline__ void half_sweep_copy(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
-                                                uint32_t first_unit, uint32_t stride, uint32_t colour,
-                                                const PhiloxFixed& pf, const Thr& T, bool flip,
-                                                bool measure, int& e, int& m) {
+// Walk of one thread over the split-plane units of a copy: when the threads
+// serving a copy are a multiple of the words per plane row, each thread keeps
+// one word column g and steps through rows (no division in the loop).
+struct UnitWalk {
+    bool rowwise;
+    uint32_t g0, row0, y0, z0, rstep, dy, dz;
+};
+
+template <int DIM>
+__device__ __forceinline__ UnitWalk make_walk(uint32_t L, uint32_t lane, uint32_t tpr) {
+    UnitWalk w;
+    const uint32_t W = L >> 3;
+    w.rowwise = (tpr % W) == 0;
+    w.g0 = lane % W;
+    w.row0 = lane / W;
+    w.rstep = tpr / W;
+    w.y0 = DIM == 3 ? w.row0 % L : w.row0;
+    w.z0 = DIM == 3 ? w.row0 / L : 0;
+    w.dy = DIM == 3 ? w.rstep % L : w.rstep;
+    w.dz = DIM == 3 ? w.rstep / L : 0;
+    return w;
+}
+
+template <int DIM, bool EA, bool SWAR, bool ROWWISE, bool MEASURE>
+__device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
+                                                  uint32_t first_unit, uint32_t stride, const UnitWalk& wk,
+                                                  uint32_t colour, const PhiloxFixed& pf, const Thr& T,
+                                                  const uint8_t* tbl, bool flip, int& e, int& m) {
     if (SWAR) {
-        const uint32_t G = L >> 3, units = N >> 3;
-        if (measure) {
-            for (uint32_t uu = first_unit; uu < units; uu += stride)
-                unit_swar<DIM, EA, true>(sp, jb, L, N, uu / G, uu % G, colour, pf, T, flip, e, m);
+        const uint32_t W = L >> 3, rows = N / L;
+        const uint8_t* jbc = EA ? jb + colour * (2u * DIM) * (N >> 1) : nullptr;
+        if (ROWWISE) {
+            uint32_t y = wk.y0, z = wk.z0;
+#pragma unroll 1
+            for (uint32_t row = wk.row0; row < rows; row += wk.rstep) {
+                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m);
+                if (DIM == 3) {
+                    y += wk.dy;
+                    z += wk.dz;
+                    if (y >= L) {
+                        y -= L;
+                        ++z;
+                    }
+                } else {
+                    y += wk.rstep;
+                }
+            }
         } else {
-            for (uint32_t uu = first_unit; uu < units; uu += stride)
-                unit_swar<DIM, EA, false>(sp, jb, L, N, uu / G, uu % G, colour, pf, T, flip, e, m);
+            const uint32_t units = N >> 3;
+            for (uint32_t uu = first_unit; uu < units; uu += stride) {
+                const uint32_t row = uu / W;
+                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, DIM == 3 ? row % L : row, DIM == 3 ? row / L : 0,
+                                             uu % W, colour, pf, tbl, flip, e, m);
+            }
         }
     } else {
         const uint32_t units = ((N >> 1) + 3) >> 2;
         int8_t* s8 = reinterpret_cast<int8_t*>(sp);
-        if (measure) {
-            for (uint32_t uu = first_unit; uu < units; uu += stride)
-                unit_scalar<DIM, EA, true>(s8, jb, L, N, uu, colour, pf, T, flip, e, m);
-        } else {
-            for (uint32_t uu = first_unit; uu < units; uu += stride)
-                unit_scalar<DIM, EA, false>(s8, jb, L, N, uu, colour, pf, T, flip, e, m);
-        }
+        for (uint32_t uu = first_unit; uu < units; uu += stride)
+            unit_scalar<DIM, EA, MEASURE>(s8, jb, L, N, uu, colour, pf, T, flip, e, m);
     }
+}
+
+template <int DIM, bool EA, bool SWAR, bool ROWWISE>
+__device__ __forceinline__ void half_sweep_copy(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
+                                                uint32_t first_unit, uint32_t stride, const UnitWalk& wk,
+                                                uint32_t colour, const PhiloxFixed& pf, const Thr& T,
+                                                const uint8_t* tbl, bool flip, bool measure, int& e, int& m) {
+    if (measure)
+        half_sweep_copy_m<DIM, EA, SWAR, ROWWISE, true>(sp, jb, L, N, first_unit, stride, wk, colour, pf, T, tbl,
+                                                        flip, e, m);
+    else
+        half_sweep_copy_m<DIM, EA, SWAR, ROWWISE, false>(sp, jb, L, N, first_unit, stride, wk, colour, pf, T, tbl,
+                                                         flip, e, m);
 }
 
 __device__ __forceinline__ uint32_t padded(uint32_t n) { return (n + 15u) & ~15u; }
 
 // Grid: one CTA per (job, instance, group of rpc replicas). blockDim.x must be
-// a multiple of rpc; blockDim.x / rpc threads serve each replica.
-template <int DIM, bool EA, bool SWAR>
+// a multiple of rpc; blockDim.x / rpc threads serve each replica. Shared
+// memory: rpc copies (split colour planes when SWAR, else row-major), then
+// the instance's bond planes (EA).
+template <int DIM, bool EA, bool SWAR, bool ROWWISE>
 __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ SweepLaunch P) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int acc_e[64], acc_m[64];
+    __shared__ __align__(16) uint32_t s_tbl[8];
     int jid = 0;
     while (jid + 1 < P.njobs && blockIdx.x >= P.cta_begin[jid + 1]) ++jid;
     const SweepJob& J = P.jobs[jid];
@@ -211,14 +334,34 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
     const uint32_t nrep = min(J.rpc, J.R - r0);
     const uint32_t N = J.N, L = J.L, stride_b = padded(N);
     const uint64_t slot0 = (uint64_t)inst * J.R + r0;
+    uint8_t* jsm = smem + (uint64_t)J.rpc * stride_b;
 
-    // ---- load: copy c of this CTA from src + parent(c) (gather) ----
-    {
-        const uint32_t words = stride_b >> 2;  // 4-byte words per copy (N % 4 == 0)
+    // ---- load: copy c of this CTA from src + parent(c) (the resampling gather) ----
+    if (SWAR) {
+        // row-major global -> colour planes: the even-x bytes of row r belong
+        // to colour (y+z)&1, the odd-x bytes to the other colour
+        const uint32_t chunks = N >> 3, W = L >> 3, H = N >> 1;
+        for (uint32_t idx = threadIdx.x; idx < nrep * chunks; idx += blockDim.x) {
+            const uint32_t c = idx / chunks, ch = idx - c * chunks;
+            const uint32_t row = ch / W;
+            const uint64_t slot = slot0 + c;
+            const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
+            const uint2 v = *reinterpret_cast<const uint2*>(J.src + srcslot * N + (uint64_t)ch * 8);
+            const uint32_t y = DIM == 3 ? row % L : row, z = DIM == 3 ? row / L : 0;
+            const uint32_t pe = (y + z) & 1u;
+            uint32_t* pl = reinterpret_cast<uint32_t*>(smem + c * stride_b);
+            pl[pe * (H >> 2) + ch] = __byte_perm(v.x, v.y, 0x6420);
+            pl[(pe ^ 1u) * (H >> 2) + ch] = __byte_perm(v.x, v.y, 0x7531);
+        }
+        if (EA) {
+            const uint4* jsrc = reinterpret_cast<const uint4*>(J.jsplit + (uint64_t)inst * 6 * N);
+            for (uint32_t idx = threadIdx.x; idx < (6 * N) >> 4; idx += blockDim.x)
+                reinterpret_cast<uint4*>(jsm)[idx] = jsrc[idx];
+        }
+    } else {
         const uint32_t nw = N >> 2;
-        for (uint32_t idx = threadIdx.x; idx < nrep * words; idx += blockDim.x) {
-            const uint32_t c = idx / words, wi = idx - c * words;
-            if (wi >= nw) continue;
+        for (uint32_t idx = threadIdx.x; idx < nrep * nw; idx += blockDim.x) {
+            const uint32_t c = idx / nw, wi = idx - c * nw;
             const uint64_t slot = slot0 + c;
             const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
             reinterpret_cast<uint32_t*>(smem + c * stride_b)[wi] =
@@ -226,15 +369,19 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
         }
         if (EA) {
             const uint8_t* jsrc = J.jbits + (uint64_t)inst * 3 * N;
-            uint8_t* jdst = smem + (uint64_t)J.rpc * stride_b;
             const uint32_t nwj = (3 * N) >> 2;
             for (uint32_t idx = threadIdx.x; idx < nwj; idx += blockDim.x)
-                reinterpret_cast<uint32_t*>(jdst)[idx] = reinterpret_cast<const uint32_t*>(jsrc)[idx];
+                reinterpret_cast<uint32_t*>(jsm)[idx] = reinterpret_cast<const uint32_t*>(jsrc)[idx];
         }
     }
     if (threadIdx.x < 64) {
         acc_e[threadIdx.x] = 0;
         acc_m[threadIdx.x] = 0;
+    }
+    if (threadIdx.x < 8) {
+        // entry a (byte 4a): dE = 4 (DIM - a); dE <= 0 is always accepted
+        const int d = DIM - (int)threadIdx.x;
+        s_tbl[threadIdx.x] = d <= 0 ? 0xFFFFFFFFu : (d == 1 ? J.thr[0] : (d == 2 ? J.thr[1] : J.thr[2]));
     }
     __syncthreads();
 
@@ -243,13 +390,15 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
     const uint32_t lane = threadIdx.x - c * tpr;
     const bool active = c < nrep;
     uint8_t* sp = smem + c * stride_b;
-    const uint8_t* jb = EA ? smem + (uint64_t)J.rpc * stride_b : nullptr;
+    const uint8_t* jb = EA ? jsm : nullptr;
+    const uint8_t* tbl = reinterpret_cast<const uint8_t*>(s_tbl);
     const uint32_t r = r0 + c;
     const uint32_t instance = J.inst_base + inst;
     const Thr T{J.thr[0], J.thr[1], J.thr[2]};
     const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
     const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
     const bool want_final = J.E || J.M || J.hist;
+    const UnitWalk wk = make_walk<DIM>(L, lane, tpr);
 
     const uint32_t nsw = J.nsweeps;
     for (uint32_t s = 0; s <= nsw; ++s) {
@@ -263,7 +412,7 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
             if (!sweep && colour == 0) continue;
             if (active) {
                 const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
-                half_sweep_copy<DIM, EA, SWAR>(sp, jb, L, N, lane, tpr, colour, pf, T, sweep,
+                half_sweep_copy<DIM, EA, SWAR, ROWWISE>(sp, jb, L, N, lane, tpr, wk, colour, pf, T, tbl, sweep,
                                                measure && colour == 1, e, m);
             }
             __syncthreads();
@@ -305,12 +454,27 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
 
     // ---- store ----
     if (nsw > 0 || J.dst != J.src || J.parent) {
-        const uint32_t words = stride_b >> 2, nw = N >> 2;
-        for (uint32_t idx = threadIdx.x; idx < nrep * words; idx += blockDim.x) {
-            const uint32_t cc = idx / words, wi = idx - cc * words;
-            if (wi >= nw) continue;
-            reinterpret_cast<uint32_t*>(J.dst + (slot0 + cc) * N)[wi] =
-                reinterpret_cast<const uint32_t*>(smem + cc * stride_b)[wi];
+        if (SWAR) {
+            const uint32_t chunks = N >> 3, W = L >> 3, H = N >> 1;
+            for (uint32_t idx = threadIdx.x; idx < nrep * chunks; idx += blockDim.x) {
+                const uint32_t cc = idx / chunks, ch = idx - cc * chunks;
+                const uint32_t row = ch / W;
+                const uint32_t y = DIM == 3 ? row % L : row, z = DIM == 3 ? row / L : 0;
+                const uint32_t pe = (y + z) & 1u;
+                const uint32_t* pl = reinterpret_cast<const uint32_t*>(smem + cc * stride_b);
+                const uint32_t ev = pl[pe * (H >> 2) + ch], od = pl[(pe ^ 1u) * (H >> 2) + ch];
+                uint2 v;
+                v.x = __byte_perm(ev, od, 0x5140);
+                v.y = __byte_perm(ev, od, 0x7362);
+                *reinterpret_cast<uint2*>(J.dst + (slot0 + cc) * N + (uint64_t)ch * 8) = v;
+            }
+        } else {
+            const uint32_t nw = N >> 2;
+            for (uint32_t idx = threadIdx.x; idx < nrep * nw; idx += blockDim.x) {
+                const uint32_t cc = idx / nw, wi = idx - cc * nw;
+                reinterpret_cast<uint32_t*>(J.dst + (slot0 + cc) * N)[wi] =
+                    reinterpret_cast<const uint32_t*>(smem + cc * stride_b)[wi];
+            }
         }
     }
 }
@@ -320,16 +484,16 @@ size_t resident_smem_bytes(const SweepLaunch& P) {
     for (int j = 0; j < P.njobs; ++j) {
         const SweepJob& J = P.jobs[j];
         size_t b = (size_t)J.rpc * ((J.N + 15u) & ~15u);
-        if (P.ea) b += 3ull * J.N;
+        if (P.ea) b += (P.swar ? 6ull : 3ull) * J.N;
         if (b > mx) mx = b;
     }
     return mx;
 }
 
-template <int DIM, bool EA, bool SWAR>
+template <int DIM, bool EA, bool SWAR, bool ROWWISE>
 static cudaError_t launch_res(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads, size_t smem,
                               cudaStream_t s) {
-    auto kern = k_sweep_resident<DIM, EA, SWAR>;
+    auto kern = k_sweep_resident<DIM, EA, SWAR, ROWWISE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -339,20 +503,19 @@ static cudaError_t launch_res(const SweepLaunch& P, uint32_t n_ctas, uint32_t th
     return cudaGetLastError();
 }
 
+template <int DIM, bool EA>
+static cudaError_t launch_res_dim(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads, size_t smem,
+                                  cudaStream_t s) {
+    if (!P.swar) return launch_res<DIM, EA, false, false>(P, n_ctas, threads, smem, s);
+    return P.rowwise ? launch_res<DIM, EA, true, true>(P, n_ctas, threads, smem, s)
+                     : launch_res<DIM, EA, true, false>(P, n_ctas, threads, smem, s);
+}
+
 cudaError_t launch_sweep_resident(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads, size_t smem,
                                   cudaStream_t s) {
-    if (P.dim == 2 && !P.ea) {
-        return P.swar ? launch_res<2, false, true>(P, n_ctas, threads, smem, s)
-                      : launch_res<2, false, false>(P, n_ctas, threads, smem, s);
-    }
-    if (P.dim == 3 && !P.ea) {
-        return P.swar ? launch_res<3, false, true>(P, n_ctas, threads, smem, s)
-                      : launch_res<3, false, false>(P, n_ctas, threads, smem, s);
-    }
-    if (P.dim == 3 && P.ea) {
-        return P.swar ? launch_res<3, true, true>(P, n_ctas, threads, smem, s)
-                      : launch_res<3, true, false>(P, n_ctas, threads, smem, s);
-    }
+    if (P.dim == 2 && !P.ea) return launch_res_dim<2, false>(P, n_ctas, threads, smem, s);
+    if (P.dim == 3 && !P.ea) return launch_res_dim<3, false>(P, n_ctas, threads, smem, s);
+    if (P.dim == 3 && P.ea) return launch_res_dim<3, true>(P, n_ctas, threads, smem, s);
     return cudaErrorInvalidValue;
 }
 

@@ -36,6 +36,12 @@ class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("resident", C.c_int32), ("threads_per_copy", C.c_uint32), ("copies_per_cta", C.c_uint32),
+                ("row_walk", C.c_int32), ("ms_per_sweep", C.c_double), ("n_candidates", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
 class LatticeDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("L", C.c_int32), ("model", C.c_int32), ("layout", C.c_int32),
                 ("start", C.c_int32), ("n_instances", C.c_uint32), ("n_replicas", C.c_uint32),
@@ -100,6 +106,8 @@ def load():
             "lattice_couplings_out": ([p, p, p, C.c_size_t], st),
             "metropolis_sweeps": ([p, p, C.c_double, C.c_uint32, p, p], st),
             "observables": ([p, p, p, p], st),
+            "gbmc_autotune": ([p, p, C.c_double, C.c_uint32, C.POINTER(Tuning)], st),
+            "gbmc_set_tuning": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tuning)], st),
             "pa_create": ([p, C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(PaConfig), C.POINTER(C.c_void_p)], st),
             "pa_free": ([p], st),
             "pa_reset": ([p, p, C.c_int32, C.c_uint64], st),
@@ -223,6 +231,21 @@ def metropolis_sweeps(ctx, lat, beta: float, n_sweeps: int, E_series=None, M_ser
 
 def observables(ctx, lat, E=None, M=None):
     _check(load().observables(ctx, lat, _ptr(E), _ptr(M)))
+
+
+def gbmc_autotune(ctx, lat, beta, n_sweeps=10) -> Tuning:
+    t = Tuning()
+    _check(load().gbmc_autotune(ctx, lat, float(beta), n_sweeps, C.byref(t)))
+    return t
+
+
+def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_walk=True):
+    """Force a launch shape for a lattice class; threads_per_copy=None clears it."""
+    if threads_per_copy is None:
+        _check(load().gbmc_set_tuning(dim, model, L, None))
+        return
+    t = Tuning(1, threads_per_copy, copies_per_cta, int(bool(row_walk)), 0.0, 0, 0)
+    _check(load().gbmc_set_tuning(dim, model, L, C.byref(t)))
 
 
 def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=1.0, betas=None, init=True,
