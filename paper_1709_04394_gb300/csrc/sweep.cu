@@ -271,7 +271,7 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
         const uint8_t* jbc = EA ? jb + colour * (2u * DIM) * (N >> 1) : nullptr;
         if (ROWWISE) {
             uint32_t y = wk.y0, z = wk.z0;
-#pragma unroll 1
+#pragma unroll 4
             for (uint32_t row = wk.row0; row < rows; row += wk.rstep) {
                 unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m);
                 if (DIM == 3) {
