@@ -257,6 +257,50 @@ gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, u
 gbmc_status pa_energies_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, int32_t *E_dst,
                             int32_t *M_dst, size_t count);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free resampling. The paper has no counterpart: this entry point */
+/* exists for callers that cannot allocate device memory -- work being       */
+/* captured into a CUDA graph (where cudaMalloc is not allowed), processes   */
+/* whose device memory belongs to another allocator or pool that must not be */
+/* bypassed, and embedded or real-time drivers that reserve all memory at    */
+/* start-up.                                                                   */
+/* ------------------------------------------------------------------------ */
+/* One resampling step of population annealing for n_instances populations of
+ * n_replicas replicas each, identical to the resampling inside pa_step (same
+ * kernels, same Philox words, same parents and ln Q), but its scratch space
+ * (histograms, integer cumulative weights, counts, weight tables, a copy of
+ * the energies; about 8.1 MiB) is a fixed array compiled into the library, which every GPU that
+ * loads the library holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   cuda_stream: stream to enqueue on (NULL = legacy default stream).
+ *   device: CUDA device index; made current by the call.
+ *   dim, n_sites: lattice dimension (2 or 3) and N = L^dim, which fix the
+ *     energy range [-dim N, dim N] and its bins of width 4.
+ *   instance_base, seed, step: Philox instance id of the first population,
+ *     key, and annealing step index i (draw k uses counter (k>>1, i, 0, c3)).
+ *   dbeta: beta_i - beta_{i-1} >= 0.
+ *   E_dev: device int32 [n_instances][n_replicas], the energies (each
+ *     population's energies must differ by multiples of 4, as Metropolis
+ *     dynamics keep them; values outside [-dim N, dim N] are clamped into it,
+ *     so invalid input gives meaningless parents but no out-of-range access).
+ *   parent_dev: device uint32 [n_instances][n_replicas] out: slot -> replica
+ *     (within its instance) it copies; children contiguous, parents in order.
+ *   lnQ_dev: device double [n_instances] out: ln Q_i of Eq. (13).
+ * Limits (GBMC_ERR_ARG beyond them): n_instances * n_replicas <= 131072,
+ * n_instances <= 1024, dim*n_sites/2 + 1 <= 65537, n_instances *
+ * (dim*n_sites/2 + 1) <= 524288.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture. Every call
+ * shares the one array and it keeps the last call's contents (each call
+ * clears what must start at zero), so calls whose work overlaps on the GPU
+ * -- on different streams, or from different host threads -- race and give
+ * wrong results: serialise them. Asynchronous: results are ready when the
+ * stream reaches them. */
+gbmc_status pa_resample_static(void *cuda_stream, int32_t device, int32_t dim, int64_t n_sites,
+                               uint32_t n_instances, uint32_t n_replicas, uint32_t instance_base,
+                               uint64_t seed, uint32_t step, double dbeta, const int32_t *E_dev,
+                               uint32_t *parent_dev, double *lnQ_dev);
+
 #ifdef __cplusplus
 }
 #endif

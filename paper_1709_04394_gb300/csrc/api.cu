@@ -58,6 +58,7 @@ const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resi
 
 namespace gbmc {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace gbmc
 
 struct gbmc_ctx {

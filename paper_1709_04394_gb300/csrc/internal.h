@@ -10,6 +10,8 @@ namespace gbmc {
 
 // Kernels enqueued by this library in this process (every <<<>>> adds one).
 void count_launch();
+// Message returned by gbmc_last_error() on the calling thread.
+void set_last_error(const char* msg);
 
 constexpr int kMaxJobs = 8;
 

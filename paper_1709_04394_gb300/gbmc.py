@@ -108,6 +108,8 @@ def load():
             "observables": ([p, p, p, p], st),
             "gbmc_autotune": ([p, p, C.c_double, C.c_uint32, C.POINTER(Tuning)], st),
             "gbmc_set_tuning": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tuning)], st),
+            "pa_resample_static": ([p, C.c_int32, C.c_int32, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                    C.c_uint64, C.c_uint32, C.c_double, p, p, p], st),
             "pa_create": ([p, C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(PaConfig), C.POINTER(C.c_void_p)], st),
             "pa_free": ([p], st),
             "pa_reset": ([p, p, C.c_int32, C.c_uint64], st),
@@ -319,3 +321,10 @@ def pa_energies_out(ctx, pa, lattice, E_dst=None, M_dst=None):
 
 def gbmc_last_error() -> str:
     return load().gbmc_last_error().decode(errors="replace")
+
+
+def pa_resample_static(stream, device, dim, n_sites, n_instances, n_replicas, instance_base, seed, step, dbeta,
+                       E, parent, lnQ):
+    """Allocation-free resampling step (static device scratch); see include/gbmc.h."""
+    _check(load().pa_resample_static(stream, device, dim, n_sites, n_instances, n_replicas, instance_base, seed,
+                                     step, float(dbeta), _ptr(E), _ptr(parent), _ptr(lnQ)))
