@@ -236,10 +236,11 @@ gbmc_status pa_populations(const gbmc_pa *pa, uint32_t *n_populations);
 
 /* One annealing step (Sec. 5.4 steps 2-4): resample every population to its
  * next inverse temperature, theta sweeps there, population measurements.
- * beta_next: NULL = the schedule's next value; else host [n_lattices]
- * (must exceed the current beta). out_host: NULL or host [n_populations].
- * Synchronises when out_host != NULL or the schedule is adaptive.
- * Returns GBMC_ERR_STATE once every lattice has reached beta_f. */
+ * beta_next: NULL = the schedule's next value; else (adaptive schedules only)
+ * host [n_lattices] explicit next betas, each above the lattice's current one.
+ * out_host: NULL or host [n_populations] (rows of lattices that have already
+ * reached beta_f are zero). Synchronises when out_host != NULL or the
+ * schedule is adaptive. Returns GBMC_ERR_STATE once the schedule is done. */
 gbmc_status pa_step(gbmc_ctx *ctx, gbmc_pa *pa, const double *beta_next, gbmc_pa_stats *out_host);
 
 /* All remaining steps; stats_host: NULL or host [n_steps_max+1][n_populations]
@@ -247,6 +248,33 @@ gbmc_status pa_step(gbmc_ctx *ctx, gbmc_pa *pa, const double *beta_next, gbmc_pa
  * so far. Synchronises. */
 gbmc_status pa_run(gbmc_ctx *ctx, gbmc_pa *pa, gbmc_pa_stats *stats_host, uint32_t stats_capacity,
                    uint32_t *n_steps_done);
+
+/* Adaptive schedules (GBMC_SCHED_BISECTION, GBMC_SCHED_MLP; one population per
+ * lattice): every step reads the population's energy histogram h(E) and picks
+ * dbeta with the overlap alpha(dbeta) = sum_E min(h/R, P1), P1 ~ h e^{-dbeta E}
+ * (Sec. 5.4 cites adaptive steps without fixing them): bisection (50 halvings
+ * of [0, min(dbeta_max, beta_f - beta)]) for the largest dbeta with alpha >=
+ * target_overlap; or the MLP proposes dbeta and is kept if its alpha lies in
+ * [overlap_lo, overlap_hi], else bisection. The chosen dbeta is read back by
+ * the host, which builds the step's fp64 weight tables (libm exp) -- so these
+ * schedules synchronise once per step. Each step is logged: */
+typedef struct {
+    double beta;            /* beta_i reached by the step */
+    double dbeta;           /* beta_i - beta_{i-1} */
+    double alpha;           /* overlap of the chosen step */
+    double proposal;        /* MLP proposal (0 in bisection mode) */
+    double alpha_proposal;  /* its overlap */
+    double var;             /* variance of E of the population the step started from */
+    float features[6];      /* MLP inputs: E/N mean, log(Var E/N + 1e-6), skewness, beta, log L, log R */
+    int32_t kind;           /* 1 bisection, 2 accepted MLP proposal, 0 explicit beta_next */
+    int32_t clamped;        /* the step hit its upper bound */
+    int32_t evals;          /* overlap evaluations spent choosing it */
+    int32_t pad;
+} gbmc_schedule_record;
+gbmc_status pa_schedule_log(const gbmc_pa *pa, uint32_t lattice, gbmc_schedule_record *out, uint32_t capacity,
+                            uint32_t *n_out);
+/* The inverse temperatures beta_0 .. beta_i reached so far by a lattice. */
+gbmc_status pa_betas(const gbmc_pa *pa, uint32_t lattice, double *out, uint32_t capacity, uint32_t *n_out);
 
 /* Replica each slot was copied from in the last resampling (device or host
  * dst, uint32 [n_copies] of that lattice; indices within the instance). */
@@ -256,6 +284,28 @@ gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, u
  * (device or host int32 [n_copies]). */
 gbmc_status pa_energies_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, int32_t *E_dst,
                             int32_t *M_dst, size_t count);
+
+/* ------------------------------------------------------------------------ */
+/* Schedule MLP: 6 inputs -> 64 tanh -> 64 tanh -> 1, output y = log(dbeta   */
+/* sigma_E). Parameters: fp32 vector [W1 (64x6 row-major), b1 (64), W2       */
+/* (64x64), b2 (64), W3 (64), b3 (1)]; forward and backward use their bf16   */
+/* roundings with fp32 accumulation. Trained on the GPU on (features,        */
+/* bisection dbeta) pairs logged by pa_schedule_log. All device buffers.     */
+/* ------------------------------------------------------------------------ */
+uint32_t gbmc_mlp_param_count(void); /* 4673 */
+/* Y[b] = network(X[b][0..5]) for b < B. */
+gbmc_status mlp_forward(gbmc_ctx *ctx, const float *params, const float *X, uint32_t B, float *Y);
+/* grad = d/dparams of (1/B) sum_b (y_b - T_b)^2 / 2 and loss[0] = that loss;
+ * B <= 128 (one CTA, deterministic order). */
+gbmc_status mlp_grad(gbmc_ctx *ctx, const float *params, const float *X, const float *T, uint32_t B, float *grad,
+                     float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step k >= 1). */
+gbmc_status mlp_adam(gbmc_ctx *ctx, float *params, const float *grad, float *m, float *v, uint32_t k, float lr);
+/* epochs x ceil(n/batch) minibatches in data order (mlp_grad + mlp_adam each);
+ * loss_out: NULL or device float [epochs][ceil(n/batch)] minibatch losses.
+ * Uses stream-ordered scratch (cudaMallocAsync) for gradients and moments. */
+gbmc_status mlp_train(gbmc_ctx *ctx, float *params, const float *X, const float *T, uint32_t n, uint32_t epochs,
+                      uint32_t batch, float lr, float *loss_out);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free resampling. The paper has no counterpart: this entry point */

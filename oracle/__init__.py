@@ -62,7 +62,7 @@ def _load():
         lib.orc_resample.restype = dbl
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
-                                   p, p, p, p, p, p, p, p, p, p]
+                                   p, p, p, p, p, p, p, p, p, p, p]
         _lib = lib
         return lib
 
@@ -160,7 +160,7 @@ def linear_betas(beta_f: float, S: int) -> np.ndarray:
     return np.array([(float(beta_f) * float(i)) / float(S) for i in range(S + 1)], dtype=np.float64)
 
 
-def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None):
+def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_energies=False):
     """Population annealing for one instance (Sec. 5.4). Returns a dict of per-step
     arrays (index 0 = beta_0 = 0) and the final population."""
     lib = _load()
@@ -181,9 +181,11 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None):
     E = np.zeros(R, dtype=np.int64)
     M = np.zeros(R, dtype=np.int64)
     parents = np.arange(R, dtype=np.uint32)
+    E_steps = np.zeros((S + 1, R), dtype=np.int64) if keep_energies else None
     lib.orc_pa_run(dim, L, _ptr(Jc), seed, instance, R, S, _ptr(betas), theta, _ptr(spins),
                    int(init), _ptr(out["lnQ"]), _ptr(out["lnZ"]), _ptr(sumE), _ptr(out["sumE2"]),
-                   _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M), _ptr(parents))
-    out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents,
+                   _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M), _ptr(parents),
+                   _ptr(E_steps))
+    out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents, E_steps=E_steps,
                spins=spins.reshape(R, N), betas=betas)
     return out

@@ -347,13 +347,14 @@ void orc_children_order(uint32_t R, const uint32_t *counts, uint32_t *parent_of_
 /* spins[R*N] in/out: if init != 0 the population is initialised here.       */
 /* Per step outputs (arrays of S+1, index 0 = beta_0): lnQ, lnZ, sum E,      */
 /* sum E^2 (as double of exact int64 sums), sum |M|, sum M^2, and a running   */
-/* FNV-1a hash of the counts; optionally the last step's slot -> parent map.   */
+/* FNV-1a hash of the counts; optionally the last step's slot -> parent map   */
+/* and every step's energies E_steps[S+1][R].                                 */
 /* ------------------------------------------------------------------------ */
 void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R,
                 uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                 double *lnQ_out, double *lnZ_out, int64_t *sumE_out, double *sumE2_out,
                 int64_t *sumAbsM_out, double *sumM2_out, uint64_t *counts_hash_out,
-                int64_t *E_final, int64_t *M_final, uint32_t *parents_last)
+                int64_t *E_final, int64_t *M_final, uint32_t *parents_last, int64_t *E_steps)
 {
     int64_t N = orc_nsites(dim, L);
     int64_t *E = (int64_t *)malloc(sizeof(int64_t) * R);
@@ -396,6 +397,7 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
             sAM += M[r] < 0 ? -M[r] : M[r];
             sM2 += (double)M[r] * (double)M[r];
         }
+        if (E_steps) memcpy(E_steps + (size_t)i * R, E, sizeof(int64_t) * R);
         if (lnQ_out) lnQ_out[i] = lnQ;
         if (lnZ_out) lnZ_out[i] = lnZ;
         if (sumE_out) sumE_out[i] = sE;

@@ -83,3 +83,26 @@ def dbeta_from_output(y: float, var: float, dbeta_max: float) -> float:
 
 def target_from_dbeta(dbeta: float, var: float) -> float:
     return math.log(dbeta * math.sqrt(max(var, 1e-12)))
+
+
+def choose_step(levels, counts, beta, L, R, N, dmax, target, params=None, lo=0.0, hi=1.0):
+    """One adaptive step: the MLP proposal (if params are given) kept when its
+    overlap lies in [lo, hi], else the bisection. Returns a dict with dbeta,
+    alpha, kind (1 bisection, 2 proposal), proposal, alpha_proposal, evals."""
+    from oracle import mlp
+
+    out = dict(proposal=0.0, alpha_proposal=0.0, evals=0)
+    _, var, _ = moments(levels, counts)
+    if params is not None:
+        x = features(levels, counts, beta, L, R, N)[None, :]
+        y, _ = mlp.forward(mlp.bf16_round(params), x)
+        prop = dbeta_from_output(float(y[0]), var, dmax)
+        a = overlap(levels, counts, prop)
+        out.update(proposal=prop, alpha_proposal=a, evals=1)
+        if lo <= a <= hi:
+            out.update(dbeta=prop, alpha=a, kind=2)
+            return out
+    d, clamped = bisect_dbeta(levels, counts, target, dmax)
+    out.update(dbeta=d, alpha=overlap(levels, counts, d), kind=1,
+               evals=out["evals"] + (1 if clamped else 1 + BISECT_ITERS))
+    return out

@@ -147,6 +147,16 @@ struct PaLat {
     int s_bits = 0;
     uint32_t pop0 = 0;                     // first population index
     uint32_t t_start = 0;
+    // adaptive schedules: weight tables of the current step in a 2-slot ring
+    bool ring = false;
+    double* hexp = nullptr;                // pinned host staging [2][nbins]
+    unsigned long long* hint = nullptr;
+    uint32_t steps = 0;                    // steps taken by this lattice
+    bool done = false;                     // reached beta_f
+    bool stepping = false;                 // takes part in the step being enqueued
+    double overlap = 0.0;                  // realised overlap of the last step
+    int32_t kind = 0;                      // how the last step was chosen
+    std::vector<gbmc_schedule_record> log;
 };
 
 }  // namespace
@@ -156,10 +166,15 @@ struct gbmc_pa {
     gbmc_pa_config cfg;
     std::vector<PaLat> lats;
     uint32_t P = 0;
-    uint32_t S = 0;        // steps of the schedule
-    uint32_t step = 0;     // steps done
+    uint32_t S = 0;        // steps of a fixed schedule; step cap of an adaptive one
+    uint32_t step = 0;     // steps enqueued
+    bool adaptive = false;
     gbmc_pa_stats* stats = nullptr;  // device [S+1][P]
+    SchedOut* sched_dev = nullptr;   // [kMaxJobs]
+    SchedOut* sched_host = nullptr;  // pinned copy
+    float* mlp_dev = nullptr;        // MLP parameters (GBMC_SCHED_MLP)
     std::vector<void*> allocs;
+    std::vector<void*> host_allocs;
 };
 
 namespace {
@@ -619,8 +634,9 @@ static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
     P.beta = pl.betas[step];
     P.dbeta = step == 0 ? 0.0 : pl.betas[step] - pl.betas[step - 1];
     if (step > 0) {
-        P.wexp = pl.wexp + (uint64_t)(step - 1) * pl.nbins;
-        P.wint = pl.wint + (uint64_t)(step - 1) * pl.nbins;
+        const uint64_t row = pl.ring ? (uint64_t)(step & 1u) : (uint64_t)(step - 1);
+        P.wexp = pl.wexp + row * pl.nbins;
+        P.wint = pl.wint + row * pl.nbins;
     }
     P.log_R = std::log((double)l->d.n_replicas);
     P.seed = l->d.seed;
@@ -631,27 +647,36 @@ static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
     P.nchunks = pl.nchunks;
     P.step = step;
     P.e_lo = pl.e_lo;
+    P.overlap = step == 0 ? 0.0 : pl.overlap;
+    P.kind = step == 0 ? 0 : pl.kind;
     return P;
 }
 
-// Sweep launch over every lattice of the run: nsweeps = theta with the
-// resampling gather (step > 0), or a measurement-only pass (step 0).
-static gbmc_status pa_sweep_launch(gbmc_pa* pa, uint32_t step) {
+// Sweep launch over the lattices taking part in this step: theta sweeps with
+// the resampling gather (step > 0), or a measurement-only pass (step 0).
+static gbmc_status pa_sweep_launch(gbmc_pa* pa, bool first) {
     SweepLaunch P;
     std::memset(&P, 0, sizeof(P));
     std::vector<const gbmc_lattice*> ls;
-    for (auto& pl : pa->lats) ls.push_back(pl.lat);
+    std::vector<PaLat*> act;
+    for (auto& pl : pa->lats)
+        if (pl.stepping) {
+            ls.push_back(pl.lat);
+            act.push_back(&pl);
+        }
+    if (act.empty()) return GBMC_OK;
     const std::vector<Tuning> tus = tune_batch(ls);
-    const gbmc_lattice* l0 = pa->lats[0].lat;
+    const gbmc_lattice* l0 = act[0]->lat;
     P.dim = l0->d.dim;
     P.ea = l0->d.model == GBMC_EA_PMJ;
     P.swar = 1;
-    for (size_t li = 0; li < pa->lats.size(); ++li) {
-        auto& pl = pa->lats[li];
+    for (size_t li = 0; li < act.size(); ++li) {
+        PaLat& pl = *act[li];
         gbmc_lattice* l = pl.lat;
         const Tuning& tu = tus[li];
         SweepJob J = base_job(l, tu);
         if (l->d.L % 8) P.swar = 0;
+        const uint32_t step = pl.steps;
         thresholds(pl.betas[step], J.thr);
         J.E = pl.E;
         J.M = pl.M;
@@ -659,7 +684,7 @@ static gbmc_status pa_sweep_launch(gbmc_pa* pa, uint32_t step) {
         J.emin = pl.emin;
         J.emax = pl.emax;
         J.sums = pl.sums;
-        if (step == 0) {
+        if (first) {
             J.nsweeps = 0;
             J.src = J.dst = l->cur;
         } else {
@@ -673,19 +698,20 @@ static gbmc_status pa_sweep_launch(gbmc_pa* pa, uint32_t step) {
     }
     gbmc_status st = launch_jobs(pa->ctx, P, tus);
     if (st != GBMC_OK) return st;
-    if (step > 0) {
-        for (int j = 0; j < P.njobs; ++j) {
-            gbmc_lattice* l = pa->lats[j].lat;
-            l->cur = P.jobs[j].dst;
-            l->t = pa->lats[j].t_start + step * pa->cfg.theta;
+    if (!first) {
+        for (size_t li = 0; li < act.size(); ++li) {
+            gbmc_lattice* l = act[li]->lat;
+            l->cur = P.jobs[li].dst;
+            l->t = act[li]->t_start + act[li]->steps * pa->cfg.theta;
         }
     }
     return GBMC_OK;
 }
 
-static gbmc_status pa_record(gbmc_pa* pa, uint32_t step) {
+static gbmc_status pa_record(gbmc_pa* pa) {
     for (auto& pl : pa->lats) {
-        PaLattice P = pa_params(pa, pl, step);
+        if (!pl.stepping) continue;
+        PaLattice P = pa_params(pa, pl, pl.steps);
         ProfScope ps_(pa->ctx, PK_PA_RECORD);
         CUDA_TRY(launch_pa_record(P, pl.lnZ, 0.0, pa->ctx->stream));
     }
@@ -696,6 +722,7 @@ static gbmc_status pa_record(gbmc_pa* pa, uint32_t step) {
 // and its measurement.
 static gbmc_status pa_begin(gbmc_pa* pa, int init) {
     cudaStream_t s = pa->ctx->stream;
+    CUDA_TRY(cudaMemsetAsync(pa->stats, 0, (uint64_t)(pa->S + 1) * pa->P * sizeof(gbmc_pa_stats), s));
     for (auto& pl : pa->lats) {
         gbmc_lattice* l = pl.lat;
         if (init) {
@@ -705,6 +732,13 @@ static gbmc_status pa_begin(gbmc_pa* pa, int init) {
                                        l->d.instance_base, l->d.seed, 1, s));
         }
         l->t = pl.t_start;
+        pl.steps = 0;
+        pl.done = false;
+        pl.stepping = true;
+        pl.overlap = 0.0;
+        pl.kind = 0;
+        pl.log.clear();
+        if (pa->adaptive) pl.betas.assign(1, 0.0);
         std::vector<double> z(2 * l->d.n_instances, 0.0);
         for (uint32_t k = 0; k < l->d.n_instances; ++k) z[k] = (double)l->N * std::log(2.0);
         CUDA_TRY(cudaMemcpyAsync(pl.lnZ, z.data(), z.size() * 8, cudaMemcpyHostToDevice, s));
@@ -714,19 +748,30 @@ static gbmc_status pa_begin(gbmc_pa* pa, int init) {
         CUDA_TRY(launch_pa_reset(P, s));
     }
     pa->step = 0;
-    gbmc_status st = pa_sweep_launch(pa, 0);
+    gbmc_status st = pa_sweep_launch(pa, true);
     if (st != GBMC_OK) return st;
-    return pa_record(pa, 0);
+    return pa_record(pa);
 }
 
 gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_lattices, const gbmc_pa_config* cfg,
                       gbmc_pa** out) {
     if (!ctx || !lattices || !cfg || !out) return fail(GBMC_ERR_ARG, "NULL argument");
     if (n_lattices == 0 || n_lattices > (uint32_t)kMaxJobs) return fail(GBMC_ERR_ARG, "1..%d lattices per run", kMaxJobs);
-    if (cfg->schedule != GBMC_SCHED_LINEAR && cfg->schedule != GBMC_SCHED_LIST)
-        return fail(GBMC_ERR_ARG, "schedule %d not supported by this build", cfg->schedule);
+    const int sched = cfg->schedule;
+    if (sched != GBMC_SCHED_LINEAR && sched != GBMC_SCHED_LIST && sched != GBMC_SCHED_BISECTION &&
+        sched != GBMC_SCHED_MLP)
+        return fail(GBMC_ERR_ARG, "unknown schedule %d", sched);
+    const bool adaptive = sched == GBMC_SCHED_BISECTION || sched == GBMC_SCHED_MLP;
     if (cfg->n_steps == 0) return fail(GBMC_ERR_ARG, "n_steps must be >= 1");
-    if (cfg->schedule == GBMC_SCHED_LIST && !cfg->betas) return fail(GBMC_ERR_ARG, "betas required for a list schedule");
+    if (cfg->theta == 0) return fail(GBMC_ERR_ARG, "theta must be >= 1");
+    if (sched == GBMC_SCHED_LIST && !cfg->betas) return fail(GBMC_ERR_ARG, "betas required for a list schedule");
+    if (sched == GBMC_SCHED_MLP && !cfg->mlp_params) return fail(GBMC_ERR_ARG, "mlp_params required for the MLP schedule");
+    if (adaptive) {
+        if (!(cfg->beta_f > 0.0) || !(cfg->dbeta_max > 0.0)) return fail(GBMC_ERR_ARG, "adaptive schedules need beta_f > 0 and dbeta_max > 0");
+        if (!(cfg->target_overlap > 0.0 && cfg->target_overlap < 1.0)) return fail(GBMC_ERR_ARG, "target_overlap must lie in (0, 1)");
+        if (sched == GBMC_SCHED_MLP && !(cfg->overlap_lo <= cfg->overlap_hi))
+            return fail(GBMC_ERR_ARG, "overlap_lo must not exceed overlap_hi");
+    }
     const gbmc_lattice* l0 = lattices[0];
     if (!l0) return fail(GBMC_ERR_ARG, "NULL lattice");
     CUDA_TRY(cudaSetDevice(ctx->device));
@@ -737,6 +782,8 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         if (l->run) return fail(GBMC_ERR_STATE, "lattice %u already in an annealing run", i);
         if (l->d.dim != l0->d.dim || l->d.model != l0->d.model)
             return fail(GBMC_ERR_ARG, "lattices of one run share dim and model");
+        if (adaptive && l->d.n_instances != 1)
+            return fail(GBMC_ERR_ARG, "adaptive schedules anneal one population per lattice (n_instances = 1)");
         for (uint32_t k = 0; k < i; ++k)
             if (lattices[k] == l) return fail(GBMC_ERR_ARG, "lattice %u listed twice", i);
         ls.push_back(l);
@@ -755,7 +802,9 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     pa->ctx = ctx;
     pa->cfg = *cfg;
     pa->cfg.betas = nullptr;
+    pa->cfg.mlp_params = nullptr;
     pa->S = cfg->n_steps;
+    pa->adaptive = adaptive;
     pa->lats.resize(n_lattices);
     gbmc_status st = GBMC_OK;
     uint32_t pop = 0;
@@ -766,6 +815,7 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         pl.pop0 = pop;
         pop += l->d.n_instances;
         pl.t_start = l->t;
+        pl.ring = adaptive;
         const uint32_t I = l->d.n_instances, R = l->d.n_replicas;
         const uint64_t C = (uint64_t)I * R;
         pl.nbins = (uint32_t)(l->d.dim * l->N / 2 + 1);
@@ -774,15 +824,18 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         int lg = 0;
         while ((1ull << lg) < R) ++lg;
         pl.s_bits = 63 - lg;
-        // schedule
-        pl.betas.resize(pa->S + 1);
-        for (uint32_t k = 0; k <= pa->S; ++k)
-            pl.betas[k] = cfg->schedule == GBMC_SCHED_LIST ? cfg->betas[k]
-                                                           : (cfg->beta_f * (double)k) / (double)pa->S;
-        if (pl.betas[0] != 0.0) st = fail(GBMC_ERR_ARG, "beta_0 must be 0");
-        for (uint32_t k = 1; k <= pa->S && st == GBMC_OK; ++k) {
-            if (!(pl.betas[k] >= pl.betas[k - 1]) || !beta_ok(pl.betas[k], l->d.dim))
-                st = fail(GBMC_ERR_ARG, "schedule must be non-decreasing with 0 <= 4*dim*beta <= 700");
+        if (!adaptive) {
+            pl.betas.resize(pa->S + 1);
+            for (uint32_t k = 0; k <= pa->S; ++k)
+                pl.betas[k] = sched == GBMC_SCHED_LIST ? cfg->betas[k] : (cfg->beta_f * (double)k) / (double)pa->S;
+            if (pl.betas[0] != 0.0) st = fail(GBMC_ERR_ARG, "beta_0 must be 0");
+            for (uint32_t k = 1; k <= pa->S && st == GBMC_OK; ++k) {
+                if (!(pl.betas[k] >= pl.betas[k - 1]) || !beta_ok(pl.betas[k], l->d.dim))
+                    st = fail(GBMC_ERR_ARG, "schedule must be non-decreasing with 0 <= 4*dim*beta <= 700");
+            }
+        } else {
+            pl.betas.assign(1, 0.0);
+            if (!beta_ok(cfg->beta_f, l->d.dim)) st = fail(GBMC_ERR_ARG, "beta_f out of range");
         }
         if (st != GBMC_OK) break;
         void* p;
@@ -818,27 +871,40 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         pl.parent = (uint32_t*)p;
         cudaError_t ce = cudaMemsetAsync(pl.counts, 0, C * 4, ctx->stream);
         if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "memset: %s", cudaGetErrorString(ce)); break; }
-        // fp64 weight tables of every step (Eq. (13)), host libm exp
-        const uint64_t tb = (uint64_t)pa->S * pl.nbins;
+        // fp64 weight tables (Eq. (13)), host libm exp: every step of a fixed
+        // schedule now; for adaptive schedules a 2-slot ring filled per step
+        const uint64_t tb = (adaptive ? 2ull : (uint64_t)pa->S) * pl.nbins;
         if ((st = dalloc(pa, &p, tb * 8)) != GBMC_OK) break;
         pl.wexp = (double*)p;
         if ((st = dalloc(pa, &p, tb * 8)) != GBMC_OK) break;
         pl.wint = (unsigned long long*)p;
-        std::vector<double> we(tb);
-        std::vector<unsigned long long> wi(tb);
-        for (uint32_t k = 1; k <= pa->S; ++k) {
-            const double dbeta = pl.betas[k] - pl.betas[k - 1];
-            double* row = we.data() + (uint64_t)(k - 1) * pl.nbins;
-            unsigned long long* irow = wi.data() + (uint64_t)(k - 1) * pl.nbins;
-            for (uint32_t b = 0; b < pl.nbins; ++b) {
-                const double w = std::exp(-(dbeta * (double)(4ll * b)));
-                row[b] = w;
-                irow[b] = (unsigned long long)std::floor(std::ldexp(w, pl.s_bits));
+        if (adaptive) {
+            void* hp = nullptr;
+            ce = cudaMallocHost(&hp, tb * 8);
+            if (ce != cudaSuccess) { st = fail(GBMC_ERR_OOM, "cudaMallocHost: %s", cudaGetErrorString(ce)); break; }
+            pa->host_allocs.push_back(hp);
+            pl.hexp = (double*)hp;
+            ce = cudaMallocHost(&hp, tb * 8);
+            if (ce != cudaSuccess) { st = fail(GBMC_ERR_OOM, "cudaMallocHost: %s", cudaGetErrorString(ce)); break; }
+            pa->host_allocs.push_back(hp);
+            pl.hint = (unsigned long long*)hp;
+        } else {
+            std::vector<double> we(tb);
+            std::vector<unsigned long long> wi(tb);
+            for (uint32_t k = 1; k <= pa->S; ++k) {
+                const double dbeta = pl.betas[k] - pl.betas[k - 1];
+                double* row = we.data() + (uint64_t)(k - 1) * pl.nbins;
+                unsigned long long* irow = wi.data() + (uint64_t)(k - 1) * pl.nbins;
+                for (uint32_t b = 0; b < pl.nbins; ++b) {
+                    const double w = std::exp(-(dbeta * (double)(4ll * b)));
+                    row[b] = w;
+                    irow[b] = (unsigned long long)std::floor(std::ldexp(w, pl.s_bits));
+                }
             }
+            ce = cudaMemcpy(pl.wexp, we.data(), tb * 8, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess) ce = cudaMemcpy(pl.wint, wi.data(), tb * 8, cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "table upload: %s", cudaGetErrorString(ce)); break; }
         }
-        ce = cudaMemcpy(pl.wexp, we.data(), tb * 8, cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess) ce = cudaMemcpy(pl.wint, wi.data(), tb * 8, cudaMemcpyHostToDevice);
-        if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "table upload: %s", cudaGetErrorString(ce)); break; }
     }
     if (st == GBMC_OK) {
         pa->P = pop;
@@ -846,8 +912,30 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         st = dalloc(pa, &p, (uint64_t)(pa->S + 1) * pa->P * sizeof(gbmc_pa_stats));
         if (st == GBMC_OK) pa->stats = (gbmc_pa_stats*)p;
     }
+    if (st == GBMC_OK && adaptive) {
+        void* p;
+        st = dalloc(pa, &p, kMaxJobs * sizeof(SchedOut));
+        if (st == GBMC_OK) pa->sched_dev = (SchedOut*)p;
+        if (st == GBMC_OK) {
+            cudaError_t ce = cudaMallocHost(&p, kMaxJobs * sizeof(SchedOut));
+            if (ce != cudaSuccess) st = fail(GBMC_ERR_OOM, "cudaMallocHost: %s", cudaGetErrorString(ce));
+            else {
+                pa->host_allocs.push_back(p);
+                pa->sched_host = (SchedOut*)p;
+            }
+        }
+        if (st == GBMC_OK && sched == GBMC_SCHED_MLP) {
+            st = dalloc(pa, &p, kMlpParams * sizeof(float));
+            if (st == GBMC_OK) {
+                pa->mlp_dev = (float*)p;
+                cudaError_t ce = cudaMemcpy(p, cfg->mlp_params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
+                if (ce != cudaSuccess) st = fail(GBMC_ERR_CUDA, "MLP upload: %s", cudaGetErrorString(ce));
+            }
+        }
+    }
     if (st != GBMC_OK) {
         for (void* p : pa->allocs) cudaFree(p);
+        for (void* p : pa->host_allocs) cudaFreeHost(p);
         delete pa;
         return st;
     }
@@ -871,6 +959,7 @@ gbmc_status pa_free(gbmc_pa* pa) {
         l->run = nullptr;
     }
     for (void* p : pa->allocs) cudaFree(p);
+    for (void* p : pa->host_allocs) cudaFreeHost(p);
     delete pa;
     return GBMC_OK;
 }
@@ -890,11 +979,13 @@ gbmc_status pa_populations(const gbmc_pa* pa, uint32_t* n) {
     return GBMC_OK;
 }
 
-static gbmc_status pa_enqueue_step(gbmc_pa* pa) {
-    const uint32_t i = pa->step + 1;
+// Resampling kernels, sweeps and the record of the step for every lattice
+// with `stepping` set (its next beta already appended to pl.betas).
+static gbmc_status pa_enqueue_common(gbmc_pa* pa) {
     cudaStream_t s = pa->ctx->stream;
     for (auto& pl : pa->lats) {
-        PaLattice P = pa_params(pa, pl, i);
+        if (!pl.stepping) continue;
+        PaLattice P = pa_params(pa, pl, pl.steps);
         {
             ProfScope ps_(pa->ctx, PK_PA_WEIGHTS);
             CUDA_TRY(launch_pa_weights(P, s));
@@ -912,21 +1003,131 @@ static gbmc_status pa_enqueue_step(gbmc_pa* pa) {
             CUDA_TRY(launch_pa_place(P, s));
         }
     }
-    gbmc_status st = pa_sweep_launch(pa, i);
+    gbmc_status st = pa_sweep_launch(pa, false);
     if (st != GBMC_OK) return st;
-    st = pa_record(pa, i);
+    st = pa_record(pa);
     if (st != GBMC_OK) return st;
-    pa->step = i;
+    ++pa->step;
     return GBMC_OK;
+}
+
+static gbmc_status pa_enqueue_fixed(gbmc_pa* pa) {
+    for (auto& pl : pa->lats) {
+        pl.stepping = true;
+        ++pl.steps;
+    }
+    return pa_enqueue_common(pa);
+}
+
+// Smallest step an adaptive schedule takes (guards against a target overlap
+// that no positive step reaches).
+constexpr double kMinStep = 1e-7;
+
+static gbmc_status pa_enqueue_adaptive(gbmc_pa* pa, const double* beta_next) {
+    cudaStream_t s = pa->ctx->stream;
+    std::vector<PaLat*> act;
+    for (auto& pl : pa->lats) {
+        pl.stepping = !pl.done;
+        if (pl.stepping) act.push_back(&pl);
+    }
+    if (act.empty()) return fail(GBMC_ERR_STATE, "every lattice has reached beta_f");
+    if (pa->step >= pa->S) return fail(GBMC_ERR_STATE, "step cap of %u reached", pa->S);
+    if (!beta_next) {
+        SchedLaunch S;
+        std::memset(&S, 0, sizeof(S));
+        for (PaLat* pl : act) {
+            SchedJob& J = S.jobs[S.njobs++];
+            J.hist = pl->hist;
+            J.emin = pl->emin;
+            J.emax = pl->emax;
+            J.e_lo = pl->e_lo;
+            J.nbins = pl->nbins;
+            J.R = pl->lat->d.n_replicas;
+            J.N = (uint32_t)pl->lat->N;
+            J.L = (uint32_t)pl->lat->d.L;
+            J.beta = pl->betas.back();
+            const double rest = pa->cfg.beta_f - J.beta;
+            J.dmax = pa->cfg.dbeta_max < rest ? pa->cfg.dbeta_max : rest;
+        }
+        S.out = pa->sched_dev;
+        S.mlp = pa->cfg.schedule == GBMC_SCHED_MLP ? pa->mlp_dev : nullptr;
+        S.target = pa->cfg.target_overlap;
+        S.lo = pa->cfg.overlap_lo;
+        S.hi = pa->cfg.overlap_hi;
+        S.mode = pa->cfg.schedule == GBMC_SCHED_MLP ? 2 : 1;
+        CUDA_TRY(launch_schedule(S, s));
+        CUDA_TRY(cudaMemcpyAsync(pa->sched_host, pa->sched_dev, S.njobs * sizeof(SchedOut), cudaMemcpyDeviceToHost, s));
+    }
+    // the staging slot written below was last read two steps ago
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t j = 0; j < act.size(); ++j) {
+        PaLat& pl = *act[j];
+        gbmc_lattice* l = pl.lat;
+        const double beta = pl.betas.back();
+        gbmc_schedule_record rec;
+        std::memset(&rec, 0, sizeof(rec));
+        double bnew;
+        uint32_t kmax = pl.nbins - 1;
+        if (beta_next) {
+            const size_t li = (size_t)(&pl - pa->lats.data());
+            bnew = beta_next[li];
+            if (!(bnew > beta) || !beta_ok(bnew, l->d.dim)) return fail(GBMC_ERR_ARG, "beta_next[%zu] must exceed the current beta", li);
+            if (bnew > pa->cfg.beta_f) bnew = pa->cfg.beta_f;
+            rec.kind = 0;
+        } else {
+            const SchedOut& o = pa->sched_host[j];
+            double d = o.dbeta > kMinStep ? o.dbeta : kMinStep;
+            bnew = beta + d;
+            if (pa->cfg.beta_f - bnew <= 1e-12 * (pa->cfg.beta_f > 1.0 ? pa->cfg.beta_f : 1.0)) bnew = pa->cfg.beta_f;
+            rec.alpha = o.alpha;
+            rec.proposal = o.proposal;
+            rec.alpha_proposal = o.alpha_proposal;
+            rec.var = o.var;
+            for (int i = 0; i < 6; ++i) rec.features[i] = o.feat[i];
+            rec.kind = o.kind;
+            rec.clamped = o.clamped;
+            rec.evals = o.evals;
+            kmax = (uint32_t)((o.emax - o.emin) >> 2);
+        }
+        rec.beta = bnew;
+        rec.dbeta = bnew - beta;
+        pl.betas.push_back(bnew);
+        ++pl.steps;
+        if (bnew >= pa->cfg.beta_f) pl.done = true;
+        pl.overlap = rec.alpha;
+        pl.kind = rec.kind;
+        pl.log.push_back(rec);
+        // weight tables of this step (Eq. (13)), host libm exp, into the ring
+        const double dbeta = rec.dbeta;
+        const uint64_t slot = (uint64_t)(pl.steps & 1u) * pl.nbins;
+        for (uint32_t b = 0; b <= kmax; ++b) {
+            const double w = std::exp(-(dbeta * (double)(4ll * b)));
+            pl.hexp[slot + b] = w;
+            pl.hint[slot + b] = (unsigned long long)std::floor(std::ldexp(w, pl.s_bits));
+        }
+        CUDA_TRY(cudaMemcpyAsync(pl.wexp + slot, pl.hexp + slot, (uint64_t)(kmax + 1) * 8, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pl.wint + slot, pl.hint + slot, (uint64_t)(kmax + 1) * 8, cudaMemcpyHostToDevice, s));
+    }
+    return pa_enqueue_common(pa);
+}
+
+static bool pa_finished(const gbmc_pa* pa) {
+    if (pa->adaptive) {
+        if (pa->step >= pa->S) return true;
+        for (auto& pl : pa->lats)
+            if (!pl.done) return false;
+        return true;
+    }
+    return pa->step >= pa->S;
 }
 
 gbmc_status pa_step(gbmc_ctx* ctx, gbmc_pa* pa, const double* beta_next, gbmc_pa_stats* out_host) {
     if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
-    if (pa->step >= pa->S) return fail(GBMC_ERR_STATE, "schedule finished after %u steps", pa->S);
-    if (beta_next) return fail(GBMC_ERR_ARG, "explicit beta_next needs an adaptive schedule");
+    if (!pa->adaptive && pa->step >= pa->S) return fail(GBMC_ERR_STATE, "schedule finished after %u steps", pa->S);
+    if (beta_next && !pa->adaptive) return fail(GBMC_ERR_ARG, "explicit beta_next needs an adaptive schedule");
     pa->ctx = ctx;
     CUDA_TRY(cudaSetDevice(ctx->device));
-    gbmc_status st = pa_enqueue_step(pa);
+    gbmc_status st = pa->adaptive ? pa_enqueue_adaptive(pa, beta_next) : pa_enqueue_fixed(pa);
     if (st != GBMC_OK) return st;
     if (out_host) {
         CUDA_TRY(cudaMemcpyAsync(out_host, pa->stats + (uint64_t)pa->step * pa->P, pa->P * sizeof(gbmc_pa_stats),
@@ -940,8 +1141,8 @@ gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32
     if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
     pa->ctx = ctx;
     CUDA_TRY(cudaSetDevice(ctx->device));
-    while (pa->step < pa->S) {
-        gbmc_status st = pa_enqueue_step(pa);
+    while (!pa_finished(pa)) {
+        gbmc_status st = pa->adaptive ? pa_enqueue_adaptive(pa, nullptr) : pa_enqueue_fixed(pa);
         if (st != GBMC_OK) return st;
     }
     if (stats_host) {
@@ -951,6 +1152,29 @@ gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (n_done) *n_done = pa->step;
+    return GBMC_OK;
+}
+
+gbmc_status pa_schedule_log(const gbmc_pa* pa, uint32_t lattice, gbmc_schedule_record* out, uint32_t capacity,
+                            uint32_t* n_out) {
+    if (!pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (lattice >= pa->lats.size()) return fail(GBMC_ERR_ARG, "lattice index out of range");
+    const auto& log = pa->lats[lattice].log;
+    const uint32_t n = (uint32_t)log.size();
+    if (out)
+        for (uint32_t i = 0; i < n && i < capacity; ++i) out[i] = log[i];
+    if (n_out) *n_out = n;
+    return GBMC_OK;
+}
+
+gbmc_status pa_betas(const gbmc_pa* pa, uint32_t lattice, double* out, uint32_t capacity, uint32_t* n_out) {
+    if (!pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (lattice >= pa->lats.size()) return fail(GBMC_ERR_ARG, "lattice index out of range");
+    const PaLat& pl = pa->lats[lattice];
+    const uint32_t n = pa->adaptive ? (uint32_t)pl.betas.size() : pl.steps + 1;
+    if (out)
+        for (uint32_t i = 0; i < n && i < capacity; ++i) out[i] = pl.betas[i];
+    if (n_out) *n_out = n;
     return GBMC_OK;
 }
 
@@ -1071,6 +1295,66 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     out->ms_per_sweep = best / (2.0 * n_sweeps);
     out->n_candidates = n_cand;
     return GBMC_OK;
+}
+
+// ------------------------------------------------------------------------
+// Schedule MLP
+// ------------------------------------------------------------------------
+
+uint32_t gbmc_mlp_param_count(void) { return (uint32_t)kMlpParams; }
+
+gbmc_status mlp_forward(gbmc_ctx* ctx, const float* params, const float* X, uint32_t B, float* Y) {
+    if (!ctx || !params || !X || !Y) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (B == 0) return GBMC_OK;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(launch_mlp_forward(params, X, B, Y, ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status mlp_grad(gbmc_ctx* ctx, const float* params, const float* X, const float* T, uint32_t B, float* grad,
+                     float* loss) {
+    if (!ctx || !params || !X || !T || !grad || !loss) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (B == 0 || B > kMlpMaxBatch) return fail(GBMC_ERR_ARG, "batch must be 1..%u", kMlpMaxBatch);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(launch_mlp_grad(params, X, T, B, grad, loss, ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status mlp_adam(gbmc_ctx* ctx, float* params, const float* grad, float* m, float* v, uint32_t k, float lr) {
+    if (!ctx || !params || !grad || !m || !v) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (k == 0) return fail(GBMC_ERR_ARG, "Adam step count starts at 1");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(launch_mlp_adam(params, grad, m, v, k, lr, ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status mlp_train(gbmc_ctx* ctx, float* params, const float* X, const float* T, uint32_t n, uint32_t epochs,
+                      uint32_t batch, float lr, float* loss_out) {
+    if (!ctx || !params || !X || !T) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (n == 0 || epochs == 0) return GBMC_OK;
+    if (batch == 0 || batch > kMlpMaxBatch) return fail(GBMC_ERR_ARG, "batch must be 1..%u", kMlpMaxBatch);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    float* work = nullptr;  // grad, m, v
+    CUDA_TRY(cudaMallocAsync((void**)&work, 3 * kMlpParams * sizeof(float) + 16, s));
+    float* g = work;
+    float* m = work + kMlpParams;
+    float* v = work + 2 * kMlpParams;
+    gbmc_status st = GBMC_OK;
+    cudaError_t e = cudaMemsetAsync(m, 0, 2 * kMlpParams * sizeof(float), s);
+    uint32_t k = 0;
+    const uint32_t nb = (n + batch - 1) / batch;
+    for (uint32_t ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        for (uint32_t bi = 0; bi < nb && e == cudaSuccess; ++bi) {
+            const uint32_t b0 = bi * batch, B = (n - b0) < batch ? (n - b0) : batch;
+            float* lp = loss_out ? loss_out + (uint64_t)ep * nb + bi : work + 3 * kMlpParams;
+            e = launch_mlp_grad(params, X + (uint64_t)b0 * kMlpIn, T + b0, B, g, lp, s);
+            if (e == cudaSuccess) e = launch_mlp_adam(params, g, m, v, ++k, lr, s);
+        }
+    }
+    if (e != cudaSuccess) st = fail(GBMC_ERR_CUDA, "mlp_train: %s", cudaGetErrorString(e));
+    cudaFreeAsync(work, s);
+    return st;
 }
 
 }  // extern "C"

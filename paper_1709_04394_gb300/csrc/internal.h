@@ -91,9 +91,11 @@ struct PaLattice {
     uint32_t* parent;         // [n_inst*R] out: source replica of each slot
     void* stats;              // gbmc_pa_stats [n_inst] record of this step (device)
     double dbeta, beta, log_R, lnZ0;
+    double overlap;           // realised overlap of an adaptive step (recorded)
     uint64_t seed;
     uint32_t R, n_inst, inst_base, nbins, nchunks, step;
     int32_t e_lo;
+    int32_t kind;             // how the step was chosen (recorded)
 };
 
 constexpr uint32_t kScanChunk = 2048;  // replicas per resampling chunk (512 threads x 4)
@@ -104,5 +106,58 @@ cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_record(const PaLattice& P, const double* lnZ, double lnQ_unused, cudaStream_t s);
 cudaError_t launch_pa_reset(const PaLattice& P, cudaStream_t s);
+
+// ---- schedule MLP (6 -> 64 -> 64 -> 1) ----
+constexpr int kMlpIn = 6;
+constexpr int kMlpHidden = 64;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpHidden * kMlpIn;
+constexpr int kOffW2 = kOffB1 + kMlpHidden;
+constexpr int kOffB2 = kOffW2 + kMlpHidden * kMlpHidden;
+constexpr int kOffW3 = kOffB2 + kMlpHidden;
+constexpr int kOffB3 = kOffW3 + kMlpHidden;
+constexpr int kMlpParams = kOffB3 + 1;  // 4673
+constexpr uint32_t kMlpMaxBatch = 128;
+
+cudaError_t launch_mlp_forward(const float* p, const float* X, uint32_t B, float* Y, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* p, const float* X, const float* T, uint32_t B, float* g, float* loss,
+                            cudaStream_t s);
+cudaError_t launch_mlp_adam(float* p, const float* g, float* m, float* v, uint32_t k, float lr, cudaStream_t s);
+
+// ---- adaptive annealing steps: overlap bisection and MLP proposals ----
+// One population per lattice (n_instances == 1).
+struct SchedJob {
+    const uint32_t* hist;     // [nbins] energy histogram of the current population
+    const int32_t* emin;
+    const int32_t* emax;
+    int32_t e_lo;
+    uint32_t nbins, R, N, L;
+    double beta, dmax;        // current beta; largest allowed step (<= beta_f - beta)
+};
+
+struct SchedOut {             // result per lattice (device, copied to the host)
+    double dbeta;             // chosen step
+    double alpha;             // realised overlap of the chosen step
+    double proposal;          // MLP proposal (0 in bisection mode)
+    double alpha_proposal;    // overlap of the proposal
+    double var;               // population variance of E
+    float feat[6];            // MLP inputs
+    int32_t kind;             // 1 bisection, 2 accepted MLP proposal
+    int32_t clamped;          // 1: the step hit dmax
+    int32_t evals;            // overlap evaluations spent
+    int32_t emin, emax;
+    int32_t pad;
+};
+
+struct SchedLaunch {
+    SchedJob jobs[kMaxJobs];
+    SchedOut* out;            // [njobs]
+    const float* mlp;         // fp32 master parameters, or null (bisection only)
+    double target, lo, hi;    // bisection target; MLP acceptance band
+    int32_t njobs;
+    int32_t mode;             // 1 bisection, 2 MLP with bisection fallback
+};
+
+cudaError_t launch_schedule(const SchedLaunch& S, cudaStream_t s);
 
 }  // namespace gbmc

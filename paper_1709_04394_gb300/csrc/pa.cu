@@ -234,8 +234,8 @@ __global__ void k_pa_record(const __grid_constant__ PaLattice P, const double* l
     st->Emax = P.emax[inst];
     st->step = P.step;
     st->n_replicas = P.R;
-    st->overlap = 0.0;
-    st->proposal_kind = 0;
+    st->overlap = P.overlap;
+    st->proposal_kind = P.kind;
     st->pad = 0;
 }
 

@@ -42,6 +42,12 @@ class Tuning(C.Structure):
                 ("pad", C.c_uint32)]
 
 
+class ScheduleRecord(C.Structure):
+    _fields_ = [("beta", C.c_double), ("dbeta", C.c_double), ("alpha", C.c_double), ("proposal", C.c_double),
+                ("alpha_proposal", C.c_double), ("var", C.c_double), ("features", C.c_float * 6),
+                ("kind", C.c_int32), ("clamped", C.c_int32), ("evals", C.c_int32), ("pad", C.c_int32)]
+
+
 class LatticeDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("L", C.c_int32), ("model", C.c_int32), ("layout", C.c_int32),
                 ("start", C.c_int32), ("n_instances", C.c_uint32), ("n_replicas", C.c_uint32),
@@ -108,6 +114,13 @@ def load():
             "observables": ([p, p, p, p], st),
             "gbmc_autotune": ([p, p, C.c_double, C.c_uint32, C.POINTER(Tuning)], st),
             "gbmc_set_tuning": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tuning)], st),
+            "pa_schedule_log": ([p, C.c_uint32, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
+            "pa_betas": ([p, C.c_uint32, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
+            "gbmc_mlp_param_count": ([], C.c_uint32),
+            "mlp_forward": ([p, p, p, C.c_uint32, p], st),
+            "mlp_grad": ([p, p, p, p, C.c_uint32, p, p], st),
+            "mlp_adam": ([p, p, p, p, p, C.c_uint32, C.c_float], st),
+            "mlp_train": ([p, p, p, p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_float, p], st),
             "pa_resample_static": ([p, C.c_int32, C.c_int32, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32,
                                     C.c_uint64, C.c_uint32, C.c_double, p, p, p], st),
             "pa_create": ([p, C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(PaConfig), C.POINTER(C.c_void_p)], st),
@@ -328,3 +341,46 @@ def pa_resample_static(stream, device, dim, n_sites, n_instances, n_replicas, in
     """Allocation-free resampling step (static device scratch); see include/gbmc.h."""
     _check(load().pa_resample_static(stream, device, dim, n_sites, n_instances, n_replicas, instance_base, seed,
                                      step, float(dbeta), _ptr(E), _ptr(parent), _ptr(lnQ)))
+
+
+def pa_schedule_log(pa, lattice=0) -> list:
+    """Per-step records of an adaptive schedule (dicts)."""
+    n = C.c_uint32()
+    _check(load().pa_schedule_log(pa, lattice, None, 0, C.byref(n)))
+    arr = (ScheduleRecord * max(1, n.value))()
+    _check(load().pa_schedule_log(pa, lattice, C.cast(arr, C.c_void_p), n.value, C.byref(n)))
+    out = []
+    for i in range(n.value):
+        r = arr[i]
+        out.append({k: (list(getattr(r, k)) if k == "features" else getattr(r, k))
+                    for k, _ in ScheduleRecord._fields_ if k != "pad"})
+    return out
+
+
+def pa_betas(pa, lattice=0) -> np.ndarray:
+    n = C.c_uint32()
+    _check(load().pa_betas(pa, lattice, None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=np.float64)
+    _check(load().pa_betas(pa, lattice, _ptr(out), n.value, C.byref(n)))
+    return out
+
+
+def gbmc_mlp_param_count() -> int:
+    return int(load().gbmc_mlp_param_count())
+
+
+def mlp_forward(ctx, params, X, Y):
+    _check(load().mlp_forward(ctx, _ptr(params), _ptr(X), X.shape[0], _ptr(Y)))
+
+
+def mlp_grad(ctx, params, X, T, grad, loss):
+    _check(load().mlp_grad(ctx, _ptr(params), _ptr(X), _ptr(T), X.shape[0], _ptr(grad), _ptr(loss)))
+
+
+def mlp_adam(ctx, params, grad, m, v, k, lr):
+    _check(load().mlp_adam(ctx, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), k, float(lr)))
+
+
+def mlp_train(ctx, params, X, T, epochs, batch, lr, loss_out=None):
+    _check(load().mlp_train(ctx, _ptr(params), _ptr(X), _ptr(T), X.shape[0], epochs, batch, float(lr),
+                            _ptr(loss_out)))
