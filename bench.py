@@ -38,6 +38,25 @@ SM_MAX_MHZ = 2070.0
 ALG_INT_OPS_PER_SITE_UPDATE = 20.0
 
 
+def recorded_traffic(kernel_files, replicas):
+    """DRAM bytes per launch from the committed ncu record, or None if the
+    kernel sources changed since the counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_resident_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in rec["source_files"]:
+            with open(os.path.join(ROOT, name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["traffic_bytes_per_replica"] * replicas
+    except Exception:
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -342,7 +361,10 @@ def main():
         "config": config,
         "replica_sweeps_per_s": (ws * w["R"] * w["theta"] * w["S"] * args.steps / (ms * 1e-3)) if w["kind"] == "pa" else None,
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu,
+                     "traffic": recorded_traffic(None, w["R"]) if w["kind"] == "pa" else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                     "scaled by replicas from profiles/sweep_resident_traffic.json)",
                      "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction "
                                     "per SMSP per cycle)",
                      "alg_ops_per_site_update": ALG_INT_OPS_PER_SITE_UPDATE,
