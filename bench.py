@@ -153,15 +153,29 @@ def max_over_ranks(dist, ws, value, device=None):
 # ----------------------------------------------------------------------------
 # workloads
 # ----------------------------------------------------------------------------
+FM, EA = 0, 1
 WORKLOADS = {
-    "pa-ising2d-L64": dict(kind="pa", dim=2, L=64, R=100000, S=100, theta=10, beta_f=1.0),
+    # population annealing 2D Ising L=64, R=10^5, beta 0->1 in 101 temperatures, theta=10
+    "pa-ising2d-L64": dict(kind="pa", lattices=[(2, 64, FM, 1, 100000)], S=100, theta=10, beta_f=1.0),
+    # single 2D Ising lattice L=4096 at beta=0.4406868, 1000 sweeps per step
     "ising2d-L4096": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868),
+    # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
+    "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
+    # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
+    "pa-mixed-2d": dict(kind="pa", lattices=[(2, 32, FM, 1, 100000), (2, 64, FM, 1, 50000),
+                                             (2, 128, FM, 1, 20000), (2, 256, FM, 1, 10000)],
+                        S=100, theta=10, beta_f=1.0),
 }
+
+
+def copies(lat):
+    dim, L, model, I, R = lat
+    return I * R
 
 
 def site_updates_per_step(w):
     if w["kind"] == "pa":
-        return w["R"] * w["L"] ** w["dim"] * w["theta"] * w["S"]
+        return sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"] * w["S"]
     return w["L"] ** w["dim"] * w["sweeps"]
 
 
@@ -170,29 +184,35 @@ def run_gpu(args, w, ws, rank, local):
 
     from paper_1709_04394_gb300 import build as gbuild
     from paper_1709_04394_gb300 import gbmc
+    from paper_1709_04394_gb300 import inputs
 
     torch.cuda.set_device(local)
     dist = init_dist(ws, "nccl")
     gbuild.build()
     stream = torch.cuda.current_stream()
     ctx = gbmc.gbmc_create(local, stream.cuda_stream)
-    N = w["L"] ** w["dim"]
     seed0 = 1000003 * (rank + 1)
     result = {}
     if w["kind"] == "pa":
-        R = w["R"]
-        spins = torch.empty(R * N, dtype=torch.int8, device="cuda")
-        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=R, seed=seed0, instance_base=rank, spins=spins)
-        tuned = gbmc.gbmc_autotune(ctx, lat, 0.5 * w["beta_f"], w["theta"])
-        result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
-                            "row_walk": tuned.row_walk, "candidates": tuned.n_candidates}
-        pa = gbmc.pa_create(ctx, [lat], w["theta"], w["S"], beta_f=w["beta_f"], init=True)
+        lats, bufs = [], []
+        for i, (dim, L, model, I, R) in enumerate(w["lattices"]):
+            buf = torch.empty(I * R * L ** dim, dtype=torch.int8, device="cuda")
+            bufs.append(buf)
+            lats.append(gbmc.lattice_init(ctx, dim, L, model=model, n_instances=I, n_replicas=R, seed=seed0,
+                                          instance_base=(rank * len(w["lattices"]) + i) * 64, spins=buf))
+        if len(lats) == 1:
+            tuned = gbmc.gbmc_autotune(ctx, lats[0], 0.5 * w["beta_f"], w["theta"])
+            result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
+                                "row_walk": tuned.row_walk, "candidates": tuned.n_candidates}
+        pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True)
 
         def step(k):
             gbmc.pa_reset(ctx, pa, True, seed0 + k)
             gbmc.pa_run(ctx, pa)
     else:
+        N = w["L"] ** w["dim"]
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0)
+        lats = [lat]
 
         def step(k):
             gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
@@ -222,63 +242,63 @@ def run_gpu(args, w, ws, rank, local):
     ms = max_over_ranks(dist, ws, ms_local, device="cuda")
     result.update(ms=ms, prof=prof, launches=launches, clocks=clocks)
 
-    # end-to-end through the C ABI with host buffers: host population in,
-    # annealing run, host population and statistics out, every step.
-    if w["kind"] == "pa":
-        R = w["R"]
-        host_in = torch.empty(R * N, dtype=torch.int8, pin_memory=True)
-        host_out = torch.empty(R * N, dtype=torch.int8, pin_memory=True)
-        from paper_1709_04394_gb300 import inputs
-
-        host_in.numpy()[:] = inputs.random_spins(R * N, seed=seed0 + 77)
-        n_e2e = max(1, min(args.steps, 3))
-        stats_bytes = 0
-        barrier(dist, ws)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(n_e2e):
-            gbmc.lattice_copy_in(ctx, lat, host_in)
+    # end-to-end through the C ABI with host buffers: the population comes in
+    # from pinned host memory, and the final population and statistics go back,
+    # every step.
+    n_e2e = max(1, min(args.steps, 3))
+    hosts_in, hosts_out = [], []
+    for i, l in enumerate(lats):
+        nb = gbmc.lattice_info(l).spin_bytes
+        hin = torch.empty(nb, dtype=torch.int8, pin_memory=True)
+        hin.numpy()[:] = inputs.random_spins(nb, seed=seed0 + 77 + i)
+        hosts_in.append(hin)
+        hosts_out.append(torch.empty(nb, dtype=torch.int8, pin_memory=True))
+    h2d = sum(h.numel() for h in hosts_in)
+    d2h = sum(h.numel() for h in hosts_out)
+    barrier(dist, ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        for l, hin in zip(lats, hosts_in):
+            gbmc.lattice_copy_in(ctx, l, hin)
+        if w["kind"] == "pa":
             gbmc.pa_reset(ctx, pa, False, seed0 + 500 + k)
             stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
-            gbmc.lattice_copy_out(ctx, lat, host_out)
-            stats_bytes = stats.nbytes
-        t_e2e = time.perf_counter() - t0
-        t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
-        result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=R * N, d2h=R * N + stats_bytes, steps=n_e2e)
+            d2h_stats = stats.nbytes
+        else:
+            gbmc.metropolis_sweeps(ctx, lats[0], w["beta"], w["sweeps"])
+            d2h_stats = 0
+        for l, hout in zip(lats, hosts_out):
+            gbmc.lattice_copy_out(ctx, l, hout)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
+    result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e)
+    if w["kind"] == "pa":
         gbmc.pa_free(pa)
-    else:
-        host = torch.empty(N, dtype=torch.int8, pin_memory=True)
-        host.numpy()[:] = __import__("paper_1709_04394_gb300.inputs", fromlist=["x"]).random_spins(N, seed=seed0)
-        n_e2e = max(1, min(args.steps, 3))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(n_e2e):
-            gbmc.lattice_copy_in(ctx, lat, host)
-            gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
-            gbmc.lattice_copy_out(ctx, lat, host)
-        t_e2e = (time.perf_counter() - t0)
-        t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
-        result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=N, d2h=N, steps=n_e2e)
-    gbmc.lattice_free(lat)
+    for l in lats:
+        gbmc.lattice_free(l)
     gbmc.gbmc_destroy(ctx)
     return result
 
 
-def cpu_oracle_sample(w, target_s=12.0):
+def cpu_oracle_sample(w):
     """Time the CPU oracle (single thread, as it stands) on a bounded sample of
     the workload; returns (site updates per ns, description, seconds)."""
     import oracle
 
     oracle.build()
     if w["kind"] == "pa":
-        R, steps = 1000, 3
+        dim, L, model, I, R = w["lattices"][0]
+        Rs = max(1, min(R, (120_000_000 // (L ** dim * w["theta"] * 3))))
+        steps = 3
         betas = oracle.linear_betas(w["beta_f"], w["S"])[: steps + 1]
+        J = oracle.couplings(L, 1, 0) if model == EA else None
         t0 = time.perf_counter()
-        oracle.pa_run(w["dim"], w["L"], 1, 0, R, betas, w["theta"])
+        oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J)
         dt = time.perf_counter() - t0
-        upd = R * w["L"] ** w["dim"] * w["theta"] * steps
-        desc = "oracle pa_run: L=%d, R=%d replicas (of %d), first %d of %d temperature steps, theta=%d" % (
-            w["L"], R, w["R"], steps, w["S"], w["theta"])
+        upd = Rs * L ** dim * w["theta"] * steps
+        desc = "oracle pa_run: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
+               "theta=%d" % (dim, L, Rs, R, steps, w["S"], w["theta"])
     else:
         n = 2
         s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
@@ -343,8 +363,8 @@ def main():
     n_l, t_l = prof.get(kname, (0, 0.0))
     avg_ms = t_l / n_l if n_l else float("nan")
     if w["kind"] == "pa":
-        upd_per_launch = w["R"] * w["L"] ** w["dim"] * w["theta"]
-        hbm_bytes_per_launch = 2 * w["R"] * w["L"] ** w["dim"] + 12 * w["R"]
+        upd_per_launch = sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"]
+        hbm_bytes_per_launch = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
     else:
         upd_per_launch = w["L"] ** w["dim"] // 2
         hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 2
@@ -359,10 +379,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8 spins / int32 energies / f64 weights", "data": "synthetic",
         "config": config,
-        "replica_sweeps_per_s": (ws * w["R"] * w["theta"] * w["S"] * args.steps / (ms * 1e-3)) if w["kind"] == "pa" else None,
+        "replica_sweeps_per_s": (ws * sum(copies(l) for l in w["lattices"]) * w["theta"] * w["S"] * args.steps
+                                 / (ms * 1e-3)) if w["kind"] == "pa" else None,
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
                      "frac": achieved / peak_alu,
-                     "traffic": recorded_traffic(None, w["R"]) if w["kind"] == "pa" else None,
+                     "traffic": recorded_traffic(None, copies(w["lattices"][0]))
+                     if args.workload == "pa-ising2d-L64" else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                      "scaled by replicas from profiles/sweep_resident_traffic.json)",
                      "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction "
@@ -378,10 +400,7 @@ def main():
         "clocks": clk,
     }
     e = res["e2e"]
-    if w["kind"] == "pa":
-        e2e_upd = w["R"] * w["L"] ** w["dim"] * w["theta"] * w["S"]
-    else:
-        e2e_upd = upd
+    e2e_upd = upd
     line["e2e"] = {"value": ws * e2e_upd / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"]}
     if not args.no_cpu_baseline:

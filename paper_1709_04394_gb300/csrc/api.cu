@@ -48,11 +48,14 @@ std::atomic<uint64_t> g_launches{0};
 
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
-    PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_COUNT
+    PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
-                                          "pa_record", "pa_reset"};
+                                          "pa_record", "pa_reset", "sweep_tiles", "schedule"};
+
+// Interior size of the tiles of large 2D lattices (window = kTile + 16).
+constexpr uint32_t kTile = 128;
 
 }  // namespace
 
@@ -122,6 +125,7 @@ struct gbmc_lattice {
     int8_t* cur;       // buffer holding the current configuration
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
     uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
+    int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
     uint32_t t;        // sweep counter
     gbmc_pa* run;      // annealing run using this lattice
 };
@@ -505,6 +509,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->owns_spins) cudaFree(l->spins);
     if (l->jbits) cudaFree(l->jbits);
     if (l->jsplit) cudaFree(l->jsplit);
+    if (l->alt) cudaFree(l->alt);
     delete l;
     return GBMC_OK;
 }
@@ -583,17 +588,55 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
         P.swar = (l->d.L % 8) == 0;
         gbmc_status st = launch_jobs(ctx, P, std::vector<Tuning>{tu});
         if (st != GBMC_OK) return st;
+    } else if (l->d.dim == 2 && l->d.model == GBMC_ISING_FM && l->d.L % kTile == 0) {
+        // large 2D lattices: shared-memory tiles with halos, up to 4 sweeps per launch
+        if (!l->alt) {
+            cudaError_t e = cudaMalloc(&l->alt, l->N * l->ncopies);
+            if (e != cudaSuccess) return fail(GBMC_ERR_OOM, "cudaMalloc(second buffer): %s", cudaGetErrorString(e));
+        }
+        TileLaunch TL;
+        std::memset(&TL, 0, sizeof(TL));
+        TL.seed = l->d.seed;
+        TL.L = (uint32_t)l->d.L;
+        TL.T = kTile;
+        TL.R = l->d.n_replicas;
+        TL.inst_base = l->d.instance_base;
+        TL.thr[0] = J.thr[0];
+        TL.thr[1] = J.thr[1];
+        const uint32_t chunk = (E_series || M_series) ? 1u : 4u;
+        for (uint32_t s = 0; s < n_sweeps; s += chunk) {
+            TL.src = l->cur;
+            TL.dst = l->cur == l->spins ? l->alt : l->spins;
+            TL.t0 = l->t + s;
+            TL.nsweeps = (n_sweeps - s) < chunk ? (n_sweeps - s) : chunk;
+            {
+                ProfScope ps_(ctx, PK_SWEEP_TILES);
+                CUDA_TRY(launch_sweep_tiles(TL, l->ncopies, ctx->stream));
+            }
+            l->cur = TL.dst;
+            if (E_series || M_series) {
+                ProfScope ps_(ctx, PK_OBS);
+                CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances,
+                                            l->d.n_replicas, E_series ? E_series + (uint64_t)s * l->ncopies : nullptr,
+                                            M_series ? M_series + (uint64_t)s * l->ncopies : nullptr, ctx->stream));
+            }
+        }
+        if (l->cur != l->spins) {
+            CUDA_TRY(cudaMemcpyAsync(l->spins, l->cur, l->N * l->ncopies, cudaMemcpyDeviceToDevice, ctx->stream));
+            l->cur = l->spins;
+        }
     } else {
         for (uint32_t s = 0; s < n_sweeps; ++s) {
             for (int colour = 0; colour < 2; ++colour) {
                 ProfScope ps_(ctx, PK_HALFSWEEP);
                 CUDA_TRY(launch_halfsweep_global(J, l->d.dim, colour, l->t + s, ctx->stream));
             }
-            ProfScope ps_(ctx, PK_OBS);
-            if (E_series || M_series)
+            if (E_series || M_series) {
+                ProfScope ps_(ctx, PK_OBS);
                 CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances,
                                             l->d.n_replicas, E_series ? E_series + (uint64_t)s * l->ncopies : nullptr,
                                             M_series ? M_series + (uint64_t)s * l->ncopies : nullptr, ctx->stream));
+            }
         }
     }
     l->t += n_sweeps;
@@ -1055,7 +1098,10 @@ static gbmc_status pa_enqueue_adaptive(gbmc_pa* pa, const double* beta_next) {
         S.lo = pa->cfg.overlap_lo;
         S.hi = pa->cfg.overlap_hi;
         S.mode = pa->cfg.schedule == GBMC_SCHED_MLP ? 2 : 1;
-        CUDA_TRY(launch_schedule(S, s));
+        {
+            ProfScope ps_(pa->ctx, PK_SCHEDULE);
+            CUDA_TRY(launch_schedule(S, s));
+        }
         CUDA_TRY(cudaMemcpyAsync(pa->sched_host, pa->sched_dev, S.njobs * sizeof(SchedOut), cudaMemcpyDeviceToHost, s));
     }
     // the staging slot written below was last read two steps ago

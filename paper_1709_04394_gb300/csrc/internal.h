@@ -69,6 +69,18 @@ cudaError_t launch_observables(const int8_t* spins, const uint8_t* jbits, int di
 size_t resident_smem_bytes(const SweepLaunch& P);
 cudaError_t launch_sweep_resident(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads,
                                   size_t smem, cudaStream_t s);
+// Tiled sweeps of large 2D ferromagnets (T | L, T % 8 == 0): up to 4 exact
+// sweeps per launch from src into dst (different buffers).
+struct TileLaunch {
+    const int8_t* src;
+    int8_t* dst;
+    uint64_t seed;
+    uint32_t L, T, R, inst_base, copy0;
+    uint32_t t0, nsweeps;     // nsweeps <= 4
+    uint32_t thr[2];          // T(4), T(8)
+};
+size_t tile_smem_bytes(uint32_t T);
+cudaError_t launch_sweep_tiles(const TileLaunch& P, uint64_t copies, cudaStream_t s);
 // Global-memory half-sweep over one job (large lattices); colour 0 or 1.
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);

@@ -122,7 +122,9 @@ __device__ __forceinline__ void unit_swar(uint8_t* sp, const uint8_t* jb, uint32
 
 __device__ __forceinline__ uint32_t neq4(uint32_t a, uint32_t b) { return (a ^ b) & 0x04040404u; }
 
-// Split-plane unit: word g of row `row` of colour plane `colour`. sp: copy
+// Split-plane unit: word g of row `row` of colour plane `colour`; q is the
+// Philox counter word of its 4 sites (row-major rank of the word over the
+// whole lattice, which differs from row * (L/8) + g inside a tile). sp: copy
 // base (plane 0 then plane 1, N/2 bytes each); jb: this colour's 2*DIM bond
 // planes (bytes 0x04 where J = -1; order same-j x, shifted x, y-1, y+1, z-1,
 // z+1); tbl: byte-addressed threshold table (entry a at byte 4a).
@@ -130,7 +132,7 @@ template <int DIM, bool EA, bool MEASURE>
 __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
                                            uint32_t row, uint32_t y, uint32_t z, uint32_t g, uint32_t colour,
                                            const PhiloxFixed& pf, const uint8_t* tbl, bool doflip, int& e_acc,
-                                           int& m_acc) {
+                                           int& m_acc, uint32_t q) {
     const uint32_t W = L >> 3, H = N >> 1;
     const uint32_t o = (y + z + colour) & 1u;
     uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * H);
@@ -162,7 +164,7 @@ __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint3
     }
     uint32_t flip = 0;
     if (doflip) {
-        const uint4 w = philox_q(pf, rw + g);
+        const uint4 w = philox_q(pf, q);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const uint32_t am = __byte_perm(a4, 0u, 0x4440u + m);  // 4a of site m
@@ -273,7 +275,8 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
             uint32_t y = wk.y0, z = wk.z0;
 #pragma unroll 4
             for (uint32_t row = wk.row0; row < rows; row += wk.rstep) {
-                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m);
+                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                             row * W + wk.g0);
                 if (DIM == 3) {
                     y += wk.dy;
                     z += wk.dz;
@@ -290,7 +293,7 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
             for (uint32_t uu = first_unit; uu < units; uu += stride) {
                 const uint32_t row = uu / W;
                 unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, DIM == 3 ? row % L : row, DIM == 3 ? row / L : 0,
-                                             uu % W, colour, pf, tbl, flip, e, m);
+                                             uu % W, colour, pf, tbl, flip, e, m, uu);
             }
         }
     } else {
@@ -517,6 +520,104 @@ cudaError_t launch_sweep_resident(const SweepLaunch& P, uint32_t n_ctas, uint32_
     if (P.dim == 3 && !P.ea) return launch_res_dim<3, false>(P, n_ctas, threads, smem, s);
     if (P.dim == 3 && P.ea) return launch_res_dim<3, true>(P, n_ctas, threads, smem, s);
     return cudaErrorInvalidValue;
+}
+
+// ---- tiled sweeps of large 2D lattices: shared-memory tiles with a halo ----
+// Each CTA loads a (T + 16) x (T + 16) window (an 8-site halo on every side,
+// periodic wrap) of one copy into shared memory as colour planes, runs up to 4
+// full sweeps on it, and writes back the T x T interior to the other buffer.
+// Half-sweep s updates rows [s + 1, W - s - 1) of the window: the region whose
+// neighbours are still exact shrinks by one site per half-sweep, so after 2k
+// <= 8 half-sweeps the interior equals the two-phase checkerboard sweeps of the
+// whole lattice (Sec. 3.1). Halo sites get updated with stale neighbours and
+// are discarded. The 8-site halo keeps every plane word aligned with a whole
+// Philox call (4 same-colour sites = 8 lattice columns).
+template <uint32_t T>
+__global__ void __launch_bounds__(256) k_sweep_tiles(const __grid_constant__ TileLaunch P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ __align__(16) uint32_t s_tbl[8];
+    constexpr uint32_t Wd = T + 16, Wg = Wd >> 3, H = (Wd * Wd) >> 1;
+    const uint32_t L = P.L, Lw = L >> 3;
+    const uint32_t tiles_x = L / T;
+    const uint32_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const uint64_t copy = (uint64_t)P.copy0 + blockIdx.y;
+    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    const int8_t* src = P.src + copy * (uint64_t)L * L;
+    int8_t* dst = P.dst + copy * (uint64_t)L * L;
+    const uint32_t y0 = (ty * T + L - 8) % L;  // global row of window row 0
+    const uint32_t xw0 = ((tx * T + L - 8) % L) >> 3;  // global 8-column chunk of window chunk 0
+    // load with periodic wrap; chunks never straddle the wrap (L % 8 == 0)
+    uint32_t* pl = reinterpret_cast<uint32_t*>(smem);
+    for (uint32_t idx = threadIdx.x; idx < Wd * Wg; idx += blockDim.x) {
+        const uint32_t rr = idx / Wg, cx = idx - rr * Wg;
+        uint32_t gy = y0 + rr, gc = xw0 + cx;
+        if (gy >= L) gy -= L;
+        if (gc >= Lw) gc -= Lw;
+        const uint2 v = *reinterpret_cast<const uint2*>(src + (uint64_t)gy * L + 8ull * gc);
+        const uint32_t pe = gy & 1u;  // colour of the even columns of this row
+        pl[pe * (H >> 2) + idx] = __byte_perm(v.x, v.y, 0x6420);
+        pl[(pe ^ 1u) * (H >> 2) + idx] = __byte_perm(v.x, v.y, 0x7531);
+    }
+    if (threadIdx.x < 8) {
+        const int d = 2 - (int)threadIdx.x;
+        s_tbl[threadIdx.x] = d <= 0 ? 0xFFFFFFFFu : (d == 1 ? P.thr[0] : P.thr[1]);
+    }
+    __syncthreads();
+    const uint8_t* tbl = reinterpret_cast<const uint8_t*>(s_tbl);
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const uint32_t instance = P.inst_base + inst;
+    int e = 0, m = 0;
+    for (uint32_t s = 0; s < 2 * P.nsweeps; ++s) {
+        const uint32_t colour = s & 1u, t = P.t0 + (s >> 1);
+        const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
+        const uint32_t row_lo = s + 1, rows = Wd - 2 * (s + 1);
+        for (uint32_t u = threadIdx.x; u < rows * Wg; u += blockDim.x) {
+            const uint32_t rr = u / Wg, g = u - rr * Wg;
+            const uint32_t row = row_lo + rr;
+            uint32_t gy = y0 + row, gc = xw0 + g;
+            if (gy >= L) gy -= L;
+            if (gc >= Lw) gc -= Lw;
+            const uint32_t q = gy * Lw + gc;
+            unit_split<2, false, false>(smem, nullptr, Wd, Wd * Wd, row, row, 0, g, colour, pf, tbl, true, e, m, q);
+        }
+        __syncthreads();
+    }
+    // store the T x T interior: window rows [8, 8 + T), chunks [1, 1 + T/8)
+    constexpr uint32_t Tc = T >> 3;
+    for (uint32_t idx = threadIdx.x; idx < T * Tc; idx += blockDim.x) {
+        const uint32_t rr = idx / Tc, cx = idx - rr * Tc;
+        const uint32_t wrow = rr + 8, wc = cx + 1;
+        const uint32_t gy = ty * T + rr, gx = tx * T + 8 * cx;
+        const uint32_t pe = gy & 1u;
+        const uint32_t ev = pl[pe * (H >> 2) + wrow * Wg + wc], od = pl[(pe ^ 1u) * (H >> 2) + wrow * Wg + wc];
+        uint2 v;
+        v.x = __byte_perm(ev, od, 0x5140);
+        v.y = __byte_perm(ev, od, 0x7362);
+        *reinterpret_cast<uint2*>(dst + (uint64_t)gy * L + gx) = v;
+    }
+}
+
+size_t tile_smem_bytes(uint32_t T) { return (size_t)(T + 16) * (T + 16); }
+
+cudaError_t launch_sweep_tiles(const TileLaunch& P, uint64_t copies, cudaStream_t s) {
+    const size_t smem = tile_smem_bytes(P.T);
+    if (P.T != 128 && P.T != 256) return cudaErrorInvalidValue;
+    auto kern = P.T == 128 ? k_sweep_tiles<128> : k_sweep_tiles<256>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const uint32_t tiles = (P.L / P.T) * (P.L / P.T);
+    for (uint64_t c0 = 0; c0 < copies; c0 += 65535) {
+        TileLaunch Q = P;
+        Q.copy0 = (uint32_t)c0;
+        const uint32_t nc = (uint32_t)((copies - c0) < 65535 ? (copies - c0) : 65535);
+        kern<<<dim3(tiles, nc), 256, smem, s>>>(Q);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---- global-memory half-sweep (large lattices) ----

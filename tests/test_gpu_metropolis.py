@@ -107,11 +107,14 @@ def test_sweeps_match_oracle(ctx, dim, L, model, n_inst, R, beta, n):
     gbmc.lattice_free(lat)
 
 
-@pytest.mark.parametrize("L,n", [(512, 3), (4096, 2)])
-def test_global_memory_path_matches_oracle(ctx, L, n):
-    # lattices too large for shared memory (L = 4096 is the single-lattice benchmark size)
+@pytest.mark.parametrize("L,n,chunks", [(512, 6, (6,)), (512, 3, (1, 2)), (4096, 2, (2,)), (384, 9, (4, 5)),
+                                        (768, 2, (2,)), (520, 2, (2,))])
+def test_large_lattice_paths_match_oracle(ctx, L, n, chunks):
+    # lattices too large for shared memory: tiled sweeps (L % 128 == 0, up to 4 sweeps
+    # per launch, any chunking) or global half-sweeps; L = 4096 is the benchmark size
     lat = gbmc.lattice_init(ctx, 2, L, seed=1)
-    gbmc.metropolis_sweeps(ctx, lat, BETA_C, n)
+    for c in chunks:
+        gbmc.metropolis_sweeps(ctx, lat, BETA_C, c)
     E, M = device_i32(1), device_i32(1)
     gbmc.observables(ctx, lat, E, M)
     got = spins_out(ctx, lat)[0]
@@ -119,6 +122,24 @@ def test_global_memory_path_matches_oracle(ctx, L, n):
     oracle.sweeps(2, L, s, None, BETA_C, 1, 0, 0, 0, n)
     np.testing.assert_array_equal(got, s)
     assert (int(E[0]), int(M[0])) == oracle.observables(2, L, s)
+    gbmc.lattice_free(lat)
+
+
+def test_tiled_path_series_and_caller_buffer(ctx):
+    L, n, R = 256 + 256, 3, 2
+    buf = torch.zeros(R * L * L, dtype=torch.int8, device="cuda")
+    lat = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=9, instance_base=2, spins=buf)
+    Es, Ms = device_i32(n * R), device_i32(n * R)
+    gbmc.metropolis_sweeps(ctx, lat, 0.5, n, Es, Ms)
+    torch.cuda.synchronize()
+    got = buf.cpu().numpy().reshape(R, -1)  # the caller's buffer holds the result
+    Es = Es.cpu().numpy().reshape(n, R)
+    for r in range(R):
+        s = oracle.init_spins(2, L, 9, 2, r, True)
+        for k in range(n):
+            oracle.sweeps(2, L, s, None, 0.5, 9, 2, r, k, 1)
+            assert Es[k, r] == oracle.observables(2, L, s)[0]
+        np.testing.assert_array_equal(got[r], s)
     gbmc.lattice_free(lat)
 
 
