@@ -167,8 +167,9 @@ FM, EA = 0, 1
 WORKLOADS = {
     # population annealing 2D Ising L=64, R=10^5, beta 0->1 in 101 temperatures, theta=10
     "pa-ising2d-L64": dict(kind="pa", lattices=[(2, 64, FM, 1, 100000)], S=100, theta=10, beta_f=1.0),
-    # single 2D Ising lattice L=4096 at beta=0.4406868, 1000 sweeps per step
-    "ising2d-L4096": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868),
+    # single 2D Ising lattice L=4096 at beta=0.4406868, 1000 sweeps per step (int8, bit-packed)
+    "ising2d-L4096": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=0),
+    "ising2d-L4096-bitpack": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=1),
     # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
     "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
@@ -221,7 +222,7 @@ def run_gpu(args, w, ws, rank, local):
             gbmc.pa_run(ctx, pa)
     else:
         N = w["L"] ** w["dim"]
-        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0)
+        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0, layout=w.get("layout", 0))
         lats = [lat]
 
         def step(k):
@@ -258,7 +259,8 @@ def run_gpu(args, w, ws, rank, local):
     n_e2e = max(1, min(args.steps, 3))
     hosts_in, hosts_out = [], []
     for i, l in enumerate(lats):
-        nb = gbmc.lattice_info(l).spin_bytes
+        info = gbmc.lattice_info(l)
+        nb = info.n_sites * info.n_copies  # int8 layout on the host side of the ABI
         hin = torch.empty(nb, dtype=torch.int8, pin_memory=True)
         hin.numpy()[:] = inputs.random_spins(nb, seed=seed0 + 77 + i)
         hosts_in.append(hin)
@@ -487,15 +489,19 @@ def main():
     value = ws * upd * args.steps / (ms * 1e6)  # site updates per ns, all ranks
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
-    kname = "sweep_resident" if w["kind"] == "pa" else "halfsweep_global"
+    kname = "sweep_resident" if w["kind"] == "pa" else \
+        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else "sweep_tiles")
     n_l, t_l = prof.get(kname, (0, 0.0))
     avg_ms = t_l / n_l if n_l else float("nan")
     if w["kind"] == "pa":
         upd_per_launch = sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"]
         hbm_bytes_per_launch = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
+    elif w.get("layout", 0) == 1:
+        upd_per_launch = w["L"] ** w["dim"] // 2          # one colour per launch
+        hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 16  # read both planes, write one (bits)
     else:
-        upd_per_launch = w["L"] ** w["dim"] // 2
-        hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 2
+        upd_per_launch = w["L"] ** w["dim"] * 4            # 4 sweeps per tiled launch
+        hbm_bytes_per_launch = w["L"] ** w["dim"] * 2 * (144 * 144) // (128 * 128)  # window in, interior out
     ops = ALG_INT_OPS_PER_SITE_UPDATE * upd_per_launch
     achieved = ops / (avg_ms * 1e-3) / 1e9  # Gop/s
     clk = res["clocks"]

@@ -73,6 +73,21 @@ gbmc_status gbmc_set_stream(gbmc_ctx *ctx, void *cuda_stream);
 gbmc_status gbmc_sync(gbmc_ctx *ctx);
 gbmc_status gbmc_destroy(gbmc_ctx *ctx);
 
+/* Resampling path of population annealing: fused = 1 (default when the device
+ * supports cooperative launches) runs the weights, ln Q / prefix sums,
+ * multinomial draws and child placement of one lattice in ONE cooperative
+ * launch with grid-wide barriers; fused = 0 uses one launch per phase. Both
+ * give identical results. */
+gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
+/* Test aid for the bounded grid barriers of the fused resampling: each
+ * barrier waits for `phantom_arrivals` CTAs more than the launch has (so with
+ * 1 the wait can only end by running out of its budget) and gives up after
+ * `budget_cycles` SM cycles (default 2e9). A wait that runs out makes the
+ * kernel return early and the next synchronising call (gbmc_sync, pa_run,
+ * pa_step with statistics) return GBMC_ERR_TIMEOUT; the context stays usable.
+ * Pass (0, 2000000000) to restore the defaults. */
+gbmc_status gbmc_test_barrier_wait(gbmc_ctx *ctx, uint32_t phantom_arrivals, uint64_t budget_cycles);
+
 /* Per-kernel timing with CUDA events recorded on the context stream around
  * every launch the library enqueues (off by default). gbmc_profile(ctx, 1)
  * clears the counters and starts recording; 0 stops. gbmc_profile_read
@@ -96,7 +111,10 @@ typedef struct {
     int32_t dim;            /* 2 or 3 */
     int32_t L;              /* linear size, even, 2 <= L <= 32768 (dim 2) / 1024 (dim 3) */
     int32_t model;          /* GBMC_ISING_FM (J = 1) or GBMC_EA_PMJ (bimodal +-J, Sec. 6) */
-    int32_t layout;         /* GBMC_INT8 or GBMC_BITPACK (dim 2, FM, L % 64 == 0) */
+    int32_t layout;         /* GBMC_INT8, or GBMC_BITPACK (2D ferromagnet, L % 64 == 0): one bit per
+                               spin, per copy two colour planes, plane c row y word w = sites
+                               j = 32w..32w+31 of colour c (x = 2j + ((y+c)&1)), bit 1 where s = -1.
+                               Sweeps and observables only (population annealing uses int8). */
     int32_t start;          /* GBMC_START_ALL_UP or GBMC_START_RANDOM */
     uint32_t n_instances;   /* disorder instances (independent couplings), >= 1 */
     uint32_t n_replicas;    /* replicas per instance, >= 1 */

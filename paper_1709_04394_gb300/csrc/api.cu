@@ -48,11 +48,13 @@ std::atomic<uint64_t> g_launches{0};
 
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
-    PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_COUNT
+    PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
+    PK_BP_HALFSWEEP, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
-                                          "pa_record", "pa_reset", "sweep_tiles", "schedule"};
+                                          "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
+                                          "bitpack_halfsweep"};
 
 // Interior size of the tiles of large 2D lattices (window = kTile + 16).
 constexpr uint32_t kTile = 128;
@@ -68,6 +70,10 @@ struct gbmc_ctx {
     int device;
     cudaStream_t stream;
     int sm_count;
+    unsigned int* words = nullptr;  // device [barrier counter, error flag]
+    bool fused = true;              // one cooperative resampling launch per lattice and step
+    uint32_t phantom = 0;           // test hook: extra barrier arrivals to wait for
+    long long budget = 2000000000;  // cycles a barrier wait may last (about 1 s)
     bool prof = false;
     struct Pending {
         int kind;
@@ -358,6 +364,22 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, void* cuda_stream) {
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    int coop = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    c->fused = coop != 0;
+    {
+        cudaError_t e = cudaMalloc(&c->words, 4 * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(GBMC_ERR_OOM, "cudaMalloc(context words): %s", cudaGetErrorString(e));
+        }
+        e = cudaMemset(c->words, 0, 4 * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            cudaFree(c->words);
+            delete c;
+            return fail(GBMC_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+        }
+    }
     *out = c;
     return GBMC_OK;
 }
@@ -368,9 +390,40 @@ gbmc_status gbmc_set_stream(gbmc_ctx* ctx, void* cuda_stream) {
     return GBMC_OK;
 }
 
+// Reads (and clears) the device error flag raised by a bounded wait that ran
+// out; the stream must have been synchronised.
+static gbmc_status check_device_error(gbmc_ctx* ctx) {
+    unsigned int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, ctx->words + 1, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(cudaMemset(ctx->words + 1, 0, sizeof(err)));
+        return fail(GBMC_ERR_TIMEOUT, "a grid barrier wait ran out of its cycle budget; results since the last "
+                                      "check are invalid");
+    }
+    return GBMC_OK;
+}
+
 gbmc_status gbmc_sync(gbmc_ctx* ctx) {
     if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    CUDA_TRY(cudaSetDevice(ctx->device));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+gbmc_status gbmc_set_resample_mode(gbmc_ctx* ctx, int32_t fused) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    int coop = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+    if (fused && !coop) return fail(GBMC_ERR_STATE, "device has no cooperative launch");
+    ctx->fused = fused != 0;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_test_barrier_wait(gbmc_ctx* ctx, uint32_t phantom_arrivals, uint64_t budget_cycles) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    if (budget_cycles == 0 || budget_cycles > (1ull << 40)) return fail(GBMC_ERR_ARG, "budget out of range");
+    ctx->phantom = phantom_arrivals;
+    ctx->budget = (long long)budget_cycles;
     return GBMC_OK;
 }
 
@@ -382,6 +435,7 @@ gbmc_status gbmc_destroy(gbmc_ctx* ctx) {
         cudaEventDestroy(p.b);
     }
     for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->words) cudaFree(ctx->words);
     delete ctx;
     return GBMC_OK;
 }
@@ -440,7 +494,9 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
         return fail(GBMC_ERR_ARG, "L too large");
     if (d->model != GBMC_ISING_FM && d->model != GBMC_EA_PMJ) return fail(GBMC_ERR_ARG, "unknown model");
     if (d->model == GBMC_EA_PMJ && d->dim != 3) return fail(GBMC_ERR_ARG, "the +-J model is three-dimensional");
-    if (d->layout != GBMC_INT8) return fail(GBMC_ERR_ARG, "layout %d not supported by this build", d->layout);
+    if (d->layout != GBMC_INT8 && d->layout != GBMC_BITPACK) return fail(GBMC_ERR_ARG, "unknown layout %d", d->layout);
+    if (d->layout == GBMC_BITPACK && (d->dim != 2 || d->model != GBMC_ISING_FM || d->L % 64 != 0))
+        return fail(GBMC_ERR_ARG, "the bit-packed layout needs a 2D ferromagnet with L %% 64 == 0");
     if (d->start != GBMC_START_ALL_UP && d->start != GBMC_START_RANDOM) return fail(GBMC_ERR_ARG, "unknown start");
     if (d->n_instances == 0 || d->n_replicas == 0) return fail(GBMC_ERR_ARG, "empty lattice set");
     if ((uint64_t)d->instance_base + d->n_instances > (1ull << 27)) return fail(GBMC_ERR_ARG, "instance ids exceed 2^27");
@@ -449,7 +505,7 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
     const uint64_t ncopies = (uint64_t)d->n_instances * d->n_replicas;
     if (d->n_replicas > 0xFFFFFFFFull || N * (uint64_t)d->dim > 0x7FFFFFFFull)
         return fail(GBMC_ERR_ARG, "lattice too large for 32-bit energies");
-    const uint64_t bytes = ncopies * N;
+    const uint64_t bytes = d->layout == GBMC_BITPACK ? ncopies * (N / 8) : ncopies * N;
     if (spins_dev) {
         if (spins_bytes < bytes) return fail(GBMC_ERR_ARG, "spins buffer has %zu bytes, need %llu", spins_bytes, (unsigned long long)bytes);
         if (((uintptr_t)spins_dev & 15) != 0) return fail(GBMC_ERR_ARG, "spins buffer must be 16-byte aligned");
@@ -496,8 +552,12 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
     }
     {
         ProfScope ps_(ctx, PK_INIT);
-        CUDA_TRY(launch_init_spins(l->spins, d->dim, (uint32_t)d->L, d->n_instances, d->n_replicas, d->instance_base,
-                                   d->seed, d->start == GBMC_START_RANDOM, ctx->stream));
+        if (d->layout == GBMC_BITPACK)
+            CUDA_TRY(launch_bp_init((uint32_t*)l->spins, (uint32_t)d->L, ncopies, d->n_replicas, d->instance_base,
+                                    d->seed, d->start == GBMC_START_RANDOM, ctx->stream));
+        else
+            CUDA_TRY(launch_init_spins(l->spins, d->dim, (uint32_t)d->L, d->n_instances, d->n_replicas,
+                                       d->instance_base, d->seed, d->start == GBMC_START_RANDOM, ctx->stream));
     }
     *out = l;
     return GBMC_OK;
@@ -518,7 +578,7 @@ gbmc_status lattice_info(const gbmc_lattice* l, gbmc_lattice_info* out) {
     if (!l || !out) return fail(GBMC_ERR_ARG, "NULL argument");
     out->n_sites = (int64_t)l->N;
     out->n_copies = (int64_t)l->ncopies;
-    out->spin_bytes = (int64_t)(l->N * l->ncopies);
+    out->spin_bytes = (int64_t)(l->d.layout == GBMC_BITPACK ? (l->N / 8) * l->ncopies : l->N * l->ncopies);
     out->sweep_counter = l->t;
     out->pad = 0;
     out->spins_dev = l->cur;
@@ -534,6 +594,18 @@ gbmc_status lattice_set_sweep_counter(gbmc_lattice* l, uint32_t t) {
 gbmc_status lattice_copy_out(gbmc_ctx* ctx, const gbmc_lattice* l, int8_t* dst, size_t bytes) {
     if (!ctx || !l || !dst) return fail(GBMC_ERR_ARG, "NULL argument");
     if (bytes != l->N * l->ncopies) return fail(GBMC_ERR_ARG, "bytes must be %llu", (unsigned long long)(l->N * l->ncopies));
+    if (l->d.layout == GBMC_BITPACK) {
+        const bool dev = is_device_ptr(dst);
+        int8_t* tmp = dst;
+        if (!dev) CUDA_TRY(cudaMallocAsync((void**)&tmp, bytes, ctx->stream));
+        CUDA_TRY(launch_bp_unpack((const uint32_t*)l->cur, tmp, (uint32_t)l->d.L, l->ncopies, ctx->stream));
+        if (!dev) {
+            CUDA_TRY(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_TRY(cudaFreeAsync(tmp, ctx->stream));
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        }
+        return GBMC_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(dst, l->cur, bytes, cudaMemcpyDefault, ctx->stream));
     if (!is_device_ptr(dst)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return GBMC_OK;
@@ -542,6 +614,22 @@ gbmc_status lattice_copy_out(gbmc_ctx* ctx, const gbmc_lattice* l, int8_t* dst, 
 gbmc_status lattice_copy_in(gbmc_ctx* ctx, gbmc_lattice* l, const int8_t* src, size_t bytes) {
     if (!ctx || !l || !src) return fail(GBMC_ERR_ARG, "NULL argument");
     if (bytes != l->N * l->ncopies) return fail(GBMC_ERR_ARG, "bytes must be %llu", (unsigned long long)(l->N * l->ncopies));
+    if (l->d.layout == GBMC_BITPACK) {
+        const bool dev = is_device_ptr(src);
+        const int8_t* tsrc = src;
+        int8_t* tmp = nullptr;
+        if (!dev) {
+            CUDA_TRY(cudaMallocAsync((void**)&tmp, bytes, ctx->stream));
+            CUDA_TRY(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            tsrc = tmp;
+        }
+        CUDA_TRY(launch_bp_pack(tsrc, (uint32_t*)l->cur, (uint32_t)l->d.L, l->ncopies, ctx->stream));
+        if (tmp) {
+            CUDA_TRY(cudaFreeAsync(tmp, ctx->stream));
+            CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        }
+        return GBMC_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(l->cur, src, bytes, cudaMemcpyDefault, ctx->stream));
     if (!is_device_ptr(src)) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return GBMC_OK;
@@ -572,6 +660,26 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
     if (n_sweeps == 0) return GBMC_OK;
     if ((uint64_t)l->t + n_sweeps > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "sweep counter would wrap");
     CUDA_TRY(cudaSetDevice(ctx->device));
+    if (l->d.layout == GBMC_BITPACK) {
+        uint32_t thr[3];
+        thresholds(beta, thr);
+        for (uint32_t s = 0; s < n_sweeps; ++s) {
+            for (uint32_t colour = 0; colour < 2; ++colour) {
+                ProfScope ps_(ctx, PK_BP_HALFSWEEP);
+                CUDA_TRY(launch_bp_halfsweep((uint32_t*)l->cur, (uint32_t)l->d.L, l->ncopies, l->d.n_replicas,
+                                             l->d.instance_base, l->d.seed, colour, l->t + s, thr[0], thr[1],
+                                             ctx->stream));
+            }
+            if (E_series || M_series) {
+                ProfScope ps_(ctx, PK_OBS);
+                CUDA_TRY(launch_bp_observables((const uint32_t*)l->cur, (uint32_t)l->d.L, l->ncopies,
+                                               E_series ? E_series + (uint64_t)s * l->ncopies : nullptr,
+                                               M_series ? M_series + (uint64_t)s * l->ncopies : nullptr, ctx->stream));
+            }
+        }
+        l->t += n_sweeps;
+        return GBMC_OK;
+    }
     const Tuning tu = tune(l);
     SweepJob J = base_job(l, tu);
     thresholds(beta, J.thr);
@@ -648,6 +756,10 @@ gbmc_status observables(gbmc_ctx* ctx, const gbmc_lattice* l, int32_t* E, int32_
     if (!E && !M) return GBMC_OK;
     CUDA_TRY(cudaSetDevice(ctx->device));
     ProfScope ps_(ctx, PK_OBS);
+    if (l->d.layout == GBMC_BITPACK) {
+        CUDA_TRY(launch_bp_observables((const uint32_t*)l->cur, (uint32_t)l->d.L, l->ncopies, E, M, ctx->stream));
+        return GBMC_OK;
+    }
     CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances, l->d.n_replicas, E, M,
                                 ctx->stream));
     return GBMC_OK;
@@ -786,6 +898,7 @@ static gbmc_status pa_begin(gbmc_pa* pa, int init) {
         for (uint32_t k = 0; k < l->d.n_instances; ++k) z[k] = (double)l->N * std::log(2.0);
         CUDA_TRY(cudaMemcpyAsync(pl.lnZ, z.data(), z.size() * 8, cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaStreamSynchronize(s));  // z is a host temporary
+        CUDA_TRY(cudaMemsetAsync(pl.counts, 0, l->ncopies * 4, s));
         PaLattice P = pa_params(pa, pl, 0);
         ProfScope ps_(pa->ctx, PK_PA_RESET);
         CUDA_TRY(launch_pa_reset(P, s));
@@ -825,6 +938,8 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         if (l->run) return fail(GBMC_ERR_STATE, "lattice %u already in an annealing run", i);
         if (l->d.dim != l0->d.dim || l->d.model != l0->d.model)
             return fail(GBMC_ERR_ARG, "lattices of one run share dim and model");
+        if (l->d.layout != GBMC_INT8)
+            return fail(GBMC_ERR_ARG, "population annealing runs on the int8 layout (lattice %u is bit-packed)", i);
         if (adaptive && l->d.n_instances != 1)
             return fail(GBMC_ERR_ARG, "adaptive schedules anneal one population per lattice (n_instances = 1)");
         for (uint32_t k = 0; k < i; ++k)
@@ -913,6 +1028,9 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
         pl.parent = (uint32_t*)p;
         cudaError_t ce = cudaMemsetAsync(pl.counts, 0, C * 4, ctx->stream);
+        // every slot starts with a valid parent, so a step whose resampling was
+        // abandoned (timed-out barrier) still gathers in bounds
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(pl.parent, 0, C * 4, ctx->stream);
         if (ce != cudaSuccess) { st = fail(GBMC_ERR_CUDA, "memset: %s", cudaGetErrorString(ce)); break; }
         // fp64 weight tables (Eq. (13)), host libm exp: every step of a fixed
         // schedule now; for adaptive schedules a 2-slot ring filled per step
@@ -1029,6 +1147,12 @@ static gbmc_status pa_enqueue_common(gbmc_pa* pa) {
     for (auto& pl : pa->lats) {
         if (!pl.stepping) continue;
         PaLattice P = pa_params(pa, pl, pl.steps);
+        if (pa->ctx->fused) {
+            GridBarrier B{pa->ctx->words, pa->ctx->words + 1, pa->ctx->budget, pa->ctx->phantom};
+            ProfScope ps_(pa->ctx, PK_PA_FUSED);
+            CUDA_TRY(launch_pa_resample_fused(P, pl.lnZ, B, pa->ctx->sm_count, s));
+            continue;
+        }
         {
             ProfScope ps_(pa->ctx, PK_PA_WEIGHTS);
             CUDA_TRY(launch_pa_weights(P, s));
@@ -1106,6 +1230,10 @@ static gbmc_status pa_enqueue_adaptive(gbmc_pa* pa, const double* beta_next) {
     }
     // the staging slot written below was last read two steps ago
     CUDA_TRY(cudaStreamSynchronize(s));
+    {
+        gbmc_status est = check_device_error(pa->ctx);
+        if (est != GBMC_OK) return est;
+    }
     for (size_t j = 0; j < act.size(); ++j) {
         PaLat& pl = *act[j];
         gbmc_lattice* l = pl.lat;
@@ -1179,6 +1307,7 @@ gbmc_status pa_step(gbmc_ctx* ctx, gbmc_pa* pa, const double* beta_next, gbmc_pa
         CUDA_TRY(cudaMemcpyAsync(out_host, pa->stats + (uint64_t)pa->step * pa->P, pa->P * sizeof(gbmc_pa_stats),
                                  cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        return check_device_error(ctx);
     }
     return GBMC_OK;
 }
@@ -1198,7 +1327,7 @@ gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     if (n_done) *n_done = pa->step;
-    return GBMC_OK;
+    return check_device_error(ctx);
 }
 
 gbmc_status pa_schedule_log(const gbmc_pa* pa, uint32_t lattice, gbmc_schedule_record* out, uint32_t capacity,
@@ -1266,6 +1395,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     if (n_sweeps == 0) n_sweeps = 1;
     std::memset(out, 0, sizeof(*out));
     CUDA_TRY(cudaSetDevice(ctx->device));
+    if (l->d.layout != GBMC_INT8) return GBMC_OK;
     const Tuning def = tune(l, false);
     if (!def.resident) return GBMC_OK;
     // time on instance 0 with at most 32768 of its replicas, on a scratch copy

@@ -1,0 +1,232 @@
+// bitpack.cu -- the bit-packed ("multi-spin coded", Sec. 3.1) layout of 2D
+// ferromagnets: one bit per spin. Per copy, two colour planes; plane c, row y,
+// word w holds the sites j = 32w .. 32w+31 of colour c in row y (site
+// x = 2j + ((y+c)&1)), bit = 1 where s = -1. L % 64 == 0.
+//
+// Sweeps use the same Philox words as the int8 layouts (the counter of a site
+// depends only on its colour rank), so both layouts give identical spins.
+// For the 32 sites of a word, the four neighbours are the same word of the
+// other plane in rows y-1, y, y+1 and that word shifted by one bit; the
+// number of unsatisfied bonds a (0..4) is summed bit-sliced (a0 + 2 a1 + 4 a2)
+// and a site flips iff a >= 2, or a = 1 and u <= T(4), or a = 0 and u <= T(8).
+#include "device.cuh"
+#include "internal.h"
+
+namespace gbmc {
+
+// Random (or all-up) start written directly in packed form: word (copy,
+// colour, row, w); the INIT word of site i is word i&3 of q = i>>2.
+__global__ void k_bp_init(uint32_t* P, uint32_t L, uint64_t words_total, uint32_t R, uint32_t inst_base, uint32_t k0,
+                          uint32_t k1, int random_start) {
+    const uint32_t Wr = L >> 6;                    // words per plane row
+    const uint64_t per_copy = 2ull * L * Wr;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < words_total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        if (random_start) {
+            const uint64_t copy = g / per_copy;
+            const uint32_t rem = (uint32_t)(g - copy * per_copy);
+            const uint32_t c = rem / (L * Wr), rw = rem - c * (L * Wr);
+            const uint32_t y = rw / Wr, w = rw - y * Wr;
+            const uint32_t inst = (uint32_t)(copy / R), r = (uint32_t)(copy - (uint64_t)inst * R);
+            const uint32_t o = (y + c) & 1u;
+            const uint32_t c3 = c3_word(kPurposeInit, 0u, inst_base + inst);
+            // sites x = 64w + o + 2b, b = 0..31: 64 consecutive columns from 64w
+            for (uint32_t qq = 0; qq < 16; ++qq) {
+                const uint32_t site0 = y * L + 64 * w + 4 * qq;
+                const uint4 v = philox4x32_10(make_uint4(site0 >> 2, 0u, r, c3), k0, k1);
+                // columns 64w + 4qq + {0,1,2,3}; those with parity o are bits b = 2qq + (col-o)/2
+                const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (uint32_t l = 0; l < 4; ++l) {
+                    if ((l & 1u) != o) continue;
+                    const uint32_t b = 2 * qq + (l >> 1);
+                    word |= (u[l] >> 31) << b;
+                }
+            }
+        }
+        P[g] = word;
+    }
+}
+
+cudaError_t launch_bp_init(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base, uint64_t seed,
+                           int random_start, cudaStream_t s) {
+    const uint64_t total = copies * 2ull * L * (L >> 6);
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    k_bp_init<<<(uint32_t)blocks, 256, 0, s>>>(P, L, total, R, inst_base, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                               random_start);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// int8 row-major <-> packed planes; one thread per packed word.
+__global__ void k_bp_pack(const int8_t* src, uint32_t* P, uint32_t L, uint64_t words_total) {
+    const uint32_t Wr = L >> 6;
+    const uint64_t per_copy = 2ull * L * Wr;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < words_total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t copy = g / per_copy;
+        const uint32_t rem = (uint32_t)(g - copy * per_copy);
+        const uint32_t c = rem / (L * Wr), rw = rem - c * (L * Wr);
+        const uint32_t y = rw / Wr, w = rw - y * Wr;
+        const uint32_t o = (y + c) & 1u;
+        const int8_t* row = src + copy * (uint64_t)L * L + (uint64_t)y * L + 64ull * w + o;
+        uint32_t word = 0;
+        for (uint32_t b = 0; b < 32; ++b) word |= (uint32_t)(row[2 * b] < 0) << b;
+        P[g] = word;
+    }
+}
+
+__global__ void k_bp_unpack(const uint32_t* P, int8_t* dst, uint32_t L, uint64_t words_total) {
+    const uint32_t Wr = L >> 6;
+    const uint64_t per_copy = 2ull * L * Wr;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < words_total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t copy = g / per_copy;
+        const uint32_t rem = (uint32_t)(g - copy * per_copy);
+        const uint32_t c = rem / (L * Wr), rw = rem - c * (L * Wr);
+        const uint32_t y = rw / Wr, w = rw - y * Wr;
+        const uint32_t o = (y + c) & 1u;
+        int8_t* row = dst + copy * (uint64_t)L * L + (uint64_t)y * L + 64ull * w + o;
+        const uint32_t word = P[g];
+        for (uint32_t b = 0; b < 32; ++b) row[2 * b] = ((word >> b) & 1u) ? -1 : 1;
+    }
+}
+
+cudaError_t launch_bp_pack(const int8_t* src, uint32_t* P, uint32_t L, uint64_t copies, cudaStream_t s) {
+    const uint64_t total = copies * 2ull * L * (L >> 6);
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    k_bp_pack<<<(uint32_t)blocks, 256, 0, s>>>(src, P, L, total);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bp_unpack(const uint32_t* P, int8_t* dst, uint32_t L, uint64_t copies, cudaStream_t s) {
+    const uint64_t total = copies * 2ull * L * (L >> 6);
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    k_bp_unpack<<<(uint32_t)blocks, 256, 0, s>>>(P, dst, L, total);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Neighbours of the colour-c word (y, w): the other plane's words in rows
+// y-1, y+1, y and the row-y word shifted by one site towards j-1 (even x) or
+// j+1 (odd x).
+__device__ __forceinline__ void bp_neighbours(const uint32_t* oth, uint32_t L, uint32_t Wr, uint32_t y, uint32_t w,
+                                              uint32_t o, uint32_t& up, uint32_t& dn, uint32_t& same,
+                                              uint32_t& side) {
+    const uint32_t yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+    up = __ldcg(oth + yu * Wr + w);
+    dn = __ldcg(oth + yd * Wr + w);
+    same = __ldcg(oth + y * Wr + w);
+    if (o) {
+        const uint32_t nx = __ldcg(oth + y * Wr + (w + 1 == Wr ? 0 : w + 1));
+        side = __funnelshift_r(same, nx, 1);   // bits j+1
+    } else {
+        const uint32_t pv = __ldcg(oth + y * Wr + (w == 0 ? Wr - 1 : w - 1));
+        side = __funnelshift_l(pv, same, 1);   // bits j-1
+    }
+}
+
+// One half-sweep of colour c over every copy: one thread per word of plane c.
+__global__ void __launch_bounds__(256) k_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R,
+                                                      uint32_t inst_base, uint32_t colour, uint32_t t, uint32_t k0,
+                                                      uint32_t k1, uint32_t T4, uint32_t T8) {
+    const uint32_t Wr = L >> 6;
+    const uint64_t plane_words = (uint64_t)L * Wr;
+    const uint64_t total = copies * plane_words;
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const uint64_t copy = g / plane_words;
+    const uint32_t rw = (uint32_t)(g - copy * plane_words);
+    const uint32_t y = rw / Wr, w = rw - y * Wr;
+    const uint32_t inst = (uint32_t)(copy / R), r = (uint32_t)(copy - (uint64_t)inst * R);
+    uint32_t* own = P + copy * 2 * plane_words + colour * plane_words;
+    const uint32_t* oth = P + copy * 2 * plane_words + (colour ^ 1u) * plane_words;
+    const uint32_t o = (y + colour) & 1u;
+    uint32_t up, dn, same, side;
+    bp_neighbours(oth, L, Wr, y, w, o, up, dn, same, side);
+    const uint32_t s = own[rw];
+    const uint32_t d1 = s ^ up, d2 = s ^ dn, d3 = s ^ same, d4 = s ^ side;  // 1 = unsatisfied bond
+    // bit-sliced a = d1 + d2 + d3 + d4 = a0 + 2 a1 + 4 a2
+    const uint32_t s1 = d1 ^ d2, c1 = d1 & d2, s2 = d3 ^ d4, c2 = d3 & d4;
+    const uint32_t a0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t a1 = c1 ^ c2 ^ c3, a2 = (c1 & c2) | (c3 & (c1 ^ c2));
+    const uint32_t ge2 = a1 | a2;            // dE <= 0: always flips
+    const uint32_t eq1 = a0 & ~ge2;          // dE = 4
+    const uint32_t eq0 = ~(a0 | ge2);        // dE = 8
+    const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, inst_base + inst), k0, k1);
+    // colour rank of bit b: k = y L/2 + 32 w + b -> q = y L/8 + 8 w + b/4
+    const uint32_t q0 = y * (L >> 3) + 8 * w;
+    uint32_t m4 = 0, m8 = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint4 v = philox_q(pf, q0 + i);
+        m4 |= ((uint32_t)(v.x <= T4) | ((uint32_t)(v.y <= T4) << 1) | ((uint32_t)(v.z <= T4) << 2) |
+               ((uint32_t)(v.w <= T4) << 3)) << (4 * i);
+        m8 |= ((uint32_t)(v.x <= T8) | ((uint32_t)(v.y <= T8) << 1) | ((uint32_t)(v.z <= T8) << 2) |
+               ((uint32_t)(v.w <= T8) << 3)) << (4 * i);
+    }
+    const uint32_t flip = ge2 | (eq1 & m4) | (eq0 & m8);
+    own[rw] = s ^ flip;
+}
+
+cudaError_t launch_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base,
+                                uint64_t seed, uint32_t colour, uint32_t t, uint32_t T4, uint32_t T8, cudaStream_t s) {
+    const uint64_t total = copies * (uint64_t)L * (L >> 6);
+    const uint64_t blocks = (total + 255) / 256;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_bp_halfsweep<<<(uint32_t)blocks, 256, 0, s>>>(P, L, copies, R, inst_base, colour, t, (uint32_t)seed,
+                                                    (uint32_t)(seed >> 32), T4, T8);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// E and M of every copy: E = -sum over odd sites of s_i h_i = -(4 N/2 - 2 sum a_i),
+// M = N - 2 (number of down spins). One block per copy.
+__global__ void k_bp_observables(const uint32_t* P, uint32_t L, int32_t* E, int32_t* M) {
+    const uint32_t Wr = L >> 6;
+    const uint64_t plane_words = (uint64_t)L * Wr;
+    const uint64_t copy = blockIdx.x;
+    const uint32_t* p0 = P + copy * 2 * plane_words;
+    const uint32_t* p1 = p0 + plane_words;
+    long long unsat = 0, down = 0;
+    for (uint32_t rw = threadIdx.x; rw < plane_words; rw += blockDim.x) {
+        const uint32_t y = rw / Wr, w = rw - y * Wr;
+        const uint32_t o = (y + 1u) & 1u;
+        uint32_t up, dn, same, side;
+        bp_neighbours(p0, L, Wr, y, w, o, up, dn, same, side);
+        const uint32_t s = p1[rw];
+        unsat += __popc(s ^ up) + __popc(s ^ dn) + __popc(s ^ same) + __popc(s ^ side);
+        down += __popc(s) + __popc(p0[rw]);
+    }
+    unsat = warp_sum(unsat);
+    down = warp_sum(down);
+    __shared__ long long su[32], sd[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        su[warp] = unsat;
+        sd[warp] = down;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += su[i], b += sd[i];
+        const long long N = (long long)L * L;
+        if (E) E[copy] = (int32_t)(-(2 * N - 2 * a));
+        if (M) M[copy] = (int32_t)(N - 2 * b);
+    }
+}
+
+cudaError_t launch_bp_observables(const uint32_t* P, uint32_t L, uint64_t copies, int32_t* E, int32_t* M,
+                                  cudaStream_t s) {
+    if (copies > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_bp_observables<<<(uint32_t)copies, 256, 0, s>>>(P, L, E, M);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

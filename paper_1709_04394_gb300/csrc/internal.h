@@ -65,6 +65,16 @@ cudaError_t launch_jbits_to_int8(const uint8_t* jbits, int8_t* out, uint32_t N, 
 cudaError_t launch_observables(const int8_t* spins, const uint8_t* jbits, int dim, uint32_t L,
                                uint32_t n_inst, uint32_t R, int32_t* E, int32_t* M, cudaStream_t s);
 
+// Bit-packed 2D ferromagnet layout (one bit per spin, per-colour planes).
+cudaError_t launch_bp_init(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base, uint64_t seed,
+                           int random_start, cudaStream_t s);
+cudaError_t launch_bp_pack(const int8_t* src, uint32_t* P, uint32_t L, uint64_t copies, cudaStream_t s);
+cudaError_t launch_bp_unpack(const uint32_t* P, int8_t* dst, uint32_t L, uint64_t copies, cudaStream_t s);
+cudaError_t launch_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base,
+                                uint64_t seed, uint32_t colour, uint32_t t, uint32_t T4, uint32_t T8, cudaStream_t s);
+cudaError_t launch_bp_observables(const uint32_t* P, uint32_t L, uint64_t copies, int32_t* E, int32_t* M,
+                                  cudaStream_t s);
+
 // Resident sweep: every copy fits in one CTA's shared memory.
 size_t resident_smem_bytes(const SweepLaunch& P);
 cudaError_t launch_sweep_resident(const SweepLaunch& P, uint32_t n_ctas, uint32_t threads,
@@ -112,6 +122,19 @@ struct PaLattice {
 
 constexpr uint32_t kScanChunk = 2048;  // replicas per resampling chunk (512 threads x 4)
 
+// Grid-wide barrier of a cooperative launch. counter: zeroed before each
+// launch; err: raised when a wait exceeds `budget` cycles (the kernel then
+// returns early and the host reports GBMC_ERR_TIMEOUT). phantom: extra arrivals
+// a barrier waits for (0 in production; tests set 1 to make a wait run out).
+struct GridBarrier {
+    unsigned int* counter;
+    unsigned int* err;
+    long long budget;
+    uint32_t phantom;
+};
+
+cudaError_t launch_pa_resample_fused(const PaLattice& P, double* lnZ, const GridBarrier& B, int n_sms,
+                                     cudaStream_t s);
 cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int first_step, cudaStream_t s);
 cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s);

@@ -28,9 +28,11 @@ namespace gbmc {
 constexpr int kScanThreads = 512;
 constexpr int kPerThread = kScanChunk / kScanThreads;  // 4
 
-__global__ void __launch_bounds__(kScanThreads) k_pa_weights(const __grid_constant__ PaLattice P) {
-    __shared__ unsigned long long sh[32];
-    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+// ---- the five phases, as block-level device functions ----
+
+// Integer weights of one chunk and their inclusive sums within the chunk.
+__device__ __forceinline__ void phase_weights(const PaLattice& P, uint32_t inst, uint32_t chunk,
+                                              unsigned long long* sh) {
     const uint64_t base = (uint64_t)inst * P.R;
     const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
     const int32_t emin = P.emin[inst];
@@ -55,19 +57,10 @@ __global__ void __launch_bounds__(kScanThreads) k_pa_weights(const __grid_consta
     if (threadIdx.x == 0) P.ctot[(uint64_t)inst * P.nchunks + chunk] = total;
 }
 
-cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s) {
-    dim3 grid(P.nchunks, P.n_inst);
-    k_pa_weights<<<grid, kScanThreads, 0, s>>>(P);
-    count_launch();
-    return cudaGetLastError();
-}
-
-// One CTA per population.
-__global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLattice P, double* lnZ,
-                                                    double* lnQ_out) {
-    __shared__ double sd[32];
-    __shared__ unsigned long long su[32];
-    const uint32_t inst = blockIdx.x;
+// ln Q of one population (fixed-order fp64 tree), ln Z += ln Q, exclusive
+// scan of its chunk totals, reset of the accumulators for the next sweep.
+__device__ __forceinline__ void phase_reduce(const PaLattice& P, uint32_t inst, double* lnZ, double* lnQ_out,
+                                             double* sd, unsigned long long* su) {
     const int32_t emin = P.emin[inst], emax = P.emax[inst];
     const uint32_t bmin = (uint32_t)(emin - P.e_lo) >> 2, bmax = (uint32_t)(emax - P.e_lo) >> 2;
     uint32_t* h = P.hist + (uint64_t)inst * P.nbins;
@@ -77,7 +70,6 @@ __global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLa
         if (hb) acc += (double)hb * P.wexp[b - bmin];
         h[b] = 0u;
     }
-    // fixed-order tree: warp butterfly, then over warps
     acc = warp_sum(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (lane == 0) sd[warp] = acc;
@@ -91,13 +83,12 @@ __global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLa
             lnZ[inst] += lnQ;
         }
     }
-    // exclusive scan of the chunk totals (nchunks may exceed blockDim)
     const unsigned long long* ct = P.ctot + (uint64_t)inst * P.nchunks;
     unsigned long long* cp = P.cpre + (uint64_t)inst * (P.nchunks + 1);
     unsigned long long carry = 0;
     for (uint32_t c0 = 0; c0 < P.nchunks; c0 += blockDim.x) {
         const uint32_t c = c0 + threadIdx.x;
-        const unsigned long long v = c < P.nchunks ? ct[c] : 0ull;
+        const unsigned long long v = c < P.nchunks ? __ldcg(ct + c) : 0ull;
         unsigned long long tot;
         const unsigned long long incl = block_inclusive_scan<unsigned long long>(v, su, &tot);
         if (c < P.nchunks) cp[c] = carry + incl - v;
@@ -110,19 +101,11 @@ __global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLa
         unsigned long long* sums = P.sums + (uint64_t)inst * 4;
         sums[0] = sums[1] = sums[2] = sums[3] = 0ull;
     }
+    __syncthreads();
 }
 
-cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int /*first_step*/, cudaStream_t s) {
-    // lnQ of the step is kept next to lnZ: lnZ[n_inst .. 2 n_inst)
-    k_pa_reduce<<<P.n_inst, 1024, 0, s>>>(P, lnZ, lnZ + P.n_inst);
-    count_launch();
-    return cudaGetLastError();
-}
-
-__global__ void __launch_bounds__(256) k_pa_draws(const __grid_constant__ PaLattice P) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t total_draws = (uint64_t)P.n_inst * P.R;
-    if (g >= total_draws) return;
+// Multinomial draw g (global over the lattice's populations).
+__device__ __forceinline__ void phase_draw(const PaLattice& P, uint64_t g) {
     const uint32_t inst = (uint32_t)(g / P.R), k = (uint32_t)(g - (uint64_t)inst * P.R);
     const uint4 w = philox4x32_10(
         make_uint4(k >> 1, P.step, 0u, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
@@ -130,36 +113,29 @@ __global__ void __launch_bounds__(256) k_pa_draws(const __grid_constant__ PaLatt
     const unsigned long long U = (k & 1u) ? (((unsigned long long)w.w << 32) | w.z)
                                           : (((unsigned long long)w.y << 32) | w.x);
     const unsigned long long* cp = P.cpre + (uint64_t)inst * (P.nchunks + 1);
-    const unsigned long long x = __umul64hi(U, cp[P.nchunks]);
+    // data written by other CTAs earlier in a fused launch: read through L2 (__ldcg)
+    const unsigned long long x = __umul64hi(U, __ldcg(cp + P.nchunks));
     // least chunk c with cp[c+1] > x
     uint32_t lo = 0, hi = P.nchunks - 1;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (cp[mid + 1] > x) hi = mid;
+        if (__ldcg(cp + mid + 1) > x) hi = mid;
         else lo = mid + 1;
     }
     const uint32_t c = lo;
-    const unsigned long long xr = x - cp[c];  // cumulative within the chunk: least j with cloc[j] > xr
+    const unsigned long long xr = x - __ldcg(cp + c);  // least j of the chunk with cloc[j] > xr
     const uint64_t base = (uint64_t)inst * P.R;
     uint32_t a = c * kScanChunk, b = min(P.R, (c + 1) * kScanChunk) - 1;
     while (a < b) {
         const uint32_t mid = (a + b) >> 1;
-        if (P.cloc[base + mid] > xr) b = mid;
+        if (__ldcg(P.cloc + base + mid) > xr) b = mid;
         else a = mid + 1;
     }
     atomicAdd(&P.counts[base + a], 1u);
 }
 
-cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s) {
-    const uint64_t total = (uint64_t)P.n_inst * P.R;
-    k_pa_draws<<<(uint32_t)((total + 255) / 256), 256, 0, s>>>(P);
-    count_launch();
-    return cudaGetLastError();
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_pa_count_scan(const __grid_constant__ PaLattice P) {
-    __shared__ uint32_t sh[32];
-    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+// Exclusive scan of the counts within one chunk, chunk total.
+__device__ __forceinline__ void phase_count_scan(const PaLattice& P, uint32_t inst, uint32_t chunk, uint32_t* sh) {
     const uint64_t base = (uint64_t)inst * P.R;
     const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
     uint32_t v[kPerThread];
@@ -168,7 +144,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pa_count_scan(const __grid_con
     for (int i = 0; i < kPerThread; ++i) {
         const uint32_t j = j0 + i;
         v[i] = run;  // exclusive within the thread
-        if (j < P.R) run += P.counts[base + j];
+        if (j < P.R) run += __ldcg(P.counts + base + j);
     }
     uint32_t total;
     const uint32_t incl = block_inclusive_scan<uint32_t>(run, sh, &total);
@@ -181,28 +157,80 @@ __global__ void __launch_bounds__(kScanThreads) k_pa_count_scan(const __grid_con
     if (threadIdx.x == 0) P.ntot[(uint64_t)inst * P.nchunks + chunk] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_pa_place(const __grid_constant__ PaLattice P) {
-    __shared__ uint32_t prefix;
-    const uint32_t inst = blockIdx.y, chunk = blockIdx.x;
+// Parent j fills slots [S_j, S_j + n_j); counts are cleared for the next step.
+__device__ __forceinline__ void phase_place(const PaLattice& P, uint32_t inst, uint32_t chunk, uint32_t* prefix) {
     const uint64_t base = (uint64_t)inst * P.R;
     if (threadIdx.x < 32) {
         uint32_t acc = 0;
-        for (uint32_t c = threadIdx.x; c < chunk; c += 32) acc += P.ntot[(uint64_t)inst * P.nchunks + c];
+        for (uint32_t c = threadIdx.x; c < chunk; c += 32) acc += __ldcg(P.ntot + (uint64_t)inst * P.nchunks + c);
         acc = warp_sum(acc);
-        if (threadIdx.x == 0) prefix = acc;
+        if (threadIdx.x == 0) *prefix = acc;
     }
     __syncthreads();
-    const uint32_t pre = prefix;
+    const uint32_t pre = *prefix;
     for (uint32_t i = threadIdx.x; i < kScanChunk; i += blockDim.x) {
         const uint32_t j = chunk * kScanChunk + i;
         if (j >= P.R) break;
-        const uint32_t n = P.counts[base + j];
+        const uint32_t n = __ldcg(P.counts + base + j);
         if (n) {
-            const uint32_t S = pre + P.sloc[base + j];
+            const uint32_t S = pre + __ldcg(P.sloc + base + j);
             for (uint32_t m = 0; m < n; ++m) P.parent[base + S + m] = j;
             P.counts[base + j] = 0u;
         }
     }
+    __syncthreads();
+}
+
+// ---- separate kernels (one per phase) ----
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_weights(const __grid_constant__ PaLattice P) {
+    __shared__ unsigned long long sh[32];
+    phase_weights(P, blockIdx.y, blockIdx.x, sh);
+}
+
+cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s) {
+    dim3 grid(P.nchunks, P.n_inst);
+    k_pa_weights<<<grid, kScanThreads, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// One CTA per population.
+__global__ void __launch_bounds__(1024) k_pa_reduce(const __grid_constant__ PaLattice P, double* lnZ,
+                                                    double* lnQ_out) {
+    __shared__ double sd[32];
+    __shared__ unsigned long long su[32];
+    phase_reduce(P, blockIdx.x, lnZ, lnQ_out, sd, su);
+}
+
+cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int /*first_step*/, cudaStream_t s) {
+    // lnQ of the step is kept next to lnZ: lnZ[n_inst .. 2 n_inst)
+    k_pa_reduce<<<P.n_inst, 1024, 0, s>>>(P, lnZ, lnZ + P.n_inst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_pa_draws(const __grid_constant__ PaLattice P) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)P.n_inst * P.R) return;
+    phase_draw(P, g);
+}
+
+cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s) {
+    const uint64_t total = (uint64_t)P.n_inst * P.R;
+    k_pa_draws<<<(uint32_t)((total + 255) / 256), 256, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_count_scan(const __grid_constant__ PaLattice P) {
+    __shared__ uint32_t sh[32];
+    phase_count_scan(P, blockIdx.y, blockIdx.x, sh);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_place(const __grid_constant__ PaLattice P) {
+    __shared__ uint32_t prefix;
+    phase_place(P, blockIdx.y, blockIdx.x, &prefix);
 }
 
 cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s) {
@@ -214,6 +242,80 @@ cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s) {
     k_pa_place<<<grid, kScanThreads, 0, s>>>(P);
     count_launch();
     return cudaGetLastError();
+}
+
+// ---- fused resampling: one cooperative launch, phases separated by grid barriers ----
+
+// Grid barrier on a monotone arrival counter. Every wait is bounded: after
+// `budget` cycles the waiting thread raises *err and gives up, the kernel
+// returns, and the host reports GBMC_ERR_TIMEOUT at its next check; nothing
+// spins forever. Returns false once *err is set.
+__device__ bool grid_barrier(const GridBarrier& B, uint32_t& target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x + B.phantom;
+        __threadfence();
+        atomicAdd(B.counter, 1u);
+        const long long t0 = clock64();
+        int ok = 1;
+        while (atomicAdd(B.counter, 0u) < target) {
+            if (atomicAdd(B.err, 0u) != 0u || clock64() - t0 > B.budget) {
+                atomicExch(B.err, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_pa_resample_fused(const __grid_constant__ PaLattice P, double* lnZ,
+                                                                     const __grid_constant__ GridBarrier B) {
+    __shared__ unsigned long long sh64[32];
+    __shared__ double sd[32];
+    __shared__ uint32_t sh32[32];
+    __shared__ uint32_t prefix;
+    uint32_t target = 0;
+    const uint32_t nch = P.n_inst * P.nchunks;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) phase_weights(P, c / P.nchunks, c % P.nchunks, sh64);
+    if (!grid_barrier(B, target)) return;
+    for (uint32_t inst = blockIdx.x; inst < P.n_inst; inst += gridDim.x)
+        phase_reduce(P, inst, lnZ, lnZ + P.n_inst, sd, sh64);
+    if (!grid_barrier(B, target)) return;
+    const uint64_t total = (uint64_t)P.n_inst * P.R;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x)
+        phase_draw(P, g);
+    if (!grid_barrier(B, target)) return;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) phase_count_scan(P, c / P.nchunks, c % P.nchunks, sh32);
+    if (!grid_barrier(B, target)) return;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) phase_place(P, c / P.nchunks, c % P.nchunks, &prefix);
+}
+
+cudaError_t launch_pa_resample_fused(const PaLattice& P, double* lnZ, const GridBarrier& B, int n_sms,
+                                     cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pa_resample_fused, kScanThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t work = (uint64_t)P.n_inst * P.nchunks;
+    uint64_t grid = (uint64_t)n_sms * (uint64_t)per_sm;
+    if (grid > work * 4) grid = work * 4;  // draws use more CTAs than chunks
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(B.counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    PaLattice Pc = P;
+    double* lz = lnZ;
+    GridBarrier Bc = B;
+    void* args[] = {&Pc, &lz, &Bc};
+    e = cudaLaunchCooperativeKernel((const void*)k_pa_resample_fused, dim3((uint32_t)grid), dim3(kScanThreads), args,
+                                    0, s);
+    count_launch();
+    return e;
 }
 
 // Record of one step for every population of a lattice, after its sweeps.

@@ -101,6 +101,8 @@ def load():
             "gbmc_sync": ([p], st),
             "gbmc_destroy": ([p], st),
             "gbmc_profile": ([p, C.c_int32], st),
+            "gbmc_set_resample_mode": ([p, C.c_int32], st),
+            "gbmc_test_barrier_wait": ([p, C.c_uint32, C.c_uint64], st),
             "gbmc_profile_read": ([p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
             "gbmc_kernel_launches": ([], C.c_uint64),
             "lattice_init": ([p, C.POINTER(LatticeDesc), p, C.c_size_t, C.POINTER(C.c_void_p)], st),
@@ -186,6 +188,14 @@ def gbmc_sync(ctx):
 
 def gbmc_destroy(ctx):
     _check(load().gbmc_destroy(ctx))
+
+
+def gbmc_set_resample_mode(ctx, fused=True):
+    _check(load().gbmc_set_resample_mode(ctx, int(bool(fused))))
+
+
+def gbmc_test_barrier_wait(ctx, phantom_arrivals=0, budget_cycles=2000000000):
+    _check(load().gbmc_test_barrier_wait(ctx, phantom_arrivals, budget_cycles))
 
 
 def gbmc_profile(ctx, enable=True):

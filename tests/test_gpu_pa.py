@@ -155,3 +155,22 @@ def test_full_size_pa_2d_l64_r100000_sampled(ctx):
 def test_full_size_pa_3d_ea_32x20000_sampled(ctx):
     # 3D +-J spin glass L = 8, 32 instances x 2 10^4 replicas, beta 0 -> 3 in 201 temperatures, theta = 10
     _sampled_full_size_check(ctx, 3, 8, gbmc.GBMC_EA_PMJ, 32, 20000, 10, 200, 3.0, 2, 24, 5)
+
+
+def test_fused_and_separate_resampling_agree(ctx):
+    # one cooperative launch per lattice and step vs one launch per phase
+    runs = []
+    for fused in (True, False):
+        gbmc.gbmc_set_resample_mode(ctx, fused)
+        lat = gbmc.lattice_init(ctx, 3, 8, model=gbmc.GBMC_EA_PMJ, n_instances=4, n_replicas=2500, seed=17)
+        pa, stats = _run_gpu(ctx, [lat], 2, 4, beta_f=2.0)
+        par = np.empty(4 * 2500, dtype=np.uint32)
+        gbmc.pa_parents_out(ctx, pa, 0, par)
+        runs.append((stats, spins_out(ctx, lat), par))
+        gbmc.pa_free(pa)
+        gbmc.lattice_free(lat)
+    gbmc.gbmc_set_resample_mode(ctx, True)
+    np.testing.assert_array_equal(runs[0][0]["sumE"], runs[1][0]["sumE"])
+    np.testing.assert_array_equal(runs[0][0]["lnZ"], runs[1][0]["lnZ"])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
