@@ -294,6 +294,16 @@ gbmc_status pa_schedule_log(const gbmc_pa *pa, uint32_t lattice, gbmc_schedule_r
 /* The inverse temperatures beta_0 .. beta_i reached so far by a lattice. */
 gbmc_status pa_betas(const gbmc_pa *pa, uint32_t lattice, double *out, uint32_t capacity, uint32_t *n_out);
 
+/* pa_run for fixed schedules (linear, list) as ONE CUDA graph: from step 0
+ * (after pa_create or pa_reset) the whole run -- every resampling launch,
+ * sweep launch and record of steps 1..S -- is captured once and replayed;
+ * later calls replay it again while the stream, the lattices' seeds, starting
+ * buffers and sweep counters and the resampling mode are unchanged (else it
+ * is captured anew). The graph uses one launch per resampling phase (plain
+ * kernel nodes). Same results as pa_run. Synchronises. */
+gbmc_status pa_run_graph(gbmc_ctx *ctx, gbmc_pa *pa, gbmc_pa_stats *stats_host, uint32_t stats_capacity,
+                         uint32_t *n_steps_done);
+
 /* Replica each slot was copied from in the last resampling (device or host
  * dst, uint32 [n_copies] of that lattice; indices within the instance). */
 gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, uint32_t *dst,

@@ -185,6 +185,12 @@ struct gbmc_pa {
     float* mlp_dev = nullptr;        // MLP parameters (GBMC_SCHED_MLP)
     std::vector<void*> allocs;
     std::vector<void*> host_allocs;
+    // CUDA graph of a whole fixed-schedule run (pa_run_graph) and the state it
+    // starts from / leaves behind
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uint64_t> graph_key;
+    std::vector<int8_t*> graph_end_cur;
+    std::vector<uint32_t> graph_end_t;
 };
 
 namespace {
@@ -1119,6 +1125,7 @@ gbmc_status pa_free(gbmc_pa* pa) {
         }
         l->run = nullptr;
     }
+    if (pa->graph) cudaGraphExecDestroy(pa->graph);
     for (void* p : pa->allocs) cudaFree(p);
     for (void* p : pa->host_allocs) cudaFreeHost(p);
     delete pa;
@@ -1320,6 +1327,91 @@ gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32
         gbmc_status st = pa->adaptive ? pa_enqueue_adaptive(pa, nullptr) : pa_enqueue_fixed(pa);
         if (st != GBMC_OK) return st;
     }
+    if (stats_host) {
+        const uint32_t rows = capacity < pa->step + 1 ? capacity : pa->step + 1;
+        CUDA_TRY(cudaMemcpyAsync(stats_host, pa->stats, (uint64_t)rows * pa->P * sizeof(gbmc_pa_stats),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (n_done) *n_done = pa->step;
+    return check_device_error(ctx);
+}
+
+// What a captured run depends on besides the run's own buffers: stream, each
+// lattice's seed, starting buffer and sweep counter, and the resampling mode.
+static std::vector<uint64_t> graph_key(const gbmc_pa* pa) {
+    std::vector<uint64_t> k{(uint64_t)(uintptr_t)pa->ctx->stream, (uint64_t)pa->ctx->fused};
+    for (auto& pl : pa->lats) {
+        k.push_back(pl.lat->d.seed);
+        k.push_back((uint64_t)(uintptr_t)pl.lat->cur);
+        k.push_back(pl.t_start);
+    }
+    return k;
+}
+
+gbmc_status pa_run_graph(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32_t capacity, uint32_t* n_done) {
+    if (!ctx || !pa) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (pa->adaptive) return fail(GBMC_ERR_ARG, "graph runs need a fixed schedule (linear or list)");
+    if (pa->step != 0) return fail(GBMC_ERR_STATE, "graph runs start from step 0 (call pa_reset)");
+    pa->ctx = ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const std::vector<uint64_t> key = graph_key(pa);
+    if (!pa->graph || key != pa->graph_key) {
+        if (pa->graph) {
+            cudaGraphExecDestroy(pa->graph);
+            pa->graph = nullptr;
+        }
+        // capture steps 1..S exactly as pa_run would enqueue them
+        std::vector<int8_t*> cur0;
+        std::vector<uint32_t> t0;
+        for (auto& pl : pa->lats) {
+            cur0.push_back(pl.lat->cur);
+            t0.push_back(pl.lat->t);
+        }
+        // captured with one launch per resampling phase (plain kernel nodes)
+        const bool prof = ctx->prof, fused = ctx->fused;
+        ctx->prof = false;
+        ctx->fused = false;
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        gbmc_status st = GBMC_OK;
+        while (st == GBMC_OK && !pa_finished(pa)) st = pa_enqueue_fixed(pa);
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        ctx->prof = prof;
+        ctx->fused = fused;
+        pa->graph_end_cur.clear();
+        pa->graph_end_t.clear();
+        for (auto& pl : pa->lats) {
+            pa->graph_end_cur.push_back(pl.lat->cur);
+            pa->graph_end_t.push_back(pl.lat->t);
+        }
+        // the capture only recorded the work: put the host state back to step 0
+        for (size_t i = 0; i < pa->lats.size(); ++i) {
+            pa->lats[i].lat->cur = cur0[i];
+            pa->lats[i].lat->t = t0[i];
+            pa->lats[i].steps = 0;
+        }
+        pa->step = 0;
+        if (st != GBMC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(GBMC_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&pa->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            pa->graph = nullptr;
+            return fail(GBMC_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ce));
+        }
+        pa->graph_key = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(pa->graph, ctx->stream));
+    for (size_t i = 0; i < pa->lats.size(); ++i) {
+        pa->lats[i].lat->cur = pa->graph_end_cur[i];
+        pa->lats[i].lat->t = pa->graph_end_t[i];
+        pa->lats[i].steps = pa->S;
+    }
+    pa->step = pa->S;
     if (stats_host) {
         const uint32_t rows = capacity < pa->step + 1 ? capacity : pa->step + 1;
         CUDA_TRY(cudaMemcpyAsync(stats_host, pa->stats, (uint64_t)rows * pa->P * sizeof(gbmc_pa_stats),

@@ -131,6 +131,7 @@ def load():
             "pa_populations": ([p, C.POINTER(C.c_uint32)], st),
             "pa_step": ([p, p, p, p], st),
             "pa_run": ([p, p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
+            "pa_run_graph": ([p, p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
             "pa_parents_out": ([p, p, C.c_uint32, p, C.c_size_t], st),
             "pa_energies_out": ([p, p, C.c_uint32, p, p, C.c_size_t], st),
         }
@@ -328,6 +329,18 @@ def pa_run(ctx, pa, capacity=None):
         out = np.zeros((capacity, P), dtype=PA_STATS_DTYPE)
     n = C.c_uint32()
     _check(load().pa_run(ctx, pa, _ptr(out), cap, C.byref(n)))
+    return (out[: n.value + 1] if out is not None else None), n.value
+
+
+def pa_run_graph(ctx, pa, capacity=None):
+    P = pa_populations(pa)
+    out = None
+    cap = 0
+    if capacity is not None:
+        cap = capacity
+        out = np.zeros((capacity, P), dtype=PA_STATS_DTYPE)
+    n = C.c_uint32()
+    _check(load().pa_run_graph(ctx, pa, _ptr(out), cap, C.byref(n)))
     return (out[: n.value + 1] if out is not None else None), n.value
 
 

@@ -174,3 +174,33 @@ def test_fused_and_separate_resampling_agree(ctx):
     np.testing.assert_array_equal(runs[0][0]["lnZ"], runs[1][0]["lnZ"])
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
     np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
+def test_graph_run_equals_stream_run_and_replays(ctx):
+    # the whole fixed-schedule run as one CUDA graph, replayed after resets
+    L, R, S, theta = 32, 3000, 6, 2
+    a = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=12)
+    b = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=12)
+    pa_a, ref = _run_gpu(ctx, [a], theta, S)
+    pa_b = gbmc.pa_create(ctx, [b], theta, S)
+    for rep in range(3):
+        if rep:
+            gbmc.pa_reset(ctx, pa_b, True, 0)
+        got, n = gbmc.pa_run_graph(ctx, pa_b, capacity=S + 1)
+        assert n == S
+        np.testing.assert_array_equal(got["sumE"], ref["sumE"])
+        np.testing.assert_array_equal(got["lnZ"], ref["lnZ"])
+        np.testing.assert_array_equal(spins_out(ctx, b), spins_out(ctx, a))
+        assert gbmc.lattice_info(b).sweep_counter == gbmc.lattice_info(a).sweep_counter
+    with pytest.raises(gbmc.GbmcError):
+        gbmc.pa_run_graph(ctx, pa_b)  # not at step 0
+    # a new seed is captured anew and matches the oracle
+    gbmc.pa_reset(ctx, pa_b, True, 99)
+    got, _ = gbmc.pa_run_graph(ctx, pa_b, capacity=S + 1)
+    ref99 = oracle.pa_run(2, L, 99, 0, R, oracle.linear_betas(1.0, S), theta)
+    np.testing.assert_array_equal(got[:, 0]["sumE"], ref99["sumE"])
+    np.testing.assert_array_equal(spins_out(ctx, b), ref99["spins"])
+    for p in (pa_a, pa_b):
+        gbmc.pa_free(p)
+    gbmc.lattice_free(a)
+    gbmc.lattice_free(b)
