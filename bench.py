@@ -303,8 +303,11 @@ def run_gpu(args, w, ws, rank, local):
     return result
 
 
-LEARNED = dict(Ls=(32, 64, 128, 256), R=50000, theta=10, beta_f=1.0, target=0.85, lo=0.80, hi=0.90,
-               dbeta_max=0.05, cap=4000, bar=1e-4)
+# MLP proposals are kept when their realised overlap lies in [0.85, 0.90]: never a
+# less conservative step than the bisection target; the network is trained
+# towards 0.97 x the bisection step so that most proposals land in the band.
+LEARNED = dict(Ls=(32, 64, 128, 256), R=50000, theta=10, beta_f=1.0, target=0.85, lo=0.85, hi=0.90,
+               dbeta_max=0.05, cap=4000, bar=1e-4, train_shrink=0.97)
 
 
 def run_learned(args):
@@ -361,7 +364,7 @@ def run_learned(args):
         for r in log:
             if r["kind"] == 1 and not r["clamped"]:
                 X.append(r["features"])
-                T.append(math.log(r["dbeta"] * math.sqrt(max(r["var"], 1e-12))))
+                T.append(math.log(cfg["train_shrink"] * r["dbeta"] * math.sqrt(max(r["var"], 1e-12))))
     X = torch.tensor(np.array(X, dtype=np.float32), device="cuda")
     T = torch.tensor(np.array(T, dtype=np.float32), device="cuda")
     rng = np.random.default_rng(5)

@@ -188,6 +188,7 @@ struct gbmc_pa {
     // CUDA graph of a whole fixed-schedule run (pa_run_graph) and the state it
     // starts from / leaves behind
     cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture_stream = nullptr;  // capture cannot use the legacy default stream
     std::vector<uint64_t> graph_key;
     std::vector<int8_t*> graph_end_cur;
     std::vector<uint32_t> graph_end_t;
@@ -1126,6 +1127,7 @@ gbmc_status pa_free(gbmc_pa* pa) {
         l->run = nullptr;
     }
     if (pa->graph) cudaGraphExecDestroy(pa->graph);
+    if (pa->capture_stream) cudaStreamDestroy(pa->capture_stream);
     for (void* p : pa->allocs) cudaFree(p);
     for (void* p : pa->host_allocs) cudaFreeHost(p);
     delete pa;
@@ -1368,15 +1370,22 @@ gbmc_status pa_run_graph(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, 
             cur0.push_back(pl.lat->cur);
             t0.push_back(pl.lat->t);
         }
-        // captured with one launch per resampling phase (plain kernel nodes)
+        // captured on a library stream (the caller's may be the legacy default
+        // stream), with one launch per resampling phase (plain kernel nodes)
+        if (!pa->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&pa->capture_stream, cudaStreamNonBlocking));
         const bool prof = ctx->prof, fused = ctx->fused;
+        cudaStream_t user_stream = ctx->stream;
         ctx->prof = false;
         ctx->fused = false;
+        ctx->stream = pa->capture_stream;
         cudaGraph_t g = nullptr;
-        CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
         gbmc_status st = GBMC_OK;
-        while (st == GBMC_OK && !pa_finished(pa)) st = pa_enqueue_fixed(pa);
-        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        if (ce == cudaSuccess) {
+            while (st == GBMC_OK && !pa_finished(pa)) st = pa_enqueue_fixed(pa);
+            ce = cudaStreamEndCapture(ctx->stream, &g);
+        }
+        ctx->stream = user_stream;
         ctx->prof = prof;
         ctx->fused = fused;
         pa->graph_end_cur.clear();
