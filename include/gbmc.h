@@ -56,6 +56,7 @@ enum { GBMC_START_ALL_UP = 0, GBMC_START_RANDOM = 1 };  /* initial state */
 typedef struct gbmc_ctx gbmc_ctx;
 typedef struct gbmc_lattice gbmc_lattice;
 typedef struct gbmc_pa gbmc_pa;
+typedef struct gbmc_pt gbmc_pt;
 
 /* Library version (major*10000 + minor*100 + patch). */
 int gbmc_version(void);
@@ -312,6 +313,28 @@ gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, u
  * (device or host int32 [n_copies]). */
 gbmc_status pa_energies_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, int32_t *E_dst,
                             int32_t *M_dst, size_t count);
+
+/* ------------------------------------------------------------------------ */
+/* Parallel tempering (Sec. 5.1, Eq. (10)), on the same sweep kernel: each    */
+/* instance's n_replicas copies are the T replicas, temperature k at          */
+/* betas[k] (ascending). One step: theta sweeps of every copy at the beta of  */
+/* its current temperature, then one exchange round over the pairs (k, k+1),  */
+/* k = round mod 2, round mod 2 + 2, ...: accepted with probability           */
+/* min(1, exp((beta_k - beta_{k+1})(E_a - E_b))) -- always if E_b >= E_a, else */
+/* iff the pair's Philox word (purpose 4: q = k>>2, word k&3, t = round,      */
+/* r = 0) is <= ceil(exp(-(beta_{k+1}-beta_k)(E_a-E_b)) 2^32) - 1 (host fp64). */
+/* Swaps exchange temperature labels (two maps), not configurations. The     */
+/* lattice (int8, shared-memory resident) belongs to the run until pt_free.  */
+/* ------------------------------------------------------------------------ */
+gbmc_status pt_create(gbmc_ctx *ctx, gbmc_lattice *lat, const double *betas /* host [n_replicas] */,
+                      uint32_t theta, gbmc_pt **out);
+gbmc_status pt_step(gbmc_ctx *ctx, gbmc_pt *pt, uint32_t n_steps);
+/* rep_of: [n_instances][T] configuration at each temperature; accepted:
+ * [n_instances][T-1] accepted swaps of each pair so far; E: [n_instances][T]
+ * energy of each configuration after the last step. Host or device; any may
+ * be NULL. Synchronises. */
+gbmc_status pt_state_out(gbmc_ctx *ctx, const gbmc_pt *pt, uint32_t *rep_of, uint32_t *accepted, int32_t *E);
+gbmc_status pt_free(gbmc_pt *pt);
 
 /* ------------------------------------------------------------------------ */
 /* Schedule MLP: 6 inputs -> 64 tanh -> 64 tanh -> 1, output y = log(dbeta   */

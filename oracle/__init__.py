@@ -61,6 +61,7 @@ def _load():
         lib.orc_resample.argtypes = [u32, p, dbl, u64, u32, u32, p]
         lib.orc_resample.restype = dbl
         lib.orc_children_order.argtypes = [u32, p, p]
+        lib.orc_pt_run.argtypes = [i32, i32, p, u64, u32, u32, p, u32, u32, u32, u32, p, p, p, p]
         lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
                                    p, p, p, p, p, p, p, p, p, p, p]
         _lib = lib
@@ -189,3 +190,23 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_ene
     out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents, E_steps=E_steps,
                spins=spins.reshape(R, N), betas=betas)
     return out
+
+
+def pt_run(dim, L, seed, instance, betas, theta, n_steps, J=None, spins=None, rep_of=None, accepted=None,
+           t0=0, round0=0):
+    """Parallel tempering (Sec. 5.1, Eq. (10)) of len(betas) replicas of one instance.
+    Returns (spins [T, N], rep_of [T], accepted [T-1], E [T]) after n_steps steps."""
+    lib = _load()
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    T = betas.size
+    N = n_sites(dim, L)
+    if spins is None:
+        spins = np.stack([init_spins(dim, L, seed, instance, r, True) for r in range(T)])
+    spins = np.ascontiguousarray(spins, dtype=np.int8).reshape(T, N).copy()
+    rep_of = np.arange(T, dtype=np.uint32) if rep_of is None else np.ascontiguousarray(rep_of, dtype=np.uint32).copy()
+    accepted = np.zeros(T - 1, dtype=np.uint32) if accepted is None else np.ascontiguousarray(accepted, dtype=np.uint32).copy()
+    E = np.zeros(T, dtype=np.int64)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    lib.orc_pt_run(dim, L, _ptr(Jc), seed, instance, T, _ptr(betas), theta, n_steps, t0, round0, _ptr(spins),
+                   _ptr(rep_of), _ptr(accepted), _ptr(E))
+    return spins, rep_of, accepted, E

@@ -420,3 +420,58 @@ void orc_philox_batch(int64_t n, const uint32_t *ctr, const uint32_t key[2], uin
 {
     for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Parallel tempering (Sec. 5.1, Eq. (10)) of T replicas of one instance.     */
+/* Temperature k has inverse temperature betas[k] (ascending); rep_of[k] is   */
+/* the configuration currently at temperature k. One step: theta sweeps of    */
+/* every configuration r at the beta of its temperature (sweep counters       */
+/* t0 + step*theta + s, replica index r), its energy, then one exchange round */
+/* over the pairs (k, k+1) with k = round mod 2, 4, ... Pair (k, k+1) holding  */
+/* configurations a, b is swapped with probability min(1, e^D),               */
+/* D = (beta_k - beta_{k+1}) (E_a - E_b): always if E_b >= E_a, else iff the   */
+/* pair's 32-bit word u (purpose 4: q = k>>2, word k&3, t = round, r = 0)     */
+/* satisfies u <= ceil(exp(-(dbeta (E_a - E_b))) 2^32) - 1 (reading R2).      */
+/* Swaps exchange temperature labels, not configurations.                     */
+/* ------------------------------------------------------------------------ */
+void orc_pt_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t T,
+                const double *betas, uint32_t theta, uint32_t n_steps, uint32_t t0, uint32_t round0,
+                int8_t *spins, uint32_t *rep_of, uint32_t *accepted, int64_t *E_out)
+{
+    int64_t N = orc_nsites(dim, L);
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * T);
+    uint32_t *temp_of = (uint32_t *)malloc(sizeof(uint32_t) * T);
+    for (uint32_t k = 0; k < T; ++k) temp_of[rep_of[k]] = k;
+    for (uint32_t step = 0; step < n_steps; ++step) {
+        for (uint32_t r = 0; r < T; ++r) {
+            orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[temp_of[r]], seed, instance, r,
+                       t0 + step * theta, theta);
+            int64_t M;
+            orc_observables(dim, L, spins + (size_t)r * N, J, &E[r], &M);
+        }
+        uint32_t round = round0 + step;
+        for (uint32_t k = round % 2; k + 1 < T; k += 2) {
+            uint32_t a = rep_of[k], b = rep_of[k + 1];
+            int accept;
+            if (E[b] >= E[a]) {
+                accept = 1;
+            } else {
+                double dbeta = betas[k + 1] - betas[k];
+                double p = exp(-(dbeta * (double)(E[a] - E[b])));
+                int64_t thr = (int64_t)ceil(ldexp(p, 32)) - 1;
+                uint32_t u = orc_word(seed, k >> 2, round, 0u, (4u << 28) | instance, k & 3u);
+                accept = (int64_t)u <= thr;
+            }
+            if (accept) {
+                rep_of[k] = b;
+                rep_of[k + 1] = a;
+                temp_of[b] = k;
+                temp_of[a] = k + 1;
+                accepted[k] += 1;
+            }
+        }
+    }
+    if (E_out) memcpy(E_out, E, sizeof(int64_t) * T);
+    free(E);
+    free(temp_of);
+}

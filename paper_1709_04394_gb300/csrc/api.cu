@@ -1634,4 +1634,145 @@ gbmc_status mlp_train(gbmc_ctx* ctx, float* params, const float* X, const float*
     return st;
 }
 
+// ------------------------------------------------------------------------
+// Parallel tempering (Sec. 5.1)
+// ------------------------------------------------------------------------
+
+struct gbmc_pt {
+    gbmc_ctx* ctx;
+    gbmc_lattice* lat;
+    std::vector<double> betas;
+    uint32_t T, M, theta, round;
+    uint32_t* thr_temp = nullptr;
+    uint32_t *temp_of = nullptr, *rep_of = nullptr, *accepted = nullptr;
+    int32_t *E = nullptr, *Mag = nullptr;
+    long long* tab = nullptr;
+    std::vector<void*> allocs;
+};
+
+gbmc_status pt_create(gbmc_ctx* ctx, gbmc_lattice* l, const double* betas, uint32_t theta, gbmc_pt** out) {
+    if (!ctx || !l || !betas || !out) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice is used by an annealing run");
+    if (l->d.layout != GBMC_INT8) return fail(GBMC_ERR_ARG, "parallel tempering runs on the int8 layout");
+    const Tuning tu = tune(l);
+    if (!tu.resident) return fail(GBMC_ERR_ARG, "lattice too large for shared-memory resident sweeps");
+    const uint32_t T = l->d.n_replicas;
+    for (uint32_t k = 0; k < T; ++k) {
+        if (!beta_ok(betas[k], l->d.dim)) return fail(GBMC_ERR_ARG, "beta[%u] out of range", k);
+        if (k > 0 && !(betas[k] >= betas[k - 1])) return fail(GBMC_ERR_ARG, "betas must be ascending");
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    gbmc_pt* pt = new (std::nothrow) gbmc_pt;
+    if (!pt) return fail(GBMC_ERR_OOM, "host allocation");
+    pt->ctx = ctx;
+    pt->lat = l;
+    pt->betas.assign(betas, betas + T);
+    pt->T = T;
+    pt->M = (uint32_t)(l->d.dim * l->N / 2);
+    pt->theta = theta;
+    pt->round = 0;
+    const uint64_t C = l->ncopies;
+    auto alloc = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) return false;
+        pt->allocs.push_back(*p);
+        return true;
+    };
+    bool ok = alloc((void**)&pt->thr_temp, 12ull * T) && alloc((void**)&pt->temp_of, 4 * C) &&
+              alloc((void**)&pt->rep_of, 4 * C) && alloc((void**)&pt->accepted, 4ull * l->d.n_instances * (T > 1 ? T - 1 : 1)) &&
+              alloc((void**)&pt->E, 4 * C) && alloc((void**)&pt->Mag, 4 * C) &&
+              alloc((void**)&pt->tab, 8ull * (T > 1 ? T - 1 : 1) * (pt->M + 1));
+    if (!ok) {
+        for (void* p : pt->allocs) cudaFree(p);
+        delete pt;
+        return fail(GBMC_ERR_OOM, "cudaMalloc for parallel tempering");
+    }
+    std::vector<uint32_t> thr(3ull * T), ident(C);
+    for (uint32_t k = 0; k < T; ++k) thresholds(betas[k], &thr[3ull * k]);
+    for (uint64_t c = 0; c < C; ++c) ident[c] = (uint32_t)(c % T);
+    std::vector<long long> tab((uint64_t)(T > 1 ? T - 1 : 1) * (pt->M + 1), 0);
+    for (uint32_t k = 0; k + 1 < T; ++k) {
+        const double dbeta = betas[k + 1] - betas[k];
+        for (uint32_t m = 0; m <= pt->M; ++m) {
+            const double p = std::exp(-(dbeta * (double)(4ll * m)));
+            tab[(uint64_t)k * (pt->M + 1) + m] = (long long)std::ceil(std::ldexp(p, 32)) - 1;
+        }
+    }
+    cudaError_t e = cudaMemcpy(pt->thr_temp, thr.data(), 12ull * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pt->temp_of, ident.data(), 4 * C, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pt->rep_of, ident.data(), 4 * C, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(pt->accepted, 0, 4ull * l->d.n_instances * (T > 1 ? T - 1 : 1));
+    if (e == cudaSuccess) e = cudaMemcpy(pt->tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        for (void* p : pt->allocs) cudaFree(p);
+        delete pt;
+        return fail(GBMC_ERR_CUDA, "parallel tempering set-up: %s", cudaGetErrorString(e));
+    }
+    l->run = (gbmc_pa*)pt;  // the lattice is owned by this run until pt_free
+    *out = pt;
+    return GBMC_OK;
+}
+
+gbmc_status pt_step(gbmc_ctx* ctx, gbmc_pt* pt, uint32_t n_steps) {
+    if (!ctx || !pt) return fail(GBMC_ERR_ARG, "NULL argument");
+    pt->ctx = ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    gbmc_lattice* l = pt->lat;
+    if ((uint64_t)l->t + (uint64_t)n_steps * pt->theta > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "sweep counter would wrap");
+    for (uint32_t n = 0; n < n_steps; ++n) {
+        const Tuning tu = tune(l);
+        SweepJob J = base_job(l, tu);
+        J.nsweeps = pt->theta;
+        J.E = pt->E;
+        J.M = pt->Mag;
+        J.thr_temp = pt->thr_temp;
+        J.temp_of = pt->temp_of;
+        SweepLaunch P;
+        std::memset(&P, 0, sizeof(P));
+        P.jobs[0] = J;
+        P.njobs = 1;
+        P.dim = l->d.dim;
+        P.ea = l->d.model == GBMC_EA_PMJ;
+        P.swar = (l->d.L % 8) == 0;
+        gbmc_status st = launch_jobs(ctx, P, std::vector<Tuning>{tu});
+        if (st != GBMC_OK) return st;
+        l->t += pt->theta;
+        PtExchange X;
+        X.E = pt->E;
+        X.rep_of = pt->rep_of;
+        X.temp_of = pt->temp_of;
+        X.accepted = pt->accepted;
+        X.tab = pt->tab;
+        X.seed = l->d.seed;
+        X.T = pt->T;
+        X.M = pt->M;
+        X.n_inst = l->d.n_instances;
+        X.inst_base = l->d.instance_base;
+        X.round = pt->round++;
+        CUDA_TRY(launch_pt_exchange(X, ctx->stream));
+    }
+    return GBMC_OK;
+}
+
+gbmc_status pt_state_out(gbmc_ctx* ctx, const gbmc_pt* pt, uint32_t* rep_of, uint32_t* accepted, int32_t* E) {
+    if (!ctx || !pt) return fail(GBMC_ERR_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const gbmc_lattice* l = pt->lat;
+    if (rep_of) CUDA_TRY(cudaMemcpyAsync(rep_of, pt->rep_of, 4 * l->ncopies, cudaMemcpyDefault, ctx->stream));
+    if (accepted)
+        CUDA_TRY(cudaMemcpyAsync(accepted, pt->accepted, 4ull * l->d.n_instances * (pt->T > 1 ? pt->T - 1 : 0),
+                                 cudaMemcpyDefault, ctx->stream));
+    if (E) CUDA_TRY(cudaMemcpyAsync(E, pt->E, 4 * l->ncopies, cudaMemcpyDefault, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBMC_OK;
+}
+
+gbmc_status pt_free(gbmc_pt* pt) {
+    if (!pt) return GBMC_OK;
+    cudaStreamSynchronize(pt->ctx->stream);
+    pt->lat->run = nullptr;
+    for (void* p : pt->allocs) cudaFree(p);
+    delete pt;
+    return GBMC_OK;
+}
+
 }  // extern "C"

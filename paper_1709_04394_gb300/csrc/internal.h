@@ -39,6 +39,8 @@ struct SweepJob {
     uint32_t nbins;
     uint32_t rpc;             // replicas per CTA (CTAs never straddle instances)
     uint32_t ctas_per_inst;
+    const uint32_t* thr_temp; // parallel tempering: [T][3] thresholds per temperature, or null
+    const uint32_t* temp_of;  // parallel tempering: [n_inst*R] temperature of each copy, or null
 };
 
 struct SweepLaunch {
@@ -141,6 +143,18 @@ cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_record(const PaLattice& P, const double* lnZ, double lnQ_unused, cudaStream_t s);
 cudaError_t launch_pa_reset(const PaLattice& P, cudaStream_t s);
+
+// ---- parallel tempering exchanges (Sec. 5.1, Eq. (10)) ----
+struct PtExchange {
+    const int32_t* E;          // [n_inst*T] energy of each configuration
+    uint32_t* rep_of;          // [n_inst*T] configuration at each temperature
+    uint32_t* temp_of;         // [n_inst*T] temperature of each configuration
+    uint32_t* accepted;        // [n_inst*(T-1)] accepted swaps per pair
+    const long long* tab;      // [T-1][M+1] threshold of pair k at energy gap 4m (-1: never)
+    uint64_t seed;
+    uint32_t T, M, n_inst, inst_base, round;
+};
+cudaError_t launch_pt_exchange(const PtExchange& X, cudaStream_t s);
 
 // ---- schedule MLP (6 -> 64 -> 64 -> 1) ----
 constexpr int kMlpIn = 6;

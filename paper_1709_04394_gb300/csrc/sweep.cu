@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int acc_e[64], acc_m[64];
     __shared__ __align__(16) uint32_t s_tbl[8];
+    __shared__ __align__(16) uint32_t s_tblc[64][8];  // per-copy tables (parallel tempering)
     int jid = 0;
     while (jid + 1 < P.njobs && blockIdx.x >= P.cta_begin[jid + 1]) ++jid;
     const SweepJob& J = P.jobs[jid];
@@ -386,6 +387,15 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
         const int d = DIM - (int)threadIdx.x;
         s_tbl[threadIdx.x] = d <= 0 ? 0xFFFFFFFFu : (d == 1 ? J.thr[0] : (d == 2 ? J.thr[1] : J.thr[2]));
     }
+    if (J.temp_of) {
+        // each copy at its own temperature: its own table
+        for (uint32_t i = threadIdx.x; i < nrep * 8; i += blockDim.x) {
+            const uint32_t c = i >> 3, a = i & 7u;
+            const uint32_t* th = J.thr_temp + 3ull * J.temp_of[slot0 + c];
+            const int d = DIM - (int)a;
+            s_tblc[c][a] = d <= 0 ? 0xFFFFFFFFu : th[d - 1];
+        }
+    }
     __syncthreads();
 
     const uint32_t tpr = blockDim.x / J.rpc;
@@ -394,10 +404,14 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
     const bool active = c < nrep;
     uint8_t* sp = smem + c * stride_b;
     const uint8_t* jb = EA ? jsm : nullptr;
-    const uint8_t* tbl = reinterpret_cast<const uint8_t*>(s_tbl);
+    const uint8_t* tbl = reinterpret_cast<const uint8_t*>(J.temp_of ? s_tblc[active ? c : 0] : s_tbl);
     const uint32_t r = r0 + c;
     const uint32_t instance = J.inst_base + inst;
-    const Thr T{J.thr[0], J.thr[1], J.thr[2]};
+    Thr T{J.thr[0], J.thr[1], J.thr[2]};
+    if (J.temp_of && active) {
+        const uint32_t* th = J.thr_temp + 3ull * J.temp_of[slot0 + c];
+        T = Thr{th[0], th[1], th[2]};
+    }
     const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
     const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
     const bool want_final = J.E || J.M || J.hist;

@@ -123,6 +123,10 @@ def load():
             "mlp_grad": ([p, p, p, p, C.c_uint32, p, p], st),
             "mlp_adam": ([p, p, p, p, p, C.c_uint32, C.c_float], st),
             "mlp_train": ([p, p, p, p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_float, p], st),
+            "pt_create": ([p, p, p, C.c_uint32, C.POINTER(C.c_void_p)], st),
+            "pt_step": ([p, p, C.c_uint32], st),
+            "pt_state_out": ([p, p, p, p, p], st),
+            "pt_free": ([p], st),
             "pa_resample_static": ([p, C.c_int32, C.c_int32, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32,
                                     C.c_uint64, C.c_uint32, C.c_double, p, p, p], st),
             "pa_create": ([p, C.POINTER(C.c_void_p), C.c_uint32, C.POINTER(PaConfig), C.POINTER(C.c_void_p)], st),
@@ -407,3 +411,22 @@ def mlp_adam(ctx, params, grad, m, v, k, lr):
 def mlp_train(ctx, params, X, T, epochs, batch, lr, loss_out=None):
     _check(load().mlp_train(ctx, _ptr(params), _ptr(X), _ptr(T), X.shape[0], epochs, batch, float(lr),
                             _ptr(loss_out)))
+
+
+def pt_create(ctx, lat, betas, theta):
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    h = C.c_void_p()
+    _check(load().pt_create(ctx, lat, b.ctypes.data, theta, C.byref(h)))
+    return h
+
+
+def pt_step(ctx, pt, n_steps=1):
+    _check(load().pt_step(ctx, pt, n_steps))
+
+
+def pt_state_out(ctx, pt, rep_of=None, accepted=None, E=None):
+    _check(load().pt_state_out(ctx, pt, _ptr(rep_of), _ptr(accepted), _ptr(E)))
+
+
+def pt_free(pt):
+    _check(load().pt_free(pt))
