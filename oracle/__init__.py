@@ -57,6 +57,7 @@ def _load():
         lib.orc_couplings.argtypes = [i32, u64, u32, p]
         lib.orc_halfsweep.argtypes = [i32, i32, p, p, p, u64, u32, u32, u32, i32]
         lib.orc_sweeps.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, u32, u32]
+        lib.orc_dcb_sweeps.argtypes = [i32, i32, p, dbl, u64, u32, u32, u32, u32, u32]
         lib.orc_observables.argtypes = [i32, i32, p, p, p, p]
         lib.orc_resample.argtypes = [u32, p, dbl, u64, u32, u32, p]
         lib.orc_resample.restype = dbl
@@ -127,6 +128,17 @@ def sweeps(dim, L, s, J, beta, seed, instance, replica, t0, n):
     _check_spins(s, dim, L)
     Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
     lib.orc_sweeps(dim, L, _ptr(s), _ptr(Jc), float(beta), seed, instance, replica, t0, n)
+
+
+def dcb_sweeps(L, tile, s, beta, seed, instance, replica, t0, k, n_rounds):
+    """n_rounds double-checkerboard rounds (k sweeps per tile and round) of a
+    2D ferromagnet ``s`` (int8, in place); the sweep counter advances by k
+    per round."""
+    lib = _load()
+    _check_spins(s, 2, L)
+    if tile <= 0 or tile % 2 or L % (2 * tile):
+        raise ValueError("L must be a multiple of 2 * tile")
+    lib.orc_dcb_sweeps(L, tile, _ptr(s), float(beta), seed, instance, replica, t0, k, n_rounds)
 
 
 def observables(dim, L, s, J=None):

@@ -42,6 +42,7 @@
  *      summed over energy levels in increasing E.
  *   R9 J_{i,mu} = +1 if the top bit of its COUPLING word is 0, else -1.
  *  R10 ln Z(beta_0 = 0) = N ln 2; ln Z_i = ln Z_{i-1} + ln Q_i.
+ *  R16 double checkerboard: see orc_dcb_sweeps.
  */
 #include <math.h>
 #include <stdint.h>
@@ -194,8 +195,14 @@ void orc_couplings(int L, uint64_t seed, uint32_t instance, int8_t *J)
 /* ------------------------------------------------------------------------ */
 /* Steps 2-3 of the Sec. 3.1 list for every site of one sub-lattice.          */
 /* ------------------------------------------------------------------------ */
-void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
-                   uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour)
+/* Metropolis updates of the colour-`colour` sites; with tile > 0 (2D only)
+ * just those in tiles of coarse colour `coarse` (Fig. 5, right: tile (a, b)
+ * holds the sites with x / tile = a, y / tile = b; its coarse colour is
+ * (a + b) mod 2). The updated sites are never neighbours, so the order within
+ * the loop does not matter. */
+static void orc_update_sites(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
+                             uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour,
+                             int tile, int coarse)
 {
     int64_t N = orc_nsites(dim, L);
     uint32_t c3 = orc_c3(ORC_PURPOSE_METRO, (uint32_t)colour, instance);
@@ -203,6 +210,7 @@ void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *th
         int x, y, z;
         orc_coords(dim, L, i, &x, &y, &z);
         if (((x + y + z) & 1) != colour) continue;
+        if (tile > 0 && ((x / tile + y / tile) & 1) != coarse) continue;
         /* rank among the sites of this colour, row-major */
         int64_t row = dim == 3 ? (int64_t)z * L + y : (int64_t)y;
         int64_t k = row * (L / 2) + (x >> 1);
@@ -223,6 +231,33 @@ void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *th
         }
         if (accept) s[i] = (int8_t)(-s[i]);
     }
+}
+
+void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
+                   uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour)
+{
+    orc_update_sites(dim, L, s, J, thr, seed, instance, replica, t, colour, 0, 0);
+}
+
+/* Double checkerboard with k hits per tile (Sec. 3.1, Fig. 5 right, the
+ * multi-hit variant): n_rounds rounds of the 2D lattice cut into tile x tile
+ * tiles (L a multiple of 2 tile). A round takes the tiles of coarse colour 0,
+ * then those of coarse colour 1; the tiles of one coarse colour each get k
+ * full checkerboard sweeps (fine colour 0, then 1) while every site outside
+ * them stays fixed. Reading R16: the j-th sweep of a tile in round m uses the
+ * sweep counter t0 + k m + j for the Philox words of its sites, so every site
+ * is visited once per counter value, as in the plain sweeps. */
+void orc_dcb_sweeps(int L, int tile, int8_t *s, double beta, uint64_t seed, uint32_t instance,
+                    uint32_t replica, uint32_t t0, uint32_t k, uint32_t n_rounds)
+{
+    int64_t thr[3];
+    orc_thresholds(beta, 2, thr);
+    for (uint32_t m = 0; m < n_rounds; ++m)
+        for (int coarse = 0; coarse < 2; ++coarse)
+            for (uint32_t j = 0; j < k; ++j)
+                for (int colour = 0; colour < 2; ++colour)
+                    orc_update_sites(2, L, s, NULL, thr, seed, instance, replica, t0 + k * m + j, colour,
+                                     tile, coarse);
 }
 
 /* n full sweeps (even sub-lattice, then odd), sweep counters t0 .. t0+n-1. */
