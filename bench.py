@@ -9,7 +9,10 @@ fresh Philox seed. The population (2 x 409.6 MB int8 buffers) is larger than
 L2, so no explicit flush is needed between steps.
 
 Other workloads (--workload): ising2d-L4096 (one L = 4096 lattice, 1000 sweeps
-per step, the single-lattice throughput case).
+per step, the single-lattice throughput case; -bitpack: one bit per spin; -dcb:
+double-checkerboard rounds with k = 10 sweeps per 64 x 64 tile load),
+pa-ea3d-L8 (3D +-J spin glass, 32 instances), pa-mixed-2d (four lattice sizes
+in one launch) and pa-learned (time to |dF| <= 1e-4 with the learned schedule).
 
 Prints one JSON line (rank 0). --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -170,6 +173,8 @@ WORKLOADS = {
     # single 2D Ising lattice L=4096 at beta=0.4406868, 1000 sweeps per step (int8, bit-packed)
     "ising2d-L4096": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=0),
     "ising2d-L4096-bitpack": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=1),
+    # the same lattice by double-checkerboard rounds (Fig. 5 right): 64 x 64 tiles, k = 10 sweeps per tile load
+    "ising2d-L4096-dcb": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=0, dcb=(10, 64)),
     # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
     "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
@@ -177,6 +182,9 @@ WORKLOADS = {
                                              (2, 128, FM, 1, 20000), (2, 256, FM, 1, 10000)],
                         S=100, theta=10, beta_f=1.0),
 }
+
+
+SWEEP_LAUNCH = {"auto": 0, "grid": 1, "persistent": 2}
 
 
 def copies(lat):
@@ -188,6 +196,15 @@ def site_updates_per_step(w):
     if w["kind"] == "pa":
         return sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"] * w["S"]
     return w["L"] ** w["dim"] * w["sweeps"]
+
+
+def sweep_lattice(gbmc, ctx, lat, w):
+    """One step of a single-lattice workload: plain or double-checkerboard sweeps."""
+    if "dcb" in w:
+        k, tile = w["dcb"]
+        gbmc.metropolis_sweeps_dcb(ctx, lat, w["beta"], w["sweeps"] // k, k, tile)
+    else:
+        gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
 
 
 def run_gpu(args, w, ws, rank, local):
@@ -202,6 +219,7 @@ def run_gpu(args, w, ws, rank, local):
     gbuild.build()
     stream = torch.cuda.current_stream()
     ctx = gbmc.gbmc_create(local, stream.cuda_stream)
+    gbmc.gbmc_set_sweep_launch(ctx, SWEEP_LAUNCH[args.sweep_launch])
     seed0 = rank_seed(rank)
     result = {}
     if w["kind"] == "pa":
@@ -214,7 +232,8 @@ def run_gpu(args, w, ws, rank, local):
         if len(lats) == 1:
             tuned = gbmc.gbmc_autotune(ctx, lats[0], 0.5 * w["beta_f"], w["theta"])
             result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
-                                "row_walk": tuned.row_walk, "candidates": tuned.n_candidates}
+                                "row_walk": tuned.row_walk, "persistent": tuned.persistent,
+                                "candidates": tuned.n_candidates}
         pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True)
 
         def step(k):
@@ -226,7 +245,7 @@ def run_gpu(args, w, ws, rank, local):
         lats = [lat]
 
         def step(k):
-            gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
+            sweep_lattice(gbmc, ctx, lat, w)
 
     for k in range(args.warmup):
         step(k)
@@ -288,7 +307,7 @@ def run_gpu(args, w, ws, rank, local):
             stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
             d2h_stats = stats.nbytes
         else:
-            gbmc.metropolis_sweeps(ctx, lats[0], w["beta"], w["sweeps"])
+            sweep_lattice(gbmc, ctx, lats[0], w)
             d2h_stats = 0
         for l, hout in zip(lats, hosts_out):
             gbmc.lattice_copy_out(ctx, l, hout)
@@ -434,6 +453,15 @@ def cpu_oracle_sample(w):
         upd = Rs * L ** dim * w["theta"] * steps
         desc = "oracle pa_run: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
                "theta=%d" % (dim, L, Rs, R, steps, w["S"], w["theta"])
+    elif "dcb" in w:
+        k, tile = w["dcb"]
+        s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
+        t0 = time.perf_counter()
+        oracle.dcb_sweeps(w["L"], tile, s, w["beta"], 1, 0, 0, 0, k, 1)
+        dt = time.perf_counter() - t0
+        upd = w["L"] ** 2 * k
+        desc = "oracle dcb_sweeps: L=%d, tile %d, 1 round of k=%d (%d of %d sweeps)" % (w["L"], tile, k, k,
+                                                                                         w["sweeps"])
     else:
         n = 2
         s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
@@ -453,6 +481,12 @@ def main():
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
     ap.add_argument("--workload", default="pa-ising2d-L64", choices=sorted(WORKLOADS) + ["pa-learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-launch", default="auto", choices=sorted(SWEEP_LAUNCH),
+                    help="resident sweep kernel: one CTA per unit (grid), CTAs claiming units (persistent), "
+                         "or the autotuned / batch default (auto)")
+    ap.add_argument("--dcb-k", type=int, default=None, help="ising2d-L4096-dcb: sweeps per tile load (default 10)")
+    ap.add_argument("--dcb-tile", type=int, default=None, help="ising2d-L4096-dcb: tile size 32, 64 or 128 "
+                                                                "(default 64)")
     ap.add_argument("--learned-seeds", type=int, default=3)
     ap.add_argument("--plain-steps", type=int, nargs="*", default=[250, 500, 1000, 2000, 4000])
     args = ap.parse_args()
@@ -462,7 +496,11 @@ def main():
                                                                   "the oracle reference arm covers the other workloads"}))
             return
         return run_learned(args)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if "dcb" in w and (args.dcb_k or args.dcb_tile):
+        k = args.dcb_k or w["dcb"][0]
+        w["dcb"] = (k, args.dcb_tile or w["dcb"][1])
+        w["sweeps"] = max(1, w["sweeps"] // k) * k
     ws, rank, local = dist_env()
     metric = "spin-flips/ns (checkerboard Metropolis site updates per ns, whole annealing runs incl. resampling)" \
         if w["kind"] == "pa" else "spin-flips/ns (checkerboard Metropolis site updates per ns)"
@@ -470,7 +508,8 @@ def main():
     config = {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
               "l2_flush": "inputs larger than L2 (2 x 409.6 MB population)" if w["kind"] == "pa"
               else "none: 16 MiB lattice is L2-resident (single-lattice case)",
-              "parallelism": "replicas only: independent populations per rank" if ws > 1 else "single GPU"}
+              "parallelism": "replicas only: independent populations per rank" if ws > 1 else "single GPU",
+              "sweep_launch": args.sweep_launch}
 
     if args.impl == "reference":
         # the CPU oracle as it stands, on the host cores, bounded sample per step
@@ -503,12 +542,16 @@ def main():
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
     kname = "sweep_resident" if w["kind"] == "pa" else \
-        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else "sweep_tiles")
+        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else ("sweep_dcb" if "dcb" in w else "sweep_tiles"))
     n_l, t_l = prof.get(kname, (0, 0.0))
     avg_ms = t_l / n_l if n_l else float("nan")
     if w["kind"] == "pa":
         upd_per_launch = sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"]
         hbm_bytes_per_launch = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
+    elif "dcb" in w:
+        k, tile = w["dcb"]
+        upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
+        hbm_bytes_per_launch = w["L"] ** 2 // 2 * ((tile + 16) ** 2 + tile ** 2) // tile ** 2  # window in, tile out
     elif w.get("layout", 0) == 1:
         upd_per_launch = w["L"] ** w["dim"] // 2          # one colour per launch
         hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 16  # read both planes, write one (bits)

@@ -80,6 +80,20 @@ gbmc_status gbmc_destroy(gbmc_ctx *ctx);
  * launch with grid-wide barriers; fused = 0 uses one launch per phase. Both
  * give identical results. */
 gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
+
+/* Launch form of the shared-memory sweep kernel (Sec. 3.1 checkerboard sweeps
+ * of copies resident in shared memory; no counterpart in the paper, which
+ * launches one thread block per tile). A work unit is one group of copies of
+ * one (lattice, instance). GRID: one thread block per unit. PERSISTENT: as
+ * many blocks as fit on the device at once, each claiming units from a
+ * counter in the context until none is left, lattices with the largest
+ * copies first. AUTO (default): persistent when the autotuned shape of the
+ * lattice class says so or when several lattices share a launch, else grid.
+ * Every form gives bit-identical results. Persistent launches of one context
+ * share its counter, so a context's work must stay on one stream (no two of
+ * its sweep launches in flight at once). Unknown mode: GBMC_ERR_ARG. */
+enum { GBMC_LAUNCH_AUTO = 0, GBMC_LAUNCH_GRID = 1, GBMC_LAUNCH_PERSISTENT = 2 };
+gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
 /* Test aid for the bounded grid barriers of the fused resampling: each
  * barrier waits for `phantom_arrivals` CTAs more than the launch has (so with
  * 1 the wait can only end by running out of its budget) and gives up after
@@ -164,6 +178,24 @@ gbmc_status lattice_couplings_out(gbmc_ctx *ctx, const gbmc_lattice *lat, int8_t
 gbmc_status metropolis_sweeps(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_sweeps,
                               int32_t *E_series_dev, int32_t *M_series_dev);
 
+/* Double-checkerboard sweeps with k hits per tile (Sec. 3.1, Fig. 5 right,
+ * the multi-hit variant). The lattice is cut into tile x tile tiles, tile
+ * (a, b) holding the sites with x / tile = a, y / tile = b and having coarse
+ * colour (a + b) mod 2. A round updates every tile of coarse colour 0, then
+ * every tile of coarse colour 1 (one launch each); a tile gets k full
+ * checkerboard sweeps (fine colour 0, then 1) from shared memory while every
+ * site outside it stays fixed. The j-th sweep of round m uses sweep counter
+ * t + k m + j (t = the lattice's counter on entry) for the Philox words of the
+ * tile's sites, the words plain sweeps would use, and the counter advances by
+ * k n_rounds; the configurations differ from plain sweeps because the order
+ * of the updates does. Every update is a Metropolis step of one site, so the
+ * chain keeps the Boltzmann distribution. Requirements (else GBMC_ERR_ARG):
+ * 2D ferromagnet, int8 layout, tile in {32, 64, 128}, L a multiple of
+ * 2 tile, k >= 1. E_series_dev / M_series_dev: NULL, or device int32
+ * [n_rounds][n_copies] receiving E and M after every round. */
+gbmc_status metropolis_sweeps_dcb(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_rounds,
+                                  uint32_t k, uint32_t tile, int32_t *E_series_dev, int32_t *M_series_dev);
+
 /* Energy E = -sum_<ij> J_ij s_i s_j (Eq. (7), forward bonds) and magnetisation
  * M = sum_i s_i of every copy, into device int32 arrays [n_copies]. */
 gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, int32_t *M_dev);
@@ -173,8 +205,9 @@ gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, 
  * (powers of two), copies per CTA, row-wise or flat walk over the words of a
  * colour plane -- are timed with CUDA events on a scratch copy of up to 32768
  * replicas of instance 0 (n_sweeps sweeps at beta, the lattice itself is left
- * unchanged), and the fastest is recorded for the lattice class (dim, model,
- * L) for the rest of the process. Every shape gives bit-identical results:
+ * unchanged), then the fastest of them once more as a persistent launch, and
+ * the fastest is recorded for the lattice class (dim, model, L) for the rest
+ * of the process. Every shape gives bit-identical results:
  * the random words depend only on (seed, sweep, replica, site). Synchronises.
  * out->resident = 0 when the lattice uses the global-memory kernel. */
 typedef struct {
@@ -184,7 +217,7 @@ typedef struct {
     int32_t row_walk;
     double ms_per_sweep;      /* best time of one sweep of the timed replicas */
     uint32_t n_candidates;
-    uint32_t pad;
+    int32_t persistent;       /* 1: persistent launch (gbmc_set_sweep_launch) */
 } gbmc_tuning;
 gbmc_status gbmc_autotune(gbmc_ctx *ctx, const gbmc_lattice *lat, double beta, uint32_t n_sweeps,
                           gbmc_tuning *out);

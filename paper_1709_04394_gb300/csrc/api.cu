@@ -49,12 +49,12 @@ std::atomic<uint64_t> g_launches{0};
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
-    PK_BP_HALFSWEEP, PK_COUNT
+    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
-                                          "bitpack_halfsweep"};
+                                          "bitpack_halfsweep", "sweep_dcb"};
 
 // Interior size of the tiles of large 2D lattices (window = kTile + 16).
 constexpr uint32_t kTile = 128;
@@ -70,8 +70,9 @@ struct gbmc_ctx {
     int device;
     cudaStream_t stream;
     int sm_count;
-    unsigned int* words = nullptr;  // device [barrier counter, error flag]
+    unsigned int* words = nullptr;  // device [barrier counter, error flag, unit claims, finished CTAs]
     bool fused = true;              // one cooperative resampling launch per lattice and step
+    int32_t launch_mode = GBMC_LAUNCH_AUTO;  // grid or persistent resident sweeps
     uint32_t phantom = 0;           // test hook: extra barrier arrivals to wait for
     long long budget = 2000000000;  // cycles a barrier wait may last (about 1 s)
     bool prof = false;
@@ -222,7 +223,8 @@ struct Tuning {
     bool resident;
     uint32_t tpr, rpc, threads;
     size_t smem;
-    bool rowwise;  // allow the division-free row walk (needs tpr % (L/8) == 0)
+    bool rowwise;     // allow the division-free row walk (needs tpr % (L/8) == 0)
+    bool persistent;  // resident CTAs claim work units instead of one CTA per unit
 };
 
 // Launch shapes chosen by gbmc_autotune (or set with gbmc_set_tuning), per
@@ -237,6 +239,7 @@ struct ShapeKey {
 struct Shape {
     uint32_t tpr, copies_per_cta;
     bool rowwise;
+    bool persistent;
 };
 std::mutex g_shape_mu;
 std::map<ShapeKey, Shape> g_shapes;
@@ -251,7 +254,7 @@ uint64_t units_per_copy(const gbmc_lattice* l) {
 }
 
 // Shape for (tpr, copies per CTA): clamp to the replica count and shared memory.
-Tuning make_tuning(const gbmc_lattice* l, uint32_t tpr, uint32_t rpc, bool rowwise) {
+Tuning make_tuning(const gbmc_lattice* l, uint32_t tpr, uint32_t rpc, bool rowwise, bool persistent = false) {
     Tuning t{};
     const uint64_t stride = (l->N + 15) & ~15ull;
     const size_t bonds = bond_bytes(l);
@@ -269,6 +272,7 @@ Tuning make_tuning(const gbmc_lattice* l, uint32_t tpr, uint32_t rpc, bool rowwi
     if (t.threads < 32) t.threads = 32, t.tpr = 32 / rpc;
     t.smem = rpc * stride + bonds;
     t.rowwise = rowwise;
+    t.persistent = persistent;
     return t;
 }
 
@@ -278,7 +282,9 @@ Tuning tune(const gbmc_lattice* l, bool use_table = true) {
     if (use_table) {
         std::lock_guard<std::mutex> g(g_shape_mu);
         auto it = g_shapes.find(ShapeKey{l->d.dim, l->d.model, l->d.L});
-        if (it != g_shapes.end()) return make_tuning(l, it->second.tpr, it->second.copies_per_cta, it->second.rowwise);
+        if (it != g_shapes.end())
+            return make_tuning(l, it->second.tpr, it->second.copies_per_cta, it->second.rowwise,
+                               it->second.persistent);
     }
     const uint64_t units = units_per_copy(l);
     uint32_t tpr = 8;
@@ -321,7 +327,29 @@ SweepJob base_job(const gbmc_lattice* l, const Tuning& tu) {
     return J;
 }
 
-gbmc_status launch_jobs(gbmc_ctx* ctx, SweepLaunch& P, const std::vector<Tuning>& tu) {
+// Enqueues one resident sweep launch of P's jobs. force_persistent: -1 takes
+// the context's launch mode (AUTO: the tuned shapes' choice, persistent for
+// batches of several lattices), 0 / 1 force a grid / persistent launch.
+gbmc_status launch_jobs(gbmc_ctx* ctx, const SweepLaunch& P0, const std::vector<Tuning>& tu,
+                        int force_persistent = -1) {
+    bool persistent = P0.njobs > 1;
+    for (int j = 0; j < P0.njobs; ++j) persistent = persistent || tu[j].persistent;
+    if (ctx->launch_mode == GBMC_LAUNCH_GRID) persistent = false;
+    if (ctx->launch_mode == GBMC_LAUNCH_PERSISTENT) persistent = true;
+    if (force_persistent >= 0) persistent = force_persistent != 0;
+    SweepLaunch P = P0;
+    if (persistent && P.njobs > 1) {
+        // units are claimed in job order: largest copies first shortens the tail
+        int order[kMaxJobs];
+        for (int j = 0; j < P.njobs; ++j) order[j] = j;
+        for (int a = 1; a < P.njobs; ++a)
+            for (int b = a; b > 0 && P0.jobs[order[b]].N > P0.jobs[order[b - 1]].N; --b) {
+                const int t = order[b];
+                order[b] = order[b - 1];
+                order[b - 1] = t;
+            }
+        for (int j = 0; j < P.njobs; ++j) P.jobs[j] = P0.jobs[order[j]];
+    }
     uint32_t total = 0, threads = 0;
     for (int j = 0; j < P.njobs; ++j) {
         P.cta_begin[j] = total;
@@ -329,13 +357,15 @@ gbmc_status launch_jobs(gbmc_ctx* ctx, SweepLaunch& P, const std::vector<Tuning>
         if (tu[j].threads > threads) threads = tu[j].threads;
     }
     P.cta_begin[P.njobs] = total;
+    P.total = total;
+    P.work = persistent ? ctx->words + 2 : nullptr;
     P.rowwise = 1;
-    for (int j = 0; j < P.njobs; ++j) {
-        const uint32_t W = P.jobs[j].L / 8, tpr = threads / P.jobs[j].rpc;
+    for (int j = 0; j < P0.njobs; ++j) {
+        const uint32_t W = P0.jobs[j].L / 8, tpr = threads / P0.jobs[j].rpc;
         if (W == 0 || tpr % W != 0 || !tu[j].rowwise) P.rowwise = 0;
     }
     // every job must use the same thread count: copies per CTA scale with it
-    for (int j = 0; j < P.njobs; ++j)
+    for (int j = 0; j < P0.njobs; ++j)
         if (tu[j].threads != threads)
             return fail(GBMC_ERR_ARG, "lattices of one launch need equal CTA shapes");
     const size_t smem = resident_smem_bytes(P);
@@ -415,6 +445,14 @@ gbmc_status gbmc_sync(gbmc_ctx* ctx) {
     CUDA_TRY(cudaSetDevice(ctx->device));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return check_device_error(ctx);
+}
+
+gbmc_status gbmc_set_sweep_launch(gbmc_ctx* ctx, int32_t mode) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    if (mode != GBMC_LAUNCH_AUTO && mode != GBMC_LAUNCH_GRID && mode != GBMC_LAUNCH_PERSISTENT)
+        return fail(GBMC_ERR_ARG, "unknown sweep launch mode %d", mode);
+    ctx->launch_mode = mode;
+    return GBMC_OK;
 }
 
 gbmc_status gbmc_set_resample_mode(gbmc_ctx* ctx, int32_t fused) {
@@ -755,6 +793,50 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
         }
     }
     l->t += n_sweeps;
+    return GBMC_OK;
+}
+
+gbmc_status metropolis_sweeps_dcb(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t n_rounds, uint32_t k,
+                                  uint32_t tile, int32_t* E_series, int32_t* M_series) {
+    if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!beta_ok(beta, l->d.dim)) return fail(GBMC_ERR_ARG, "beta must satisfy 0 <= 4*dim*beta <= 700 (got %g)", beta);
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice is owned by an annealing run");
+    if (l->d.dim != 2 || l->d.model != GBMC_ISING_FM || l->d.layout != GBMC_INT8)
+        return fail(GBMC_ERR_ARG, "double-checkerboard sweeps need a 2D ferromagnet in the int8 layout");
+    if (tile != 32 && tile != 64 && tile != 128) return fail(GBMC_ERR_ARG, "tile must be 32, 64 or 128 (got %u)", tile);
+    if (l->d.L % (2 * tile) != 0) return fail(GBMC_ERR_ARG, "L = %d is not a multiple of 2 * tile", (int)l->d.L);
+    if (k == 0) return fail(GBMC_ERR_ARG, "k must be >= 1");
+    if (n_rounds == 0) return GBMC_OK;
+    if ((uint64_t)l->t + (uint64_t)n_rounds * k > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "sweep counter would wrap");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    uint32_t thr[3];
+    thresholds(beta, thr);
+    TileLaunch TL;
+    std::memset(&TL, 0, sizeof(TL));
+    TL.src = TL.dst = l->cur;
+    TL.seed = l->d.seed;
+    TL.L = (uint32_t)l->d.L;
+    TL.T = tile;
+    TL.R = l->d.n_replicas;
+    TL.inst_base = l->d.instance_base;
+    TL.thr[0] = thr[0];
+    TL.thr[1] = thr[1];
+    TL.nsweeps = k;
+    for (uint32_t m = 0; m < n_rounds; ++m) {
+        TL.t0 = l->t + m * k;
+        for (uint32_t coarse = 0; coarse < 2; ++coarse) {
+            TL.coarse = coarse;
+            ProfScope ps_(ctx, PK_SWEEP_DCB);
+            CUDA_TRY(launch_sweep_dcb(TL, l->ncopies, ctx->stream));
+        }
+        if (E_series || M_series) {
+            ProfScope ps_(ctx, PK_OBS);
+            CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances,
+                                        l->d.n_replicas, E_series ? E_series + (uint64_t)m * l->ncopies : nullptr,
+                                        M_series ? M_series + (uint64_t)m * l->ncopies : nullptr, ctx->stream));
+        }
+    }
+    l->t += n_rounds * k;
     return GBMC_OK;
 }
 
@@ -1486,7 +1568,22 @@ gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tu
     const uint32_t tpr = shape->threads_per_copy, rpc = shape->copies_per_cta;
     if (tpr == 0 || (tpr & (tpr - 1)) || tpr > 256 || rpc == 0 || rpc > 64 || tpr * rpc > 256)
         return fail(GBMC_ERR_ARG, "threads_per_copy must be a power of two <= 256, copies_per_cta in 1..64, product <= 256");
-    g_shapes[k] = Shape{tpr, rpc, shape->row_walk != 0};
+    g_shapes[k] = Shape{tpr, rpc, shape->row_walk != 0, shape->persistent != 0};
+    return GBMC_OK;
+}
+
+// One untimed launch, then two launches timed with CUDA events (synchronises).
+static gbmc_status time_launches(gbmc_ctx* ctx, const SweepLaunch& P, const std::vector<Tuning>& tv,
+                                 int persistent, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    gbmc_status st;
+    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
+    cudaEventRecord(e0, ctx->stream);
+    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
+    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    if (ce != cudaSuccess) return fail(GBMC_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
     return GBMC_OK;
 }
 
@@ -1509,7 +1606,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     const uint32_t W = (uint32_t)l->d.L / 8;
     const uint64_t units = units_per_copy(l);
     double best = 1e30;
-    Shape best_shape{def.tpr, def.rpc, true};
+    Shape best_shape{def.tpr, def.rpc, true, false};
     uint32_t n_cand = 0;
     gbmc_status st = GBMC_OK;
     for (uint32_t tpr = 8; tpr <= 256 && st == GBMC_OK; tpr <<= 1) {
@@ -1536,24 +1633,42 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
                 P.ea = l->d.model == GBMC_EA_PMJ;
                 P.swar = (l->d.L % 8) == 0;
                 std::vector<Tuning> tv{tu};
-                // warm-up launch, then two timed launches
-                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
-                cudaEventRecord(e0, ctx->stream);
-                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
-                if ((st = launch_jobs(ctx, P, tv)) != GBMC_OK) break;
-                cudaEventRecord(e1, ctx->stream);
-                cudaError_t ce = cudaEventSynchronize(e1);
                 float ms = 0.f;
-                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-                if (ce != cudaSuccess) {
-                    st = fail(GBMC_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
-                    break;
-                }
+                if ((st = time_launches(ctx, P, tv, 0, e0, e1, &ms)) != GBMC_OK) break;
                 ++n_cand;
                 if (ms < best) {
                     best = ms;
-                    best_shape = Shape{tu.tpr, tu.rpc, rw != 0};
+                    best_shape = Shape{tu.tpr, tu.rpc, rw != 0, false};
                 }
+            }
+        }
+    }
+    if (st == GBMC_OK) {
+        // the best grid shape again as a persistent launch
+        Tuning tu = make_tuning(l, best_shape.tpr, best_shape.copies_per_cta, best_shape.rowwise, true);
+        SweepLaunch P;
+        std::memset(&P, 0, sizeof(P));
+        SweepJob J = base_job(l, tu);
+        J.src = J.dst = scratch;
+        J.R = R;
+        J.n_inst = 1;
+        J.ctas_per_inst = (R + tu.rpc - 1) / tu.rpc;
+        J.nsweeps = n_sweeps;
+        J.t0 = 0;
+        thresholds(beta, J.thr);
+        P.jobs[0] = J;
+        P.njobs = 1;
+        P.dim = l->d.dim;
+        P.ea = l->d.model == GBMC_EA_PMJ;
+        P.swar = (l->d.L % 8) == 0;
+        std::vector<Tuning> tv{tu};
+        float ms = 0.f;
+        st = time_launches(ctx, P, tv, 1, e0, e1, &ms);
+        if (st == GBMC_OK) {
+            ++n_cand;
+            if (ms < best) {
+                best = ms;
+                best_shape.persistent = true;
             }
         }
     }
@@ -1569,6 +1684,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     out->threads_per_copy = best_shape.tpr;
     out->copies_per_cta = best_shape.copies_per_cta;
     out->row_walk = best_shape.rowwise ? 1 : 0;
+    out->persistent = best_shape.persistent ? 1 : 0;
     out->ms_per_sweep = best / (2.0 * n_sweeps);
     out->n_candidates = n_cand;
     return GBMC_OK;

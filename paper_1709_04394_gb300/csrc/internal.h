@@ -51,6 +51,9 @@ struct SweepLaunch {
     int32_t ea;
     int32_t swar;                      // 1: every job has L % 8 == 0 (split colour planes)
     int32_t rowwise;                   // 1: every job's threads per copy are a multiple of L/8
+    uint32_t total;                    // work units (= cta_begin[njobs])
+    unsigned int* work;                // persistent launch: [claim counter, finished CTAs], both 0
+                                       // at launch; null: one CTA per unit
 };
 
 // ---- launchers (return cudaError_t of the launch) ----
@@ -88,11 +91,15 @@ struct TileLaunch {
     int8_t* dst;
     uint64_t seed;
     uint32_t L, T, R, inst_base, copy0;
-    uint32_t t0, nsweeps;     // nsweeps <= 4
+    uint32_t t0, nsweeps;     // nsweeps <= 4 (halo tiles); k hits per tile (double checkerboard)
     uint32_t thr[2];          // T(4), T(8)
+    uint32_t coarse;          // double checkerboard: coarse colour of the tiles of this launch
 };
 size_t tile_smem_bytes(uint32_t T);
 cudaError_t launch_sweep_tiles(const TileLaunch& P, uint64_t copies, cudaStream_t s);
+// Double checkerboard (Fig. 5 right): the tiles of coarse colour P.coarse, each
+// swept P.nsweeps times in place (src == dst); T in {32, 64, 128}, L % 2T == 0.
+cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t s);
 // Global-memory half-sweep over one job (large lattices); colour 0 or 1.
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);

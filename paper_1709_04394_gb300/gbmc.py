@@ -24,6 +24,7 @@ GBMC_ISING_FM, GBMC_EA_PMJ = 0, 1
 GBMC_INT8, GBMC_BITPACK = 0, 1
 GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
 GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
+GBMC_LAUNCH_AUTO, GBMC_LAUNCH_GRID, GBMC_LAUNCH_PERSISTENT = 0, 1, 2
 
 
 class GbmcError(RuntimeError):
@@ -39,7 +40,7 @@ class KernelTime(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("resident", C.c_int32), ("threads_per_copy", C.c_uint32), ("copies_per_cta", C.c_uint32),
                 ("row_walk", C.c_int32), ("ms_per_sweep", C.c_double), ("n_candidates", C.c_uint32),
-                ("pad", C.c_uint32)]
+                ("persistent", C.c_int32)]
 
 
 class ScheduleRecord(C.Structure):
@@ -102,6 +103,7 @@ def load():
             "gbmc_destroy": ([p], st),
             "gbmc_profile": ([p, C.c_int32], st),
             "gbmc_set_resample_mode": ([p, C.c_int32], st),
+            "gbmc_set_sweep_launch": ([p, C.c_int32], st),
             "gbmc_test_barrier_wait": ([p, C.c_uint32, C.c_uint64], st),
             "gbmc_profile_read": ([p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
             "gbmc_kernel_launches": ([], C.c_uint64),
@@ -113,6 +115,7 @@ def load():
             "lattice_copy_in": ([p, p, p, C.c_size_t], st),
             "lattice_couplings_out": ([p, p, p, C.c_size_t], st),
             "metropolis_sweeps": ([p, p, C.c_double, C.c_uint32, p, p], st),
+            "metropolis_sweeps_dcb": ([p, p, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32, p, p], st),
             "observables": ([p, p, p, p], st),
             "gbmc_autotune": ([p, p, C.c_double, C.c_uint32, C.POINTER(Tuning)], st),
             "gbmc_set_tuning": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tuning)], st),
@@ -199,6 +202,10 @@ def gbmc_set_resample_mode(ctx, fused=True):
     _check(load().gbmc_set_resample_mode(ctx, int(bool(fused))))
 
 
+def gbmc_set_sweep_launch(ctx, mode=GBMC_LAUNCH_AUTO):
+    _check(load().gbmc_set_sweep_launch(ctx, int(mode)))
+
+
 def gbmc_test_barrier_wait(ctx, phantom_arrivals=0, budget_cycles=2000000000):
     _check(load().gbmc_test_barrier_wait(ctx, phantom_arrivals, budget_cycles))
 
@@ -259,6 +266,12 @@ def metropolis_sweeps(ctx, lat, beta: float, n_sweeps: int, E_series=None, M_ser
     _check(load().metropolis_sweeps(ctx, lat, float(beta), n_sweeps, _ptr(E_series), _ptr(M_series)))
 
 
+def metropolis_sweeps_dcb(ctx, lat, beta: float, n_rounds: int, k: int, tile: int = 64, E_series=None,
+                          M_series=None):
+    _check(load().metropolis_sweeps_dcb(ctx, lat, float(beta), n_rounds, k, tile, _ptr(E_series),
+                                        _ptr(M_series)))
+
+
 def observables(ctx, lat, E=None, M=None):
     _check(load().observables(ctx, lat, _ptr(E), _ptr(M)))
 
@@ -269,12 +282,12 @@ def gbmc_autotune(ctx, lat, beta, n_sweeps=10) -> Tuning:
     return t
 
 
-def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_walk=True):
+def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_walk=True, persistent=False):
     """Force a launch shape for a lattice class; threads_per_copy=None clears it."""
     if threads_per_copy is None:
         _check(load().gbmc_set_tuning(dim, model, L, None))
         return
-    t = Tuning(1, threads_per_copy, copies_per_cta, int(bool(row_walk)), 0.0, 0, 0)
+    t = Tuning(1, threads_per_copy, copies_per_cta, int(bool(row_walk)), 0.0, 0, int(bool(persistent)))
     _check(load().gbmc_set_tuning(dim, model, L, C.byref(t)))
 
 

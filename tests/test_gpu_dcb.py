@@ -1,0 +1,82 @@
+"""GPU parity of the double-checkerboard sweeps with k hits per tile
+(Sec. 3.1, Fig. 5 right): spins, per-round E and M and the sweep counter
+against the oracle's tile-by-tile order, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_04394_gb300 import gbmc
+from tests.gpu_common import ctx, device_i32, spins_out, torch  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+BETA_C = 0.4406868
+
+
+@pytest.mark.parametrize("L,tile,k,rounds,R,beta", [
+    (64, 32, 3, 2, 3, BETA_C),
+    (256, 64, 1, 3, 2, 0.3),
+    (256, 128, 4, 1, 1, 0.6),
+    (512, 64, 10, 1, 1, BETA_C),
+    (128, 32, 2, 2, 5, 0.0),        # beta = 0: every visit flips
+    (4096, 64, 10, 1, 1, BETA_C),   # the benchmark lattice, whole
+])
+def test_dcb_matches_oracle(ctx, L, tile, k, rounds, R, beta):
+    seed = 11 + L
+    lat = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=seed, instance_base=2)
+    gbmc.lattice_set_sweep_counter(lat, 5)
+    Es, Ms = device_i32(rounds * R), device_i32(rounds * R)
+    gbmc.metropolis_sweeps_dcb(ctx, lat, beta, rounds, k, tile, Es, Ms)
+    got = spins_out(ctx, lat)
+    Es = Es.cpu().numpy().reshape(rounds, R)
+    Ms = Ms.cpu().numpy().reshape(rounds, R)
+    for r in range(R):
+        s = oracle.init_spins(2, L, seed, 2, r, True)
+        for m in range(rounds):
+            oracle.dcb_sweeps(L, tile, s, beta, seed, 2, r, 5 + m * k, k, 1)
+            assert (Es[m, r], Ms[m, r]) == oracle.observables(2, L, s), (r, m)
+        np.testing.assert_array_equal(got[r], s, err_msg="replica %d" % r)
+    assert gbmc.lattice_info(lat).sweep_counter == 5 + rounds * k
+    gbmc.lattice_free(lat)
+
+
+def test_dcb_continues_counters_and_mixes_with_plain_sweeps(ctx):
+    L, tile, seed = 128, 32, 4
+    a = gbmc.lattice_init(ctx, 2, L, n_replicas=2, seed=seed)
+    b = gbmc.lattice_init(ctx, 2, L, n_replicas=2, seed=seed)
+    gbmc.metropolis_sweeps(ctx, a, 0.5, 3)
+    gbmc.metropolis_sweeps_dcb(ctx, a, 0.5, 1, 2, tile)
+    gbmc.metropolis_sweeps_dcb(ctx, a, 0.5, 1, 2, tile)
+    gbmc.metropolis_sweeps(ctx, b, 0.5, 3)
+    gbmc.metropolis_sweeps_dcb(ctx, b, 0.5, 2, 2, tile)
+    ga, gb = spins_out(ctx, a), spins_out(ctx, b)
+    np.testing.assert_array_equal(ga, gb)
+    for r in range(2):
+        s = oracle.init_spins(2, L, seed, 0, r, True)
+        oracle.sweeps(2, L, s, None, 0.5, seed, 0, r, 0, 3)
+        oracle.dcb_sweeps(L, tile, s, 0.5, seed, 0, r, 3, 2, 2)
+        np.testing.assert_array_equal(ga[r], s)
+        plain = oracle.init_spins(2, L, seed, 0, r, True)
+        oracle.sweeps(2, L, plain, None, 0.5, seed, 0, r, 0, 7)
+        assert not np.array_equal(plain, s)  # same random words, another order
+    assert gbmc.lattice_info(a).sweep_counter == 7
+    gbmc.lattice_free(a)
+    gbmc.lattice_free(b)
+
+
+def test_dcb_rejects_unsupported_lattices(ctx):
+    lat = gbmc.lattice_init(ctx, 2, 96, seed=1)
+    for tile in (48, 64):  # 48: no kernel; 64: 96 is not a multiple of 128
+        with pytest.raises(gbmc.GbmcError) as e:
+            gbmc.metropolis_sweeps_dcb(ctx, lat, 0.4, 1, 1, tile)
+        assert e.value.status == gbmc.GBMC_ERR_ARG
+    gbmc.lattice_free(lat)
+    lat = gbmc.lattice_init(ctx, 2, 128, seed=1)
+    with pytest.raises(gbmc.GbmcError):
+        gbmc.metropolis_sweeps_dcb(ctx, lat, 0.4, 1, 0, 32)  # k = 0
+    gbmc.lattice_free(lat)
+    for kw in (dict(dim=3, L=64), dict(dim=2, L=64, layout=gbmc.GBMC_BITPACK)):
+        lat = gbmc.lattice_init(ctx, kw.pop("dim"), kw.pop("L"), seed=1, **kw)
+        with pytest.raises(gbmc.GbmcError):
+            gbmc.metropolis_sweeps_dcb(ctx, lat, 0.4, 1, 1, 32)
+        gbmc.lattice_free(lat)

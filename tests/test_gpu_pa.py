@@ -75,12 +75,18 @@ def test_pa_3d_ea_instances_match_oracle(ctx, L):
     gbmc.lattice_free(lat)
 
 
-def test_pa_mixed_batch_in_one_launch_matches_oracle(ctx):
-    # lattices of uneven L advance together: one sweep launch covers both
+@pytest.mark.parametrize("mode", [gbmc.GBMC_LAUNCH_AUTO, gbmc.GBMC_LAUNCH_GRID, gbmc.GBMC_LAUNCH_PERSISTENT])
+def test_pa_mixed_batch_in_one_launch_matches_oracle(ctx, mode):
+    # lattices of uneven L advance together: one sweep launch covers both, as
+    # one CTA per unit or as persistent CTAs claiming units largest-first
     S, theta = 4, 2
     a = gbmc.lattice_init(ctx, 2, 16, n_replicas=600, seed=3, instance_base=0)
     b = gbmc.lattice_init(ctx, 2, 32, n_replicas=300, seed=3, instance_base=1)
-    pa, stats = _run_gpu(ctx, [a, b], theta, S)
+    gbmc.gbmc_set_sweep_launch(ctx, mode)
+    try:
+        pa, stats = _run_gpu(ctx, [a, b], theta, S)
+    finally:
+        gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_AUTO)
     assert gbmc.pa_populations(pa) == 2
     for pop, (lat, L, R) in enumerate(((a, 16, 600), (b, 32, 300))):
         ref = oracle.pa_run(2, L, 3, pop, R, oracle.linear_betas(1.0, S), theta)

@@ -27,13 +27,44 @@ def test_every_shape_matches_oracle(ctx, dim, L, model, R):
     ref = np.stack(ref)
     try:
         for tpr, rpc, rw in SHAPES:
-            gbmc.gbmc_set_tuning(dim, model, L, tpr, rpc, rw)
-            lat = gbmc.lattice_init(ctx, dim, L, model=model, n_replicas=R, seed=seed)
-            gbmc.metropolis_sweeps(ctx, lat, beta, n)
-            np.testing.assert_array_equal(spins_out(ctx, lat), ref, err_msg=str((tpr, rpc, rw)))
-            gbmc.lattice_free(lat)
+            for pers in (False, True):
+                gbmc.gbmc_set_tuning(dim, model, L, tpr, rpc, rw, persistent=pers)
+                lat = gbmc.lattice_init(ctx, dim, L, model=model, n_replicas=R, seed=seed)
+                gbmc.metropolis_sweeps(ctx, lat, beta, n)
+                np.testing.assert_array_equal(spins_out(ctx, lat), ref, err_msg=str((tpr, rpc, rw, pers)))
+                gbmc.lattice_free(lat)
     finally:
         gbmc.gbmc_set_tuning(dim, model, L, None)
+
+
+def test_persistent_launch_with_many_more_units_than_ctas(ctx):
+    # 25000 copies of L = 16 in groups of 8: 3125 units for at most
+    # 152 x 8 resident CTAs, so CTAs claim several units each; the claim
+    # counter must be back at 0 for each of the consecutive launches
+    L, R, beta, seed = 16, 25000, 0.44, 21
+    lat = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=seed)
+    gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_PERSISTENT)
+    try:
+        for _ in range(3):
+            gbmc.metropolis_sweeps(ctx, lat, beta, 2)
+    finally:
+        gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_AUTO)
+    got = spins_out(ctx, lat)
+    E, M = torch.empty(R, dtype=torch.int32, device="cuda"), torch.empty(R, dtype=torch.int32, device="cuda")
+    gbmc.observables(ctx, lat, E, M)
+    E = E.cpu().numpy()
+    for r in list(range(0, R, 997)) + [R - 1]:
+        s = oracle.init_spins(2, L, seed, 0, r, True)
+        oracle.sweeps(2, L, s, None, beta, seed, 0, r, 0, 6)
+        np.testing.assert_array_equal(got[r], s, err_msg="replica %d" % r)
+        assert E[r] == oracle.observables(2, L, s)[0]
+    gbmc.lattice_free(lat)
+
+
+def test_sweep_launch_mode_is_checked(ctx):
+    with pytest.raises(gbmc.GbmcError) as e:
+        gbmc.gbmc_set_sweep_launch(ctx, 7)
+    assert e.value.status == gbmc.GBMC_ERR_ARG
 
 
 def test_autotune_leaves_lattice_and_results_unchanged(ctx):
@@ -43,7 +74,7 @@ def test_autotune_leaves_lattice_and_results_unchanged(ctx):
     t = gbmc.gbmc_autotune(ctx, lat, 0.44, 3)
     try:
         assert t.resident == 1 and t.n_candidates >= 2 and t.ms_per_sweep > 0
-        assert t.threads_per_copy in (8, 16, 32, 64, 128, 256)
+        assert t.threads_per_copy in (8, 16, 32, 64, 128, 256) and t.persistent in (0, 1)
         np.testing.assert_array_equal(spins_out(ctx, lat), before)
         assert gbmc.lattice_info(lat).sweep_counter == 0
         pa = gbmc.pa_create(ctx, [lat], 2, 3)
