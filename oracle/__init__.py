@@ -61,6 +61,11 @@ def _load():
         lib.orc_observables.argtypes = [i32, i32, p, p, p, p]
         lib.orc_resample.argtypes = [u32, p, dbl, u64, u32, u32, p]
         lib.orc_resample.restype = dbl
+        lib.orc_resample_nearest.argtypes = [u32, p, dbl, u32, u32, u64, u32, u32, p, p]
+        lib.orc_resample_nearest.restype = dbl
+        lib.orc_pa_run_nearest.argtypes = [i32, i32, p, u64, u32, u32, u32, u32, p, u32, p, i32,
+                                           p, p, p, p, p, p]
+        lib.orc_pa_run_nearest.restype = i32
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pt_run.argtypes = [i32, i32, p, u64, u32, u32, p, u32, u32, u32, u32, p, p, p, p]
         lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
@@ -160,6 +165,18 @@ def resample(E, dbeta, seed, instance, step):
     return counts, lnQ
 
 
+def resample_nearest(E, dbeta, R0, cap, seed, instance, step):
+    """Nearest-integer resampling counts (variable population), the new
+    population size and ln Q of one annealing step (reading R17)."""
+    lib = _load()
+    E = np.ascontiguousarray(E, dtype=np.int64)
+    counts = np.empty(E.size, dtype=np.uint32)
+    Rn = np.zeros(1, dtype=np.uint64)
+    lnQ = lib.orc_resample_nearest(E.size, _ptr(E), float(dbeta), R0, cap, seed, instance, step, _ptr(counts),
+                                   _ptr(Rn))
+    return counts, int(Rn[0]), lnQ
+
+
 def children_order(counts):
     lib = _load()
     counts = np.ascontiguousarray(counts, dtype=np.uint32)
@@ -202,6 +219,30 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_ene
     out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents, E_steps=E_steps,
                spins=spins.reshape(R, N), betas=betas)
     return out
+
+
+def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None):
+    """Population annealing with nearest-integer resampling and a variable
+    population (at most cap replicas). Returns a dict of per-step arrays
+    (lnQ, lnZ, sumE, nrep), the final population (its first nrep[-1] rows)
+    and ok = False if a step would have needed more than cap replicas."""
+    lib = _load()
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    S = betas.size - 1
+    N = n_sites(dim, L)
+    spins = np.zeros(cap * N, dtype=np.int8)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    lnQ = np.zeros(S + 1)
+    lnZ = np.zeros(S + 1)
+    sumE = np.zeros(S + 1, dtype=np.int64)
+    nrep = np.zeros(S + 1, dtype=np.uint32)
+    E = np.zeros(cap, dtype=np.int64)
+    parents = np.zeros(cap, dtype=np.uint32)
+    rc = lib.orc_pa_run_nearest(dim, L, _ptr(Jc), seed, instance, R0, cap, S, _ptr(betas), theta, _ptr(spins), 1,
+                                _ptr(lnQ), _ptr(lnZ), _ptr(sumE), _ptr(nrep), _ptr(E), _ptr(parents))
+    n = int(nrep[S]) if rc == 0 else 0
+    return dict(lnQ=lnQ, lnZ=lnZ, sumE=sumE, nrep=nrep, ok=rc == 0, spins=spins.reshape(cap, N)[:n],
+                E=E[:n], parents=parents[:n], betas=betas)
 
 
 def pt_run(dim, L, seed, instance, betas, theta, n_steps, J=None, spins=None, rep_of=None, accepted=None,

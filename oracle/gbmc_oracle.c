@@ -43,6 +43,8 @@
  *   R9 J_{i,mu} = +1 if the top bit of its COUPLING word is 0, else -1.
  *  R10 ln Z(beta_0 = 0) = N ln 2; ln Z_i = ln Z_{i-1} + ln Q_i.
  *  R16 double checkerboard: see orc_dcb_sweeps.
+ *  R17 nearest-integer resampling, variable population: see
+ *      orc_resample_nearest.
  */
 #include <math.h>
 #include <stdint.h>
@@ -307,8 +309,8 @@ static int orc_ceil_log2(uint64_t R)
     return b;
 }
 
-double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
-                    uint32_t instance, uint32_t step, uint32_t *counts)
+/* ln Q_i of Eq. (13) for the R replicas' energies E (reading R7), and E_min. */
+static double orc_lnQ(uint32_t R, const int64_t *E, double dbeta, int64_t *Emin_out)
 {
     /* minimum energy of the population */
     int64_t Emin = E[0];
@@ -329,7 +331,26 @@ double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
         a = b;
     }
     free(sorted);
-    double lnQ = -dbeta * (double)Emin + log(sum) - log((double)R);
+    *Emin_out = Emin;
+    return -dbeta * (double)Emin + log(sum) - log((double)R);
+}
+
+/* The 64-bit uniform of resampling draw k (reading R1: purpose RESAMPLE). */
+static uint64_t orc_resample_u64(uint64_t seed, uint32_t instance, uint32_t step, uint32_t k)
+{
+    uint32_t ctr[4] = {k >> 1, step, 0u, orc_c3(ORC_PURPOSE_RESAMPLE, 0u, instance)};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    unsigned l = k & 1u;
+    return ((uint64_t)out[2 * l + 1] << 32) | (uint64_t)out[2 * l];
+}
+
+double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
+                    uint32_t instance, uint32_t step, uint32_t *counts)
+{
+    int64_t Emin;
+    double lnQ = orc_lnQ(R, E, dbeta, &Emin);
 
     /* integer weights and their cumulative sums in replica order */
     int s = 63 - orc_ceil_log2(R);
@@ -346,12 +367,7 @@ double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
 
     /* R multinomial draws */
     for (uint32_t k = 0; k < R; ++k) {
-        uint32_t ctr[4] = {k >> 1, step, 0u, orc_c3(ORC_PURPOSE_RESAMPLE, 0u, instance)};
-        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-        uint32_t out[4];
-        orc_philox4x32_10(ctr, key, out);
-        unsigned l = k & 1u;
-        uint64_t U = ((uint64_t)out[2 * l + 1] << 32) | (uint64_t)out[2 * l];
+        uint64_t U = orc_resample_u64(seed, instance, step, k);
         uint64_t x = (uint64_t)(((unsigned __int128)U * (unsigned __int128)total) >> 64);
         /* least j with C_j > x, by bisection over the increasing C */
         uint32_t lo = 0, hi = R - 1;
@@ -363,6 +379,42 @@ double orc_resample(uint32_t R, const int64_t *E, double dbeta, uint64_t seed,
         counts[lo] += 1;
     }
     free(C);
+    return lnQ;
+}
+
+/* Sec. 5.4 step 2 with nearest-integer resampling and a variable population
+ * (reading R17). Replica j (of R_prev) gets tau_j = R0 W_j / C copies in
+ * expectation, the weight e^{-dbeta E_j} / Q_i of the paper rescaled by
+ * R0 / R_prev so that the expected population is R0 at every step, with
+ * integer weights W_j = floor(2^s exp(-dbeta (E_j - Emin))), s = 63 -
+ * ceil(log2 cap), and C = sum_j W_j: n_j = floor(tau_j) plus one more copy
+ * with probability frac(tau_j), i.e. iff floor(U64_j C / 2^64) < (R0 W_j mod C)
+ * (U64_j: resampling word j). Writes counts[R_prev], *R_new = sum_j n_j;
+ * returns ln Q_i of Eq. (13) with R_{i-1} = R_prev. */
+double orc_resample_nearest(uint32_t R_prev, const int64_t *E, double dbeta, uint32_t R0, uint32_t cap,
+                            uint64_t seed, uint32_t instance, uint32_t step, uint32_t *counts,
+                            uint64_t *R_new)
+{
+    int64_t Emin;
+    double lnQ = orc_lnQ(R_prev, E, dbeta, &Emin);
+    int s = 63 - orc_ceil_log2(cap);
+    uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * R_prev);
+    uint64_t C = 0;
+    for (uint32_t j = 0; j < R_prev; ++j) {
+        W[j] = (uint64_t)floor(ldexp(exp(-(dbeta * (double)(E[j] - Emin))), s));
+        C += W[j];
+    }
+    uint64_t total = 0;
+    for (uint32_t j = 0; j < R_prev; ++j) {
+        uint64_t num = (uint64_t)R0 * W[j];
+        uint64_t n0 = num / C, rem = num % C;
+        uint64_t U = orc_resample_u64(seed, instance, step, j);
+        uint64_t x = (uint64_t)(((unsigned __int128)U * (unsigned __int128)C) >> 64);
+        counts[j] = (uint32_t)(n0 + (x < rem ? 1u : 0u));
+        total += counts[j];
+    }
+    free(W);
+    *R_new = total;
     return lnQ;
 }
 
@@ -448,6 +500,72 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
     free(counts);
     free(parent);
     free(next);
+}
+
+/* Population annealing (Sec. 5.4) with nearest-integer resampling and a
+ * variable population size (reading R17): R_0 = R0 replicas at beta_0, at most
+ * cap at any step. spins[cap*N]; the first R_i slots hold the population after
+ * step i. Per step: lnQ, lnZ, sum E over the population and its size R_i;
+ * E_final[cap] / parents_last[cap] for the last step's first R_S slots.
+ * Returns 0, or -1 (outputs up to that step valid) if a step would need more
+ * than cap replicas. */
+int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R0,
+                       uint32_t cap, uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
+                       double *lnQ_out, double *lnZ_out, int64_t *sumE_out, uint32_t *nrep_out,
+                       int64_t *E_final, uint32_t *parents_last)
+{
+    int64_t N = orc_nsites(dim, L);
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * cap);
+    int64_t *M = (int64_t *)malloc(sizeof(int64_t) * cap);
+    uint32_t *counts = (uint32_t *)malloc(sizeof(uint32_t) * cap);
+    uint32_t *parent = (uint32_t *)malloc(sizeof(uint32_t) * cap);
+    int8_t *next = (int8_t *)malloc((size_t)cap * (size_t)N);
+    int rc = 0;
+
+    if (init)
+        for (uint32_t r = 0; r < R0; ++r)
+            orc_init_spins(dim, L, seed, instance, r, 1, spins + (size_t)r * N);
+
+    uint32_t R = R0;
+    double lnZ = (double)N * log(2.0);
+    for (uint32_t i = 0; i <= S; ++i) {
+        double lnQ = 0.0;
+        if (i > 0) {
+            double dbeta = betas[i] - betas[i - 1];
+            uint64_t Rn;
+            lnQ = orc_resample_nearest(R, E, dbeta, R0, cap, seed, instance, i, counts, &Rn);
+            if (Rn > cap) {
+                rc = -1;
+                break;
+            }
+            orc_children_order(R, counts, parent);
+            R = (uint32_t)Rn;
+            if (parents_last) memcpy(parents_last, parent, sizeof(uint32_t) * R);
+            for (uint32_t m = 0; m < R; ++m)
+                memcpy(next + (size_t)m * N, spins + (size_t)parent[m] * N, (size_t)N);
+            memcpy(spins, next, (size_t)R * (size_t)N);
+            for (uint32_t r = 0; r < R; ++r)
+                orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                           (i - 1) * theta, theta);
+            lnZ += lnQ;
+        }
+        int64_t sE = 0;
+        for (uint32_t r = 0; r < R; ++r) {
+            orc_observables(dim, L, spins + (size_t)r * N, J, &E[r], &M[r]);
+            sE += E[r];
+        }
+        if (lnQ_out) lnQ_out[i] = lnQ;
+        if (lnZ_out) lnZ_out[i] = lnZ;
+        if (sumE_out) sumE_out[i] = sE;
+        if (nrep_out) nrep_out[i] = R;
+    }
+    if (E_final) memcpy(E_final, E, sizeof(int64_t) * R);
+    free(E);
+    free(M);
+    free(counts);
+    free(parent);
+    free(next);
+    return rc;
 }
 
 /* Batch form of the generator for tests: n counters, one key. */
