@@ -69,7 +69,9 @@ def _load():
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pt_run.argtypes = [i32, i32, p, u64, u32, u32, p, u32, u32, u32, u32, p, p, p, p]
         lib.orc_pa_run.argtypes = [i32, i32, p, u64, u32, u32, u32, p, u32, p, i32,
-                                   p, p, p, p, p, p, p, p, p, p, p]
+                                   p, p, p, p, p, p, p, p, p, p, p, i32]
+        lib.orc_msc_sweeps.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, u32, u32]
+        lib.orc_msc_uniforms.argtypes = [u64, u64, u32, u32, i32, u32, p]
         _lib = lib
         return lib
 
@@ -135,6 +137,23 @@ def sweeps(dim, L, s, J, beta, seed, instance, replica, t0, n):
     lib.orc_sweeps(dim, L, _ptr(s), _ptr(Jc), float(beta), seed, instance, replica, t0, n)
 
 
+def msc_uniforms(seed, k, t, group, colour, instance):
+    """The 32 uniforms of replicas 32 group .. 32 group + 31 at colour-rank k."""
+    lib = _load()
+    out = np.empty(32, dtype=np.uint32)
+    lib.orc_msc_uniforms(seed, k, t, group, colour, instance, _ptr(out))
+    return out
+
+
+def msc_sweeps(dim, L, s, J, beta, seed, instance, replica, t0, n):
+    """n checkerboard sweeps of replica ``replica`` with the multi-spin-coded
+    random numbers (reading R18): LCG outputs seeded per 32-replica group."""
+    lib = _load()
+    _check_spins(s, dim, L)
+    Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
+    lib.orc_msc_sweeps(dim, L, _ptr(s), _ptr(Jc), float(beta), seed, instance, replica, t0, n)
+
+
 def dcb_sweeps(L, tile, s, beta, seed, instance, replica, t0, k, n_rounds):
     """n_rounds double-checkerboard rounds (k sweeps per tile and round) of a
     2D ferromagnet ``s`` (int8, in place); the sweep counter advances by k
@@ -178,9 +197,10 @@ def resample_nearest(E, dbeta, R0, cap, seed, instance, step):
 
 
 def children_order(counts):
+    """Slot -> parent map: children of parent j contiguous, parents in order."""
     lib = _load()
     counts = np.ascontiguousarray(counts, dtype=np.uint32)
-    parent = np.empty(counts.size, dtype=np.uint32)
+    parent = np.empty(int(counts.sum(dtype=np.uint64)), dtype=np.uint32)
     lib.orc_children_order(counts.size, _ptr(counts), _ptr(parent))
     return parent
 
@@ -190,9 +210,10 @@ def linear_betas(beta_f: float, S: int) -> np.ndarray:
     return np.array([(float(beta_f) * float(i)) / float(S) for i in range(S + 1)], dtype=np.float64)
 
 
-def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_energies=False):
+def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_energies=False, msc=False):
     """Population annealing for one instance (Sec. 5.4). Returns a dict of per-step
-    arrays (index 0 = beta_0 = 0) and the final population."""
+    arrays (index 0 = beta_0 = 0) and the final population. msc: sweeps with the
+    multi-spin-coded random numbers (reading R18)."""
     lib = _load()
     betas = np.ascontiguousarray(betas, dtype=np.float64)
     S = betas.size - 1
@@ -215,7 +236,7 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_ene
     lib.orc_pa_run(dim, L, _ptr(Jc), seed, instance, R, S, _ptr(betas), theta, _ptr(spins),
                    int(init), _ptr(out["lnQ"]), _ptr(out["lnZ"]), _ptr(sumE), _ptr(out["sumE2"]),
                    _ptr(sumAbsM), _ptr(out["sumM2"]), _ptr(hashes), _ptr(E), _ptr(M), _ptr(parents),
-                   _ptr(E_steps))
+                   _ptr(E_steps), int(bool(msc)))
     out.update(sumE=sumE, sumAbsM=sumAbsM, counts_hash=hashes, E=E, M=M, parents=parents, E_steps=E_steps,
                spins=spins.reshape(R, N), betas=betas)
     return out

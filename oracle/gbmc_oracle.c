@@ -45,6 +45,10 @@
  *  R16 double checkerboard: see orc_dcb_sweeps.
  *  R17 nearest-integer resampling, variable population: see
  *      orc_resample_nearest.
+ *  R18 multi-spin coding across replicas (Sec. 5.4): replicas 32 w .. 32 w +
+ *      31 share, at each site and visit, one Philox word (purpose MSC 5,
+ *      counter (k >> 2, t, w, c3), word k & 3) that seeds an LCG; replica
+ *      32 w + b compares the LCG's (b + 1)-th output with the threshold.
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,6 +59,12 @@
 #define ORC_PURPOSE_INIT 1u
 #define ORC_PURPOSE_RESAMPLE 2u
 #define ORC_PURPOSE_COUPLING 3u
+#define ORC_PURPOSE_MSC 5u
+
+/* The linear congruential generator of the multi-spin-coded sweeps (reading
+ * R18): x -> a x + c mod 2^32 with the constants of Numerical Recipes. */
+#define ORC_LCG_A 1664525u
+#define ORC_LCG_C 1013904223u
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Sec. 4, counter-based generators).                         */
@@ -202,9 +212,21 @@ void orc_couplings(int L, uint64_t seed, uint32_t instance, int8_t *J)
  * holds the sites with x / tile = a, y / tile = b; its coarse colour is
  * (a + b) mod 2). The updated sites are never neighbours, so the order within
  * the loop does not matter. */
+/* Uniform of replica `replica` at colour-rank k in the multi-spin-coded
+ * sweeps (reading R18): the Philox word of (q = k >> 2, t, group = replica /
+ * 32, purpose MSC) seeds the LCG, whose (replica mod 32) + 1-th output it is. */
+static uint32_t orc_msc_uniform(uint64_t seed, uint64_t k, uint32_t t, uint32_t replica, int colour,
+                                uint32_t instance)
+{
+    uint32_t x = orc_word(seed, (uint32_t)(k >> 2), t, replica >> 5,
+                          orc_c3(ORC_PURPOSE_MSC, (uint32_t)colour, instance), (unsigned)(k & 3));
+    for (uint32_t j = 0; j <= (replica & 31u); ++j) x = ORC_LCG_A * x + ORC_LCG_C;
+    return x;
+}
+
 static void orc_update_sites(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
                              uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour,
-                             int tile, int coarse)
+                             int tile, int coarse, int msc)
 {
     int64_t N = orc_nsites(dim, L);
     uint32_t c3 = orc_c3(ORC_PURPOSE_METRO, (uint32_t)colour, instance);
@@ -228,7 +250,8 @@ static void orc_update_sites(int dim, int L, int8_t *s, const int8_t *J, const i
         if (dE <= 0) {
             accept = 1;
         } else {
-            uint32_t u = orc_word(seed, (uint32_t)(k >> 2), t, replica, c3, (unsigned)(k & 3));
+            uint32_t u = msc ? orc_msc_uniform(seed, (uint64_t)k, t, replica, colour, instance)
+                             : orc_word(seed, (uint32_t)(k >> 2), t, replica, c3, (unsigned)(k & 3));
             accept = (int64_t)u <= thr[dE / 4 - 1];
         }
         if (accept) s[i] = (int8_t)(-s[i]);
@@ -238,7 +261,27 @@ static void orc_update_sites(int dim, int L, int8_t *s, const int8_t *J, const i
 void orc_halfsweep(int dim, int L, int8_t *s, const int8_t *J, const int64_t *thr,
                    uint64_t seed, uint32_t instance, uint32_t replica, uint32_t t, int colour)
 {
-    orc_update_sites(dim, L, s, J, thr, seed, instance, replica, t, colour, 0, 0);
+    orc_update_sites(dim, L, s, J, thr, seed, instance, replica, t, colour, 0, 0, 0);
+}
+
+/* The 32 uniforms of one multi-spin-coded group at colour-rank k (tests). */
+void orc_msc_uniforms(uint64_t seed, uint64_t k, uint32_t t, uint32_t group, int colour, uint32_t instance,
+                      uint32_t *out)
+{
+    for (uint32_t b = 0; b < 32; ++b) out[b] = orc_msc_uniform(seed, k, t, 32u * group + b, colour, instance);
+}
+
+/* n checkerboard sweeps with the multi-spin-coded random numbers (reading
+ * R18) of replica `replica`: the same Metropolis rule and order as
+ * orc_sweeps, only the uniform of each (site, visit) differs. */
+void orc_msc_sweeps(int dim, int L, int8_t *s, const int8_t *J, double beta, uint64_t seed,
+                    uint32_t instance, uint32_t replica, uint32_t t0, uint32_t n)
+{
+    int64_t thr[3];
+    orc_thresholds(beta, dim, thr);
+    for (uint32_t m = 0; m < n; ++m)
+        for (int colour = 0; colour < 2; ++colour)
+            orc_update_sites(dim, L, s, J, thr, seed, instance, replica, t0 + m, colour, 0, 0, 1);
 }
 
 /* Double checkerboard with k hits per tile (Sec. 3.1, Fig. 5 right, the
@@ -259,7 +302,7 @@ void orc_dcb_sweeps(int L, int tile, int8_t *s, double beta, uint64_t seed, uint
             for (uint32_t j = 0; j < k; ++j)
                 for (int colour = 0; colour < 2; ++colour)
                     orc_update_sites(2, L, s, NULL, thr, seed, instance, replica, t0 + k * m + j, colour,
-                                     tile, coarse);
+                                     tile, coarse, 0);
 }
 
 /* n full sweeps (even sub-lattice, then odd), sweep counters t0 .. t0+n-1. */
@@ -435,13 +478,14 @@ void orc_children_order(uint32_t R, const uint32_t *counts, uint32_t *parent_of_
 /* Per step outputs (arrays of S+1, index 0 = beta_0): lnQ, lnZ, sum E,      */
 /* sum E^2 (as double of exact int64 sums), sum |M|, sum M^2, and a running   */
 /* FNV-1a hash of the counts; optionally the last step's slot -> parent map   */
-/* and every step's energies E_steps[S+1][R].                                 */
+/* and every step's energies E_steps[S+1][R]. msc != 0: the sweeps take the  */
+/* multi-spin-coded random numbers (reading R18).                             */
 /* ------------------------------------------------------------------------ */
 void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R,
                 uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                 double *lnQ_out, double *lnZ_out, int64_t *sumE_out, double *sumE2_out,
                 int64_t *sumAbsM_out, double *sumM2_out, uint64_t *counts_hash_out,
-                int64_t *E_final, int64_t *M_final, uint32_t *parents_last, int64_t *E_steps)
+                int64_t *E_final, int64_t *M_final, uint32_t *parents_last, int64_t *E_steps, int msc)
 {
     int64_t N = orc_nsites(dim, L);
     int64_t *E = (int64_t *)malloc(sizeof(int64_t) * R);
@@ -470,9 +514,14 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
             for (uint32_t m = 0; m < R; ++m)
                 memcpy(next + (size_t)m * N, spins + (size_t)parent[m] * N, (size_t)N);
             memcpy(spins, next, (size_t)R * (size_t)N);
-            for (uint32_t r = 0; r < R; ++r)
-                orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
-                           (i - 1) * theta, theta);
+            for (uint32_t r = 0; r < R; ++r) {
+                if (msc)
+                    orc_msc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                                   (i - 1) * theta, theta);
+                else
+                    orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                               (i - 1) * theta, theta);
+            }
             lnZ += lnQ;
         }
         int64_t sE = 0, sAM = 0;
@@ -508,7 +557,7 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
  * step i. Per step: lnQ, lnZ, sum E over the population and its size R_i;
  * E_final[cap] / parents_last[cap] for the last step's first R_S slots.
  * Returns 0, or -1 (outputs up to that step valid) if a step would need more
- * than cap replicas. */
+ * than cap replicas or would leave none. */
 int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R0,
                        uint32_t cap, uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                        double *lnQ_out, double *lnZ_out, int64_t *sumE_out, uint32_t *nrep_out,
@@ -534,7 +583,7 @@ int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t 
             double dbeta = betas[i] - betas[i - 1];
             uint64_t Rn;
             lnQ = orc_resample_nearest(R, E, dbeta, R0, cap, seed, instance, i, counts, &Rn);
-            if (Rn > cap) {
+            if (Rn > cap || Rn == 0) {  /* outgrown the capacity, or died out */
                 rc = -1;
                 break;
             }
