@@ -153,6 +153,16 @@ def rank_instance_base(rank: int, lattice: int, n_lattices: int) -> int:
     return (rank * n_lattices + lattice) * 64
 
 
+def sum_over_ranks(dist, ws, value, device=None):
+    if ws == 1:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def max_over_ranks(dist, ws, value, device=None):
     if ws == 1:
         return value
@@ -177,6 +187,10 @@ WORKLOADS = {
     "ising2d-L4096-dcb": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=0, dcb=(10, 64)),
     # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
     "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
+    # the default workload with nearest-integer resampling and a variable population:
+    # R_0 = 10^5, capacity 1.05 10^5 (Sec. 5.4, Eq. (13) with R_{i-1})
+    "pa-ising2d-L64-nearest": dict(kind="pa", lattices=[(2, 64, FM, 1, 105000)], S=100, theta=10, beta_f=1.0,
+                                   nearest=100000),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
     "pa-mixed-2d": dict(kind="pa", lattices=[(2, 32, FM, 1, 100000), (2, 64, FM, 1, 50000),
                                              (2, 128, FM, 1, 20000), (2, 256, FM, 1, 10000)],
@@ -234,11 +248,18 @@ def run_gpu(args, w, ws, rank, local):
             result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
                                 "row_walk": tuned.row_walk, "persistent": tuned.persistent,
                                 "candidates": tuned.n_candidates}
-        pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True)
+        kw = dict(resample=gbmc.GBMC_RESAMPLE_NEAREST, initial_replicas=w["nearest"]) if "nearest" in w else {}
+        pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True, **kw)
 
         def step(k):
             gbmc.pa_reset(ctx, pa, True, seed0 + k)
-            gbmc.pa_run(ctx, pa)
+            if "nearest" not in w:
+                gbmc.pa_run(ctx, pa)
+                return site_updates_per_step(w)
+            # variable populations: count the updates the run made (sizes R_1..R_S)
+            stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
+            return sum(int(stats[1:, p]["n_replicas"].sum()) * l[1] ** l[0] * w["theta"]
+                       for p, l in enumerate(w["lattices"]))
     else:
         N = w["L"] ** w["dim"]
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0, layout=w.get("layout", 0))
@@ -246,6 +267,7 @@ def run_gpu(args, w, ws, rank, local):
 
         def step(k):
             sweep_lattice(gbmc, ctx, lat, w)
+            return site_updates_per_step(w)
 
     for k in range(args.warmup):
         step(k)
@@ -259,8 +281,9 @@ def run_gpu(args, w, ws, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        upd = 0
         for k in range(args.steps):
-            step(first + k)
+            upd += step(first + k)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(dist, ws)
@@ -268,19 +291,21 @@ def run_gpu(args, w, ws, rank, local):
         if profile:
             prof = gbmc.gbmc_profile_read(ctx)
             gbmc.gbmc_profile(ctx, False)
-        return e0.elapsed_time(e1), prof
+        return e0.elapsed_time(e1), prof, upd
 
     # timed region: K steps bracketed by barrier + synchronize, no instrumentation
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = gbmc.gbmc_kernel_launches()
-    ms_local, _ = timed(args.warmup, False)
+    ms_local, _, upd_local = timed(args.warmup, False)
     launches = gbmc.gbmc_kernel_launches() - launches0
     clocks = sampler.stop()
     # the same K steps again with a CUDA event pair around every launch: per-kernel times
-    ms_prof, prof = timed(args.warmup + args.steps, True)
+    ms_prof, prof, _ = timed(args.warmup + args.steps, True)
     ms = max_over_ranks(dist, ws, ms_local, device="cuda")
-    result.update(ms=ms, ms_profiled=ms_prof, prof=prof, launches=launches, clocks=clocks)
+    upd_all = sum_over_ranks(dist, ws, float(upd_local), device="cuda")
+    result.update(ms=ms, ms_profiled=ms_prof, prof=prof, launches=launches, clocks=clocks, upd_all=upd_all,
+                  upd_local=upd_local)
 
     # end-to-end through the C ABI with host buffers: the population comes in
     # from pinned host memory, and the final population and statistics go back,
@@ -448,11 +473,18 @@ def cpu_oracle_sample(w):
         betas = oracle.linear_betas(w["beta_f"], w["S"])[: steps + 1]
         J = oracle.couplings(L, 1, 0) if model == EA else None
         t0 = time.perf_counter()
-        oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J)
+        if "nearest" in w:
+            Rs = min(Rs, w["nearest"])
+            r = oracle.pa_run_nearest(dim, L, 1, 0, Rs, Rs + Rs // 10 + 16, betas, w["theta"], J=J)
+            upd = int(r["nrep"][1:].sum()) * L ** dim * w["theta"]
+            name = "pa_run_nearest"
+        else:
+            oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J)
+            upd = Rs * L ** dim * w["theta"] * steps
+            name = "pa_run"
         dt = time.perf_counter() - t0
-        upd = Rs * L ** dim * w["theta"] * steps
-        desc = "oracle pa_run: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
-               "theta=%d" % (dim, L, Rs, R, steps, w["S"], w["theta"])
+        desc = "oracle %s: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
+               "theta=%d" % (name, dim, L, Rs, w.get("nearest", R), steps, w["S"], w["theta"])
     elif "dcb" in w:
         k, tile = w["dcb"]
         s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
@@ -538,7 +570,8 @@ def main():
         return
     peaks, peak_src = load_peaks()
     ms = res["ms"]
-    value = ws * upd * args.steps / (ms * 1e6)  # site updates per ns, all ranks
+    value = res["upd_all"] / (ms * 1e6)  # site updates per ns, all ranks
+    upd_step = res["upd_local"] / args.steps  # this rank's updates per step (variable populations: measured)
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
     kname = "sweep_resident" if w["kind"] == "pa" else \
@@ -546,8 +579,10 @@ def main():
     n_l, t_l = prof.get(kname, (0, 0.0))
     avg_ms = t_l / n_l if n_l else float("nan")
     if w["kind"] == "pa":
-        upd_per_launch = sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"]
-        hbm_bytes_per_launch = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
+        # variable populations: the mean population of the timed runs
+        live = [upd_step / (w["S"] * w["theta"] * l[1] ** l[0]) if "nearest" in w else copies(l) for l in w["lattices"]]
+        upd_per_launch = sum(n * l[1] ** l[0] for n, l in zip(live, w["lattices"])) * w["theta"]
+        hbm_bytes_per_launch = sum(n * (2 * l[1] ** l[0] + 12) for n, l in zip(live, w["lattices"]))
     elif "dcb" in w:
         k, tile = w["dcb"]
         upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
@@ -569,8 +604,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8 spins / int32 energies / f64 weights", "data": "synthetic",
         "config": config,
-        "replica_sweeps_per_s": (ws * sum(copies(l) for l in w["lattices"]) * w["theta"] * w["S"] * args.steps
-                                 / (ms * 1e-3)) if w["kind"] == "pa" else None,
+        "replica_sweeps_per_s": (res["upd_all"] / (w["lattices"][0][1] ** w["lattices"][0][0]) / (ms * 1e-3))
+        if w["kind"] == "pa" and len(w["lattices"]) == 1 else None,
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
                      "frac": achieved / peak_alu,
                      "traffic": recorded_traffic(None, copies(w["lattices"][0]))
@@ -592,7 +627,7 @@ def main():
         "clocks": clk,
     }
     e = res["e2e"]
-    e2e_upd = upd
+    e2e_upd = upd_step
     line["e2e"] = {"value": ws * e2e_upd / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"]}
     if not args.no_cpu_baseline:

@@ -230,6 +230,22 @@ gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tu
 /* Population annealing (Sec. 5.4): every (lattice, instance) pair is one     */
 /* population of n_replicas replicas annealed from beta_0 = 0.               */
 /* ------------------------------------------------------------------------ */
+/* Resampling laws (Sec. 5.4 step 2):
+ *  MULTINOMIAL: R draws from the integer weights W_j = floor(2^s
+ *    exp(-dbeta (E_j - Emin))), s = 63 - ceil(log2 R); the population stays R.
+ *  NEAREST: replica j gets floor(tau_j) copies and one more with probability
+ *    frac(tau_j), tau_j = R_0 W_j / sum_k W_k (s from the capacity): the weight
+ *    e^{-dbeta E_j} / Q_i of the paper rescaled so that the expected population
+ *    is R_0 at every step; the size R_i varies and Q_i of Eq. (13) uses
+ *    R_{i-1}. The extra copy is decided exactly in integers: floor(U64_j C /
+ *    2^64) < (R_0 W_j mod C), C = sum_k W_k, U64_j the resampling word of
+ *    replica j. The first R_i slots of each population are live; a step that
+ *    would need more slots than the capacity keeps the first `capacity`
+ *    children, and the next gbmc_sync / pa_step / pa_run returns
+ *    GBMC_ERR_STATE (the run is then invalid); so does a step that leaves a
+ *    population empty. Fixed schedules only. */
+enum { GBMC_RESAMPLE_MULTINOMIAL = 0, GBMC_RESAMPLE_NEAREST = 1 };
+
 enum {
     GBMC_SCHED_LINEAR = 0,    /* beta_i = (beta_f * i) / n_steps, i = 0..n_steps */
     GBMC_SCHED_LIST = 1,      /* beta_i = betas[i], i = 0..n_steps, betas[0] = 0 */
@@ -250,6 +266,9 @@ typedef struct {
     const float *mlp_params; /* GBMC_SCHED_MLP: host fp32 parameters, gbmc_mlp_param_count() */
     double overlap_lo;       /* GBMC_SCHED_MLP: accept a proposal if lo <= overlap <= hi */
     double overlap_hi;
+    int32_t resample;        /* GBMC_RESAMPLE_MULTINOMIAL (0, constant R) or GBMC_RESAMPLE_NEAREST */
+    uint32_t initial_replicas; /* GBMC_RESAMPLE_NEAREST: R_0 (0 = n_replicas); the lattices'
+                                  n_replicas is then the capacity of each population */
 } gbmc_pa_config;
 
 /* Per-population record of one annealing step (after its sweeps). */
@@ -262,7 +281,7 @@ typedef struct {
     int64_t sumAbsM, sumM2;  /* exact sums of |M| and M^2 */
     int32_t Emin, Emax;      /* population energy range */
     uint32_t step;           /* i */
-    uint32_t n_replicas;     /* R */
+    uint32_t n_replicas;     /* R_i: population size after step i (R for multinomial) */
     double overlap;          /* adaptive schedules: realised histogram overlap, else 0 */
     int32_t proposal_kind;   /* 0 fixed, 1 bisection, 2 accepted MLP proposal */
     int32_t pad;

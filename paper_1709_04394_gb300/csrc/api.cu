@@ -70,7 +70,8 @@ struct gbmc_ctx {
     int device;
     cudaStream_t stream;
     int sm_count;
-    unsigned int* words = nullptr;  // device [barrier counter, error flag, unit claims, finished CTAs]
+    unsigned int* words = nullptr;  // device [barrier counter, error flag, unit claims, finished CTAs,
+                                    //         population overflow flag, 3 spare]
     bool fused = true;              // one cooperative resampling launch per lattice and step
     int32_t launch_mode = GBMC_LAUNCH_AUTO;  // grid or persistent resident sweeps
     uint32_t phantom = 0;           // test hook: extra barrier arrivals to wait for
@@ -168,6 +169,7 @@ struct PaLat {
     double overlap = 0.0;                  // realised overlap of the last step
     int32_t kind = 0;                      // how the last step was chosen
     std::vector<gbmc_schedule_record> log;
+    uint32_t* nrep = nullptr;              // nearest-integer law: [2][n_inst] R_i by step parity
 };
 
 }  // namespace
@@ -180,6 +182,8 @@ struct gbmc_pa {
     uint32_t S = 0;        // steps of a fixed schedule; step cap of an adaptive one
     uint32_t step = 0;     // steps enqueued
     bool adaptive = false;
+    bool nearest = false;  // nearest-integer resampling, variable populations
+    uint32_t R0 = 0;       // its initial (and expected) population
     gbmc_pa_stats* stats = nullptr;  // device [S+1][P]
     SchedOut* sched_dev = nullptr;   // [kMaxJobs]
     SchedOut* sched_host = nullptr;  // pinned copy
@@ -405,12 +409,12 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, void* cuda_stream) {
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     c->fused = coop != 0;
     {
-        cudaError_t e = cudaMalloc(&c->words, 4 * sizeof(unsigned int));
+        cudaError_t e = cudaMalloc(&c->words, 8 * sizeof(unsigned int));
         if (e != cudaSuccess) {
             delete c;
             return fail(GBMC_ERR_OOM, "cudaMalloc(context words): %s", cudaGetErrorString(e));
         }
-        e = cudaMemset(c->words, 0, 4 * sizeof(unsigned int));
+        e = cudaMemset(c->words, 0, 8 * sizeof(unsigned int));
         if (e != cudaSuccess) {
             cudaFree(c->words);
             delete c;
@@ -427,15 +431,21 @@ gbmc_status gbmc_set_stream(gbmc_ctx* ctx, void* cuda_stream) {
     return GBMC_OK;
 }
 
-// Reads (and clears) the device error flag raised by a bounded wait that ran
-// out; the stream must have been synchronised.
+// Reads (and clears) the device error flags: a bounded wait that ran out
+// (word 1) and a population that outgrew its capacity (word 4); the stream
+// must have been synchronised.
 static gbmc_status check_device_error(gbmc_ctx* ctx) {
-    unsigned int err = 0;
-    CUDA_TRY(cudaMemcpy(&err, ctx->words + 1, sizeof(err), cudaMemcpyDeviceToHost));
-    if (err) {
-        CUDA_TRY(cudaMemset(ctx->words + 1, 0, sizeof(err)));
+    unsigned int w[8] = {};
+    CUDA_TRY(cudaMemcpy(w, ctx->words, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w[1]) {
+        CUDA_TRY(cudaMemset(ctx->words + 1, 0, sizeof(unsigned int)));
         return fail(GBMC_ERR_TIMEOUT, "a grid barrier wait ran out of its cycle budget; results since the last "
                                       "check are invalid");
+    }
+    if (w[4]) {
+        CUDA_TRY(cudaMemset(ctx->words + 4, 0, sizeof(unsigned int)));
+        return fail(GBMC_ERR_STATE, "a population outgrew its capacity (nearest-integer resampling); the run "
+                                    "is invalid");
     }
     return GBMC_OK;
 }
@@ -893,6 +903,14 @@ static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
     P.e_lo = pl.e_lo;
     P.overlap = step == 0 ? 0.0 : pl.overlap;
     P.kind = step == 0 ? 0 : pl.kind;
+    if (pa->nearest) {
+        const uint32_t I = l->d.n_instances;
+        P.nnext = pl.nrep + (uint64_t)(step & 1u) * I;
+        P.nprev = step == 0 ? nullptr : pl.nrep + (uint64_t)((step - 1) & 1u) * I;
+        P.overflow = pa->ctx->words + 4;
+        P.R0 = pa->R0;
+        P.nearest = 1;
+    }
     return P;
 }
 
@@ -928,6 +946,7 @@ static gbmc_status pa_sweep_launch(gbmc_pa* pa, bool first) {
         J.emin = pl.emin;
         J.emax = pl.emax;
         J.sums = pl.sums;
+        if (pa->nearest) J.nlive = pl.nrep + (uint64_t)(step & 1u) * l->d.n_instances;
         if (first) {
             J.nsweeps = 0;
             J.src = J.dst = l->cur;
@@ -1011,6 +1030,10 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     if (cfg->theta == 0) return fail(GBMC_ERR_ARG, "theta must be >= 1");
     if (sched == GBMC_SCHED_LIST && !cfg->betas) return fail(GBMC_ERR_ARG, "betas required for a list schedule");
     if (sched == GBMC_SCHED_MLP && !cfg->mlp_params) return fail(GBMC_ERR_ARG, "mlp_params required for the MLP schedule");
+    if (cfg->resample != GBMC_RESAMPLE_MULTINOMIAL && cfg->resample != GBMC_RESAMPLE_NEAREST)
+        return fail(GBMC_ERR_ARG, "unknown resampling law %d", cfg->resample);
+    const bool nearest = cfg->resample == GBMC_RESAMPLE_NEAREST;
+    if (nearest && adaptive) return fail(GBMC_ERR_ARG, "nearest-integer resampling needs a fixed schedule");
     if (adaptive) {
         if (!(cfg->beta_f > 0.0) || !(cfg->dbeta_max > 0.0)) return fail(GBMC_ERR_ARG, "adaptive schedules need beta_f > 0 and dbeta_max > 0");
         if (!(cfg->target_overlap > 0.0 && cfg->target_overlap < 1.0)) return fail(GBMC_ERR_ARG, "target_overlap must lie in (0, 1)");
@@ -1031,6 +1054,12 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
             return fail(GBMC_ERR_ARG, "population annealing runs on the int8 layout (lattice %u is bit-packed)", i);
         if (adaptive && l->d.n_instances != 1)
             return fail(GBMC_ERR_ARG, "adaptive schedules anneal one population per lattice (n_instances = 1)");
+        if (l->d.n_replicas != l0->d.n_replicas && nearest)
+            return fail(GBMC_ERR_ARG, "nearest-integer resampling: every lattice has the same capacity");
+        if (nearest && cfg->initial_replicas > l->d.n_replicas)
+            return fail(GBMC_ERR_ARG, "initial_replicas exceeds the capacity n_replicas of lattice %u", i);
+        if (!nearest && cfg->initial_replicas != 0 && cfg->initial_replicas != l->d.n_replicas)
+            return fail(GBMC_ERR_ARG, "multinomial resampling keeps R = n_replicas (initial_replicas must be 0)");
         for (uint32_t k = 0; k < i; ++k)
             if (lattices[k] == l) return fail(GBMC_ERR_ARG, "lattice %u listed twice", i);
         ls.push_back(l);
@@ -1052,6 +1081,8 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     pa->cfg.mlp_params = nullptr;
     pa->S = cfg->n_steps;
     pa->adaptive = adaptive;
+    pa->nearest = nearest;
+    pa->R0 = cfg->initial_replicas ? cfg->initial_replicas : l0->d.n_replicas;
     pa->lats.resize(n_lattices);
     gbmc_status st = GBMC_OK;
     uint32_t pop = 0;
@@ -1116,6 +1147,10 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         pl.ntot = (uint32_t*)p;
         if ((st = dalloc(pa, &p, C * 4)) != GBMC_OK) break;
         pl.parent = (uint32_t*)p;
+        if (nearest) {
+            if ((st = dalloc(pa, &p, 2ull * I * 4)) != GBMC_OK) break;
+            pl.nrep = (uint32_t*)p;
+        }
         cudaError_t ce = cudaMemsetAsync(pl.counts, 0, C * 4, ctx->stream);
         // every slot starts with a valid parent, so a step whose resampling was
         // abandoned (timed-out barrier) still gathers in bounds
@@ -1254,7 +1289,8 @@ static gbmc_status pa_enqueue_common(gbmc_pa* pa) {
         }
         {
             ProfScope ps_(pa->ctx, PK_PA_DRAWS);
-            CUDA_TRY(launch_pa_draws(P, s));
+            if (pa->nearest) CUDA_TRY(launch_pa_nearest(P, s));
+            else CUDA_TRY(launch_pa_draws(P, s));
         }
         {
             ProfScope ps_(pa->ctx, PK_PA_PLACE);
@@ -1424,7 +1460,8 @@ gbmc_status pa_run(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, uint32
 // What a captured run depends on besides the run's own buffers: stream, each
 // lattice's seed, starting buffer and sweep counter, and the resampling mode.
 static std::vector<uint64_t> graph_key(const gbmc_pa* pa) {
-    std::vector<uint64_t> k{(uint64_t)(uintptr_t)pa->ctx->stream, (uint64_t)pa->ctx->fused};
+    std::vector<uint64_t> k{(uint64_t)(uintptr_t)pa->ctx->stream, (uint64_t)pa->ctx->fused,
+                            (uint64_t)pa->ctx->launch_mode};
     for (auto& pl : pa->lats) {
         k.push_back(pl.lat->d.seed);
         k.push_back((uint64_t)(uintptr_t)pl.lat->cur);

@@ -41,6 +41,7 @@ struct SweepJob {
     uint32_t ctas_per_inst;
     const uint32_t* thr_temp; // parallel tempering: [T][3] thresholds per temperature, or null
     const uint32_t* temp_of;  // parallel tempering: [n_inst*R] temperature of each copy, or null
+    const uint32_t* nlive;    // variable populations: [n_inst] live copies (the first ones); null: R
 };
 
 struct SweepLaunch {
@@ -127,6 +128,12 @@ struct PaLattice {
     uint32_t R, n_inst, inst_base, nbins, nchunks, step;
     int32_t e_lo;
     int32_t kind;             // how the step was chosen (recorded)
+    // nearest-integer resampling with variable populations (R = capacity):
+    const uint32_t* nprev;    // [n_inst] R_{i-1} (read), or null (multinomial, constant R)
+    uint32_t* nnext;          // [n_inst] R_i (written by the placement), or null
+    unsigned int* overflow;   // raised when children exceed the capacity
+    uint32_t R0;              // target population
+    int32_t nearest;          // 1: nearest-integer law instead of multinomial draws
 };
 
 constexpr uint32_t kScanChunk = 2048;  // replicas per resampling chunk (512 threads x 4)
@@ -147,6 +154,7 @@ cudaError_t launch_pa_resample_fused(const PaLattice& P, double* lnZ, const Grid
 cudaError_t launch_pa_weights(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_reduce(const PaLattice& P, double* lnZ, int first_step, cudaStream_t s);
 cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s);
+cudaError_t launch_pa_nearest(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_place(const PaLattice& P, cudaStream_t s);
 cudaError_t launch_pa_record(const PaLattice& P, const double* lnZ, double lnQ_unused, cudaStream_t s);
 cudaError_t launch_pa_reset(const PaLattice& P, cudaStream_t s);

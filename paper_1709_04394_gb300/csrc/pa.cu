@@ -17,6 +17,12 @@
 //   k_pa_count_scan, k_pa_place : exclusive scan of the counts; parent j fills
 //                  slots [S_j, S_j + n_j): children contiguous, parents in order.
 // The sweep kernel then gathers slot c from parent[c] while loading.
+//
+// Nearest-integer law (variable populations, P.nprev / P.nnext set): the
+// draws are replaced by k_pa_nearest -- replica j gets floor(tau_j) copies
+// plus one with probability frac(tau_j), tau_j = R0 W_j / C, decided in
+// integers -- every phase only looks at the R_{i-1} live replicas, ln Q uses
+// R_{i-1}, and the placement writes R_i (at most the capacity P.R).
 #include <climits>
 
 #include "../../include/gbmc.h"
@@ -28,12 +34,26 @@ namespace gbmc {
 constexpr int kScanThreads = 512;
 constexpr int kPerThread = kScanChunk / kScanThreads;  // 4
 
+// Replicas of population `inst` before this step's resampling: R_{i-1}.
+__device__ __forceinline__ uint32_t live_prev(const PaLattice& P, uint32_t inst) {
+    return P.nprev ? __ldcg(P.nprev + inst) : P.R;
+}
+
+// 64-bit uniform of resampling draw (or replica) k of population `inst`.
+__device__ __forceinline__ unsigned long long resample_u64(const PaLattice& P, uint32_t inst, uint32_t k) {
+    const uint4 w = philox4x32_10(
+        make_uint4(k >> 1, P.step, 0u, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
+        (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    return (k & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
+}
+
 // ---- the five phases, as block-level device functions ----
 
 // Integer weights of one chunk and their inclusive sums within the chunk.
 __device__ __forceinline__ void phase_weights(const PaLattice& P, uint32_t inst, uint32_t chunk,
                                               unsigned long long* sh) {
     const uint64_t base = (uint64_t)inst * P.R;
+    const uint32_t live = live_prev(P, inst);
     const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
     const int32_t emin = P.emin[inst];
     unsigned long long w[kPerThread];
@@ -42,7 +62,7 @@ __device__ __forceinline__ void phase_weights(const PaLattice& P, uint32_t inst,
     for (int i = 0; i < kPerThread; ++i) {
         const uint32_t j = j0 + i;
         unsigned long long v = 0;
-        if (j < P.R) v = P.wint[(uint32_t)(P.E[base + j] - emin) >> 2];
+        if (j < live) v = P.wint[(uint32_t)(P.E[base + j] - emin) >> 2];
         run += v;
         w[i] = run;
     }
@@ -62,13 +82,15 @@ __device__ __forceinline__ void phase_weights(const PaLattice& P, uint32_t inst,
 __device__ __forceinline__ void phase_reduce(const PaLattice& P, uint32_t inst, double* lnZ, double* lnQ_out,
                                              double* sd, unsigned long long* su) {
     const int32_t emin = P.emin[inst], emax = P.emax[inst];
-    const uint32_t bmin = (uint32_t)(emin - P.e_lo) >> 2, bmax = (uint32_t)(emax - P.e_lo) >> 2;
     uint32_t* h = P.hist + (uint64_t)inst * P.nbins;
     double acc = 0.0;
-    for (uint32_t b = bmin + threadIdx.x; b <= bmax; b += blockDim.x) {
-        const uint32_t hb = h[b];
-        if (hb) acc += (double)hb * P.wexp[b - bmin];
-        h[b] = 0u;
+    if (emin <= emax) {  // an empty population (variable sizes) has no range
+        const uint32_t bmin = (uint32_t)(emin - P.e_lo) >> 2, bmax = (uint32_t)(emax - P.e_lo) >> 2;
+        for (uint32_t b = bmin + threadIdx.x; b <= bmax; b += blockDim.x) {
+            const uint32_t hb = h[b];
+            if (hb) acc += (double)hb * P.wexp[b - bmin];
+            h[b] = 0u;
+        }
     }
     acc = warp_sum(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -78,7 +100,8 @@ __device__ __forceinline__ void phase_reduce(const PaLattice& P, uint32_t inst, 
         double v = lane < nwarps ? sd[lane] : 0.0;
         v = warp_sum(v);
         if (lane == 0) {
-            const double lnQ = -P.dbeta * (double)emin + log(v) - P.log_R;
+            const double log_R = P.nprev ? log((double)live_prev(P, inst)) : P.log_R;
+            const double lnQ = -P.dbeta * (double)emin + log(v) - log_R;
             lnQ_out[inst] = lnQ;
             lnZ[inst] += lnQ;
         }
@@ -107,11 +130,7 @@ __device__ __forceinline__ void phase_reduce(const PaLattice& P, uint32_t inst, 
 // Multinomial draw g (global over the lattice's populations).
 __device__ __forceinline__ void phase_draw(const PaLattice& P, uint64_t g) {
     const uint32_t inst = (uint32_t)(g / P.R), k = (uint32_t)(g - (uint64_t)inst * P.R);
-    const uint4 w = philox4x32_10(
-        make_uint4(k >> 1, P.step, 0u, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
-        (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-    const unsigned long long U = (k & 1u) ? (((unsigned long long)w.w << 32) | w.z)
-                                          : (((unsigned long long)w.y << 32) | w.x);
+    const unsigned long long U = resample_u64(P, inst, k);
     const unsigned long long* cp = P.cpre + (uint64_t)inst * (P.nchunks + 1);
     // data written by other CTAs earlier in a fused launch: read through L2 (__ldcg)
     const unsigned long long x = __umul64hi(U, __ldcg(cp + P.nchunks));
@@ -134,9 +153,26 @@ __device__ __forceinline__ void phase_draw(const PaLattice& P, uint64_t g) {
     atomicAdd(&P.counts[base + a], 1u);
 }
 
+// Nearest-integer copies of replica g (global over the lattice's populations):
+// n_j = floor(R0 W_j / C) + [floor(U64_j C / 2^64) < (R0 W_j mod C)], C = sum W.
+// R0 W_j <= capacity 2^s <= 2^63 and C <= R_{i-1} 2^s <= 2^63 by the choice of s.
+__device__ __forceinline__ void phase_nearest(const PaLattice& P, uint64_t g) {
+    const uint32_t inst = (uint32_t)(g / P.R), j = (uint32_t)(g - (uint64_t)inst * P.R);
+    if (j >= live_prev(P, inst)) return;
+    const uint64_t base = (uint64_t)inst * P.R;
+    // W_j from the inclusive in-chunk sums (E_min was already reset by ln Q's phase)
+    const unsigned long long W = __ldcg(P.cloc + base + j) - ((j % kScanChunk) ? __ldcg(P.cloc + base + j - 1) : 0ull);
+    const unsigned long long C = __ldcg(P.cpre + (uint64_t)inst * (P.nchunks + 1) + P.nchunks);
+    const unsigned long long num = (unsigned long long)P.R0 * W;
+    const unsigned long long n0 = num / C, rem = num - n0 * C;
+    const unsigned long long x = __umul64hi(resample_u64(P, inst, j), C);
+    P.counts[base + j] = (uint32_t)n0 + (x < rem ? 1u : 0u);
+}
+
 // Exclusive scan of the counts within one chunk, chunk total.
 __device__ __forceinline__ void phase_count_scan(const PaLattice& P, uint32_t inst, uint32_t chunk, uint32_t* sh) {
     const uint64_t base = (uint64_t)inst * P.R;
+    const uint32_t live = live_prev(P, inst);
     const uint32_t j0 = chunk * kScanChunk + threadIdx.x * kPerThread;
     uint32_t v[kPerThread];
     uint32_t run = 0;
@@ -144,7 +180,7 @@ __device__ __forceinline__ void phase_count_scan(const PaLattice& P, uint32_t in
     for (int i = 0; i < kPerThread; ++i) {
         const uint32_t j = j0 + i;
         v[i] = run;  // exclusive within the thread
-        if (j < P.R) run += __ldcg(P.counts + base + j);
+        if (j < live) run += __ldcg(P.counts + base + j);
     }
     uint32_t total;
     const uint32_t incl = block_inclusive_scan<uint32_t>(run, sh, &total);
@@ -152,14 +188,17 @@ __device__ __forceinline__ void phase_count_scan(const PaLattice& P, uint32_t in
 #pragma unroll
     for (int i = 0; i < kPerThread; ++i) {
         const uint32_t j = j0 + i;
-        if (j < P.R) P.sloc[base + j] = excl + v[i];
+        if (j < live) P.sloc[base + j] = excl + v[i];
     }
     if (threadIdx.x == 0) P.ntot[(uint64_t)inst * P.nchunks + chunk] = total;
 }
 
 // Parent j fills slots [S_j, S_j + n_j); counts are cleared for the next step.
+// Variable populations: slots at or beyond the capacity are not written (the
+// overflow flag is raised instead) and the last chunk's CTA records R_i.
 __device__ __forceinline__ void phase_place(const PaLattice& P, uint32_t inst, uint32_t chunk, uint32_t* prefix) {
     const uint64_t base = (uint64_t)inst * P.R;
+    const uint32_t live = live_prev(P, inst);
     if (threadIdx.x < 32) {
         uint32_t acc = 0;
         for (uint32_t c = threadIdx.x; c < chunk; c += 32) acc += __ldcg(P.ntot + (uint64_t)inst * P.nchunks + c);
@@ -168,13 +207,27 @@ __device__ __forceinline__ void phase_place(const PaLattice& P, uint32_t inst, u
     }
     __syncthreads();
     const uint32_t pre = *prefix;
+    if (P.nnext && threadIdx.x == 0 && chunk + 1 == P.nchunks) {
+        uint64_t total = (uint64_t)pre + __ldcg(P.ntot + (uint64_t)inst * P.nchunks + chunk);
+        if (total > P.R || total == 0) {  // outgrown its capacity, or died out
+            atomicExch(P.overflow, 1u);
+            if (total > P.R) total = P.R;
+        }
+        P.nnext[inst] = (uint32_t)total;
+    }
     for (uint32_t i = threadIdx.x; i < kScanChunk; i += blockDim.x) {
         const uint32_t j = chunk * kScanChunk + i;
-        if (j >= P.R) break;
+        if (j >= live) break;
         const uint32_t n = __ldcg(P.counts + base + j);
         if (n) {
-            const uint32_t S = pre + __ldcg(P.sloc + base + j);
-            for (uint32_t m = 0; m < n; ++m) P.parent[base + S + m] = j;
+            const uint64_t S = (uint64_t)pre + __ldcg(P.sloc + base + j);
+            for (uint32_t m = 0; m < n; ++m) {
+                if (S + m >= P.R) {
+                    atomicExch(P.overflow, 1u);
+                    break;
+                }
+                P.parent[base + S + m] = j;
+            }
             P.counts[base + j] = 0u;
         }
     }
@@ -219,6 +272,19 @@ __global__ void __launch_bounds__(256) k_pa_draws(const __grid_constant__ PaLatt
 cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s) {
     const uint64_t total = (uint64_t)P.n_inst * P.R;
     k_pa_draws<<<(uint32_t)((total + 255) / 256), 256, 0, s>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_pa_nearest(const __grid_constant__ PaLattice P) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)P.n_inst * P.R) return;
+    phase_nearest(P, g);
+}
+
+cudaError_t launch_pa_nearest(const PaLattice& P, cudaStream_t s) {
+    const uint64_t total = (uint64_t)P.n_inst * P.R;
+    k_pa_nearest<<<(uint32_t)((total + 255) / 256), 256, 0, s>>>(P);
     count_launch();
     return cudaGetLastError();
 }
@@ -288,8 +354,10 @@ __global__ void __launch_bounds__(kScanThreads) k_pa_resample_fused(const __grid
         phase_reduce(P, inst, lnZ, lnZ + P.n_inst, sd, sh64);
     if (!grid_barrier(B, target)) return;
     const uint64_t total = (uint64_t)P.n_inst * P.R;
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x)
-        phase_draw(P, g);
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+        if (P.nearest) phase_nearest(P, g);
+        else phase_draw(P, g);
+    }
     if (!grid_barrier(B, target)) return;
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) phase_count_scan(P, c / P.nchunks, c % P.nchunks, sh32);
     if (!grid_barrier(B, target)) return;
@@ -335,7 +403,7 @@ __global__ void k_pa_record(const __grid_constant__ PaLattice P, const double* l
     st->Emin = P.emin[inst];
     st->Emax = P.emax[inst];
     st->step = P.step;
-    st->n_replicas = P.R;
+    st->n_replicas = P.nnext ? P.nnext[inst] : P.R;
     st->overlap = P.overlap;
     st->proposal_kind = P.kind;
     st->pad = 0;
@@ -357,6 +425,7 @@ __global__ void k_pa_reset(const __grid_constant__ PaLattice P) {
         P.emax[inst] = INT_MIN;
         unsigned long long* sums = P.sums + (uint64_t)inst * 4;
         sums[0] = sums[1] = sums[2] = sums[3] = 0ull;
+        if (P.nnext) P.nnext[inst] = P.R0;  // R_0
     }
 }
 

@@ -116,7 +116,10 @@ __device__ __forceinline__ void resident_unit(const SweepLaunch& P, uint32_t uni
     const uint32_t local = unit - P.cta_begin[jid];
     const uint32_t inst = local / J.ctas_per_inst;
     const uint32_t r0 = (local - inst * J.ctas_per_inst) * J.rpc;
-    const uint32_t nrep = min(J.rpc, J.R - r0);
+    // variable populations: only the first nlive[inst] slots hold replicas
+    const uint32_t live = J.nlive ? J.nlive[inst] : J.R;
+    if (r0 >= live) return;  // uniform over the CTA, before any barrier
+    const uint32_t nrep = min(J.rpc, live - r0);
     const uint32_t N = J.N, L = J.L, stride_b = padded(N);
     const uint64_t slot0 = (uint64_t)inst * J.R + r0;
     uint8_t* jsm = smem + (uint64_t)J.rpc * stride_b;
@@ -290,12 +293,14 @@ __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ 
         resident_unit<DIM, EA, SWAR, ROWWISE>(P, blockIdx.x);
         return;
     }
-    __shared__ uint32_t s_unit;
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(P.work, 1u);
+    __shared__ uint32_t s_unit[2];
+    for (uint32_t it = 0;; ++it) {
+        // alternate slots: a unit without replicas returns with no barrier, so
+        // the next claim must not overwrite the slot slower threads still read
+        if (threadIdx.x == 0) s_unit[it & 1u] = atomicAdd(P.work, 1u);
         // also orders the previous unit's store loop before the next load
         __syncthreads();
-        const uint32_t u = s_unit;
+        const uint32_t u = s_unit[it & 1u];
         if (u >= P.total) break;
         resident_unit<DIM, EA, SWAR, ROWWISE>(P, u);
     }

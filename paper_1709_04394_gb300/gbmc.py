@@ -25,6 +25,7 @@ GBMC_INT8, GBMC_BITPACK = 0, 1
 GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
 GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
 GBMC_LAUNCH_AUTO, GBMC_LAUNCH_GRID, GBMC_LAUNCH_PERSISTENT = 0, 1, 2
+GBMC_RESAMPLE_MULTINOMIAL, GBMC_RESAMPLE_NEAREST = 0, 1
 
 
 class GbmcError(RuntimeError):
@@ -64,7 +65,7 @@ class PaConfig(C.Structure):
     _fields_ = [("theta", C.c_uint32), ("n_steps", C.c_uint32), ("schedule", C.c_int32), ("init", C.c_int32),
                 ("beta_f", C.c_double), ("betas", C.c_void_p), ("target_overlap", C.c_double),
                 ("dbeta_max", C.c_double), ("mlp_params", C.c_void_p), ("overlap_lo", C.c_double),
-                ("overlap_hi", C.c_double)]
+                ("overlap_hi", C.c_double), ("resample", C.c_int32), ("initial_replicas", C.c_uint32)]
 
 
 class PaStats(C.Structure):
@@ -292,7 +293,8 @@ def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_
 
 
 def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=1.0, betas=None, init=True,
-              target_overlap=0.85, dbeta_max=0.05, mlp_params=None, overlap_lo=0.83, overlap_hi=0.90):
+              target_overlap=0.85, dbeta_max=0.05, mlp_params=None, overlap_lo=0.83, overlap_hi=0.90,
+              resample=GBMC_RESAMPLE_MULTINOMIAL, initial_replicas=0):
     arr = (C.c_void_p * len(lattices))(*[l.value if isinstance(l, C.c_void_p) else l for l in lattices])
     keep = []
     bptr = None
@@ -306,7 +308,7 @@ def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=
         keep.append(m)
         mptr = m.ctypes.data
     cfg = PaConfig(theta, n_steps, schedule, int(bool(init)), beta_f, bptr, target_overlap, dbeta_max, mptr,
-                   overlap_lo, overlap_hi)
+                   overlap_lo, overlap_hi, resample, initial_replicas)
     h = C.c_void_p()
     _check(load().pa_create(ctx, arr, len(lattices), C.byref(cfg), C.byref(h)))
     return h
