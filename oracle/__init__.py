@@ -64,7 +64,7 @@ def _load():
         lib.orc_resample_nearest.argtypes = [u32, p, dbl, u32, u32, u64, u32, u32, p, p]
         lib.orc_resample_nearest.restype = dbl
         lib.orc_pa_run_nearest.argtypes = [i32, i32, p, u64, u32, u32, u32, u32, p, u32, p, i32,
-                                           p, p, p, p, p, p]
+                                           p, p, p, p, p, p, i32]
         lib.orc_pa_run_nearest.restype = i32
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pt_run.argtypes = [i32, i32, p, u64, u32, u32, p, u32, u32, u32, u32, p, p, p, p]
@@ -72,6 +72,10 @@ def _load():
                                    p, p, p, p, p, p, p, p, p, p, p, i32]
         lib.orc_msc_sweeps.argtypes = [i32, i32, p, p, dbl, u64, u32, u32, u32, u32]
         lib.orc_msc_uniforms.argtypes = [u64, u64, u32, u32, i32, u32, p]
+        lib.orc_sw_bond_threshold.argtypes = [dbl]
+        lib.orc_sw_bond_threshold.restype = C.c_int64
+        lib.orc_sw_update.argtypes = [i32, i32, p, dbl, u64, u32, u32, u32, p]
+        lib.orc_sw_bonds.argtypes = [i32, i32, p, dbl, u64, u32, u32, u32, p]
         _lib = lib
         return lib
 
@@ -152,6 +156,31 @@ def msc_sweeps(dim, L, s, J, beta, seed, instance, replica, t0, n):
     _check_spins(s, dim, L)
     Jc = None if J is None else np.ascontiguousarray(J, dtype=np.int8)
     lib.orc_msc_sweeps(dim, L, _ptr(s), _ptr(Jc), float(beta), seed, instance, replica, t0, n)
+
+
+def sw_bond_threshold(beta):
+    """T_bond = ceil((1 - exp(-2 beta)) 2^32) - 1 of the Swendsen-Wang bonds."""
+    return int(_load().orc_sw_bond_threshold(float(beta)))
+
+
+def sw_bonds(dim, L, s, beta, seed, instance, replica, t):
+    """Active flags [N, dim] of the forward bonds in a Swendsen-Wang update."""
+    lib = _load()
+    _check_spins(s, dim, L)
+    a = np.empty(s.size * dim, dtype=np.uint8)
+    lib.orc_sw_bonds(dim, L, _ptr(np.ascontiguousarray(s)), float(beta), seed, instance, replica, t, _ptr(a))
+    return a.reshape(s.size, dim)
+
+
+def sw_update(dim, L, s, beta, seed, instance, replica, t, want_labels=False):
+    """One Swendsen-Wang update (Sec. 3.3; reading R19) of ferromagnet ``s``
+    (int8, in place) with counter t; optionally returns the cluster name
+    (smallest site index) of every site before the flip."""
+    lib = _load()
+    _check_spins(s, dim, L)
+    lab = np.empty(s.size, dtype=np.int32) if want_labels else None
+    lib.orc_sw_update(dim, L, _ptr(s), float(beta), seed, instance, replica, t, _ptr(lab))
+    return lab
 
 
 def dcb_sweeps(L, tile, s, beta, seed, instance, replica, t0, k, n_rounds):
@@ -242,7 +271,7 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_ene
     return out
 
 
-def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None):
+def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None, msc=False):
     """Population annealing with nearest-integer resampling and a variable
     population (at most cap replicas). Returns a dict of per-step arrays
     (lnQ, lnZ, sumE, nrep), the final population (its first nrep[-1] rows)
@@ -260,7 +289,7 @@ def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None):
     E = np.zeros(cap, dtype=np.int64)
     parents = np.zeros(cap, dtype=np.uint32)
     rc = lib.orc_pa_run_nearest(dim, L, _ptr(Jc), seed, instance, R0, cap, S, _ptr(betas), theta, _ptr(spins), 1,
-                                _ptr(lnQ), _ptr(lnZ), _ptr(sumE), _ptr(nrep), _ptr(E), _ptr(parents))
+                                _ptr(lnQ), _ptr(lnZ), _ptr(sumE), _ptr(nrep), _ptr(E), _ptr(parents), int(bool(msc)))
     n = int(nrep[S]) if rc == 0 else 0
     return dict(lnQ=lnQ, lnZ=lnZ, sumE=sumE, nrep=nrep, ok=rc == 0, spins=spins.reshape(cap, N)[:n],
                 E=E[:n], parents=parents[:n], betas=betas)

@@ -45,6 +45,7 @@
  *  R16 double checkerboard: see orc_dcb_sweeps.
  *  R17 nearest-integer resampling, variable population: see
  *      orc_resample_nearest.
+ *  R19 Swendsen-Wang (Sec. 3.3): see orc_sw_update.
  *  R18 multi-spin coding across replicas (Sec. 5.4): replicas 32 w .. 32 w +
  *      31 share, at each site and visit, one Philox word (purpose MSC 5,
  *      counter (k >> 2, t, w, c3), word k & 3) that seeds an LCG; replica
@@ -60,6 +61,8 @@
 #define ORC_PURPOSE_RESAMPLE 2u
 #define ORC_PURPOSE_COUPLING 3u
 #define ORC_PURPOSE_MSC 5u
+#define ORC_PURPOSE_SW_BOND 6u
+#define ORC_PURPOSE_SW_FLIP 7u
 
 /* The linear congruential generator of the multi-spin-coded sweeps (reading
  * R18): x -> a x + c mod 2^32 with the constants of Numerical Recipes. */
@@ -557,11 +560,11 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
  * step i. Per step: lnQ, lnZ, sum E over the population and its size R_i;
  * E_final[cap] / parents_last[cap] for the last step's first R_S slots.
  * Returns 0, or -1 (outputs up to that step valid) if a step would need more
- * than cap replicas or would leave none. */
+ * than cap replicas or would leave none. msc != 0: multi-spin-coded sweeps. */
 int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R0,
                        uint32_t cap, uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                        double *lnQ_out, double *lnZ_out, int64_t *sumE_out, uint32_t *nrep_out,
-                       int64_t *E_final, uint32_t *parents_last)
+                       int64_t *E_final, uint32_t *parents_last, int msc)
 {
     int64_t N = orc_nsites(dim, L);
     int64_t *E = (int64_t *)malloc(sizeof(int64_t) * cap);
@@ -593,9 +596,14 @@ int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t 
             for (uint32_t m = 0; m < R; ++m)
                 memcpy(next + (size_t)m * N, spins + (size_t)parent[m] * N, (size_t)N);
             memcpy(spins, next, (size_t)R * (size_t)N);
-            for (uint32_t r = 0; r < R; ++r)
-                orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
-                           (i - 1) * theta, theta);
+            for (uint32_t r = 0; r < R; ++r) {
+                if (msc)
+                    orc_msc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                                   (i - 1) * theta, theta);
+                else
+                    orc_sweeps(dim, L, spins + (size_t)r * N, J, betas[i], seed, instance, r,
+                               (i - 1) * theta, theta);
+            }
             lnZ += lnQ;
         }
         int64_t sE = 0;
@@ -615,6 +623,86 @@ int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t 
     free(parent);
     free(next);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Swendsen-Wang cluster update of the ferromagnet (Sec. 3.3, its three       */
+/* steps; reading R19).                                                       */
+/*  1. bond b = dim * i + mu (forward bond of site i along axis mu) is active */
+/*     iff s_i = s_j and u <= T_bond, u its Philox word (purpose SW_BOND 6,   */
+/*     counter (b >> 2, t, replica, c3), word b & 3), T_bond =               */
+/*     ceil(p 2^32) - 1 with p = 1 - exp(-2 beta) (so "r < p" as in R2);      */
+/*  2. clusters = connected components of the active bonds, each named by its */
+/*     smallest site index (found here by breadth-first search from the       */
+/*     sites in increasing order);                                            */
+/*  3. a cluster flips iff the top bit of the Philox word of its name r       */
+/*     (purpose SW_FLIP 7, counter (r >> 2, t, replica, c3), word r & 3) is 1.*/
+/* label (may be NULL): [N] the cluster name of every site.                   */
+/* ------------------------------------------------------------------------ */
+int64_t orc_sw_bond_threshold(double beta)
+{
+    double p = 1.0 - exp(-2.0 * beta);
+    return (int64_t)ceil(ldexp(p, 32)) - 1;
+}
+
+/* Step 1: active[dim * i + mu] of every forward bond. */
+void orc_sw_bonds(int dim, int L, const int8_t *s, double beta, uint64_t seed, uint32_t instance,
+                  uint32_t replica, uint32_t t, uint8_t *active)
+{
+    int64_t N = orc_nsites(dim, L);
+    int64_t Tb = orc_sw_bond_threshold(beta);
+    uint32_t cb = orc_c3(ORC_PURPOSE_SW_BOND, 0u, instance);
+    for (int64_t i = 0; i < N; ++i)
+        for (int mu = 0; mu < dim; ++mu) {
+            int Jn;
+            int64_t j = orc_neighbour(dim, L, i, 2 * mu, NULL, &Jn);
+            int64_t b = (int64_t)dim * i + mu;
+            uint32_t u = orc_word(seed, (uint32_t)(b >> 2), t, replica, cb, (unsigned)(b & 3));
+            active[b] = (uint8_t)(s[i] == s[j] && (int64_t)u <= Tb);
+        }
+}
+
+void orc_sw_update(int dim, int L, int8_t *s, double beta, uint64_t seed, uint32_t instance, uint32_t replica,
+                   uint32_t t, int32_t *label)
+{
+    int64_t N = orc_nsites(dim, L);
+    uint8_t *active = (uint8_t *)malloc((size_t)N * (dim == 3 ? 3u : 2u));
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    uint32_t cf = orc_c3(ORC_PURPOSE_SW_FLIP, 0u, instance);
+
+    /* 1. bond variables */
+    orc_sw_bonds(dim, L, s, beta, seed, instance, replica, t, active);
+    /* 2. connected components, named by their smallest site */
+    for (int64_t i = 0; i < N; ++i) lab[i] = -1;
+    for (int64_t root = 0; root < N; ++root) {
+        if (lab[root] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        lab[root] = (int32_t)root;
+        queue[tail++] = root;
+        while (head < tail) {
+            int64_t i = queue[head++];
+            for (int n = 0; n < 2 * dim; ++n) {
+                int Jn;
+                int64_t j = orc_neighbour(dim, L, i, n, NULL, &Jn);
+                int64_t b = (n % 2 == 0) ? (int64_t)dim * i + n / 2 : (int64_t)dim * j + n / 2;
+                if (active[b] && lab[j] < 0) {
+                    lab[j] = (int32_t)root;
+                    queue[tail++] = j;
+                }
+            }
+        }
+    }
+    /* 3. flip every cluster with probability 1/2 */
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t r = lab[i];
+        uint32_t w = orc_word(seed, (uint32_t)(r >> 2), t, replica, cf, (unsigned)(r & 3));
+        if (w >> 31) s[i] = (int8_t)(-s[i]);
+        if (label) label[i] = lab[i];
+    }
+    free(active);
+    free(lab);
+    free(queue);
 }
 
 /* Batch form of the generator for tests: n counters, one key. */
