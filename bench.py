@@ -39,6 +39,9 @@ SM_MAX_MHZ = 2070.0
 # Philox4x32-10 per call: 10 rounds x (2 wide products = 4 32-bit multiply
 # halves + 2 three-way xors = 4 xor ops) = 80 integer ops for 4 sites.
 ALG_INT_OPS_PER_SITE_UPDATE = 20.0
+# Multi-spin-coded sweeps: per replica update one LCG step (multiply, add) and
+# one threshold comparison, plus an 80-op Philox call per 4 sites x 32 replicas.
+ALG_INT_OPS_PER_MSC_UPDATE = 3.0 + 80.0 / 128.0
 
 
 def recorded_traffic(kernel_files, replicas):
@@ -185,12 +188,16 @@ WORKLOADS = {
     "ising2d-L4096-bitpack": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=1),
     # the same lattice by double-checkerboard rounds (Fig. 5 right): 64 x 64 tiles, k = 10 sweeps per tile load
     "ising2d-L4096-dcb": dict(kind="sweeps", dim=2, L=4096, sweeps=1000, beta=0.4406868, layout=0, dcb=(10, 64)),
+    # the same lattice by Swendsen-Wang cluster updates (Sec. 3.3): 100 updates per step at beta_c
+    "ising2d-L4096-sw": dict(kind="sweeps", dim=2, L=4096, sweeps=100, beta=0.4406868, layout=0, sw=True),
     # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
     "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
     # the default workload with nearest-integer resampling and a variable population:
     # R_0 = 10^5, capacity 1.05 10^5 (Sec. 5.4, Eq. (13) with R_{i-1})
     "pa-ising2d-L64-nearest": dict(kind="pa", lattices=[(2, 64, FM, 1, 105000)], S=100, theta=10, beta_f=1.0,
                                    nearest=100000),
+    # the default workload with multi-spin-coded sweeps (32 replicas per word, LCG uniforms)
+    "pa-ising2d-L64-msc": dict(kind="pa", lattices=[(2, 64, FM, 1, 100000)], S=100, theta=10, beta_f=1.0, msc=True),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
     "pa-mixed-2d": dict(kind="pa", lattices=[(2, 32, FM, 1, 100000), (2, 64, FM, 1, 50000),
                                              (2, 128, FM, 1, 20000), (2, 256, FM, 1, 10000)],
@@ -217,6 +224,8 @@ def sweep_lattice(gbmc, ctx, lat, w):
     if "dcb" in w:
         k, tile = w["dcb"]
         gbmc.metropolis_sweeps_dcb(ctx, lat, w["beta"], w["sweeps"] // k, k, tile)
+    elif w.get("sw"):
+        gbmc.swendsen_wang(ctx, lat, w["beta"], w["sweeps"])
     else:
         gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
 
@@ -243,12 +252,14 @@ def run_gpu(args, w, ws, rank, local):
             bufs.append(buf)
             lats.append(gbmc.lattice_init(ctx, dim, L, model=model, n_instances=I, n_replicas=R, seed=seed0,
                                           instance_base=rank_instance_base(rank, i, len(w["lattices"])), spins=buf))
-        if len(lats) == 1:
+        if len(lats) == 1 and not w.get("msc"):
             tuned = gbmc.gbmc_autotune(ctx, lats[0], 0.5 * w["beta_f"], w["theta"])
             result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
                                 "row_walk": tuned.row_walk, "persistent": tuned.persistent,
                                 "candidates": tuned.n_candidates}
         kw = dict(resample=gbmc.GBMC_RESAMPLE_NEAREST, initial_replicas=w["nearest"]) if "nearest" in w else {}
+        if w.get("msc"):
+            kw["sweep_rng"] = gbmc.GBMC_RNG_MSC
         pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True, **kw)
 
         def step(k):
@@ -479,12 +490,20 @@ def cpu_oracle_sample(w):
             upd = int(r["nrep"][1:].sum()) * L ** dim * w["theta"]
             name = "pa_run_nearest"
         else:
-            oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J)
+            oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J, msc=bool(w.get("msc")))
             upd = Rs * L ** dim * w["theta"] * steps
-            name = "pa_run"
+            name = "pa_run (multi-spin-coded random numbers)" if w.get("msc") else "pa_run"
         dt = time.perf_counter() - t0
         desc = "oracle %s: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
                "theta=%d" % (name, dim, L, Rs, w.get("nearest", R), steps, w["S"], w["theta"])
+    elif w.get("sw"):
+        s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
+        t0 = time.perf_counter()
+        for u in range(2):
+            oracle.sw_update(w["dim"], w["L"], s, w["beta"], 1, 0, 0, u)
+        dt = time.perf_counter() - t0
+        upd = w["L"] ** w["dim"] * 2
+        desc = "oracle sw_update: L=%d, 2 of %d updates" % (w["L"], w["sweeps"])
     elif "dcb" in w:
         k, tile = w["dcb"]
         s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
@@ -574,15 +593,21 @@ def main():
     upd_step = res["upd_local"] / args.steps  # this rank's updates per step (variable populations: measured)
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
-    kname = "sweep_resident" if w["kind"] == "pa" else \
-        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else ("sweep_dcb" if "dcb" in w else "sweep_tiles"))
+    kname = ("sweep_msc" if w.get("msc") else "sweep_resident") if w["kind"] == "pa" else \
+        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else
+         ("sweep_dcb" if "dcb" in w else ("swendsen_wang" if w.get("sw") else "sweep_tiles")))
     n_l, t_l = prof.get(kname, (0, 0.0))
+    if w.get("sw"):
+        n_l //= 3  # one update = bond, union and flip launches
     avg_ms = t_l / n_l if n_l else float("nan")
     if w["kind"] == "pa":
         # variable populations: the mean population of the timed runs
         live = [upd_step / (w["S"] * w["theta"] * l[1] ** l[0]) if "nearest" in w else copies(l) for l in w["lattices"]]
         upd_per_launch = sum(n * l[1] ** l[0] for n, l in zip(live, w["lattices"])) * w["theta"]
         hbm_bytes_per_launch = sum(n * (2 * l[1] ** l[0] + 12) for n, l in zip(live, w["lattices"]))
+    elif w.get("sw"):
+        upd_per_launch = w["L"] ** w["dim"]                 # one Swendsen-Wang update (three launches)
+        hbm_bytes_per_launch = w["L"] ** w["dim"] * 13      # spins 1+2, bond flags 1+1, forest 4+4 bytes per site
     elif "dcb" in w:
         k, tile = w["dcb"]
         upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
@@ -593,12 +618,23 @@ def main():
     else:
         upd_per_launch = w["L"] ** w["dim"] * 4            # 4 sweeps per tiled launch
         hbm_bytes_per_launch = w["L"] ** w["dim"] * 2 * (144 * 144) // (128 * 128)  # window in, interior out
-    ops = ALG_INT_OPS_PER_SITE_UPDATE * upd_per_launch
+    alg_ops = ALG_INT_OPS_PER_MSC_UPDATE if w.get("msc") else ALG_INT_OPS_PER_SITE_UPDATE
+    ops = alg_ops * upd_per_launch
     achieved = ops / (avg_ms * 1e-3) / 1e9  # Gop/s
     clk = res["clocks"]
     peak_alu = N_SMS * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e9  # Gop/s: one warp instruction per SMSP per cycle
     hbm_gbs = hbm_bytes_per_launch / (avg_ms * 1e-3) / 1e9
     total_ms = sum(t for _, t in prof.values())
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
+            "frac": achieved / peak_alu,
+            "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction per SMSP "
+                           "per cycle)",
+            "alg_ops_per_site_update": alg_ops}
+    if w.get("sw"):
+        # cluster updates: bytes per update against the measured copy bandwidth
+        roof = {"bound": "hbm", "kernel": kname, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "alg_bytes_per_site_update": 13}
     line = {
         "metric": metric, "value": value, "unit": "spin-flips/ns", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -606,15 +642,11 @@ def main():
         "config": config,
         "replica_sweeps_per_s": (res["upd_all"] / (w["lattices"][0][1] ** w["lattices"][0][0]) / (ms * 1e-3))
         if w["kind"] == "pa" and len(w["lattices"]) == 1 else None,
-        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
-                     "frac": achieved / peak_alu,
+        "roofline": {**roof,
                      "traffic": recorded_traffic(None, copies(w["lattices"][0]))
                      if args.workload == "pa-ising2d-L64" else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                      "scaled by replicas from profiles/sweep_resident_traffic.json)",
-                     "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction "
-                                    "per SMSP per cycle)",
-                     "alg_ops_per_site_update": ALG_INT_OPS_PER_SITE_UPDATE,
                      "avg_launch_ms": avg_ms, "launches": n_l,
                      "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
                      "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,

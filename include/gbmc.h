@@ -196,6 +196,41 @@ gbmc_status metropolis_sweeps(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uin
 gbmc_status metropolis_sweeps_dcb(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_rounds,
                                   uint32_t k, uint32_t tile, int32_t *E_series_dev, int32_t *M_series_dev);
 
+/* Checkerboard sweeps with multi-spin coding across replicas (Sec. 5.4: 32
+ * copies coded together, their random numbers from a linear congruential
+ * generator re-seeded by Philox). Replica slots 32 w .. 32 w + 31 of an
+ * instance form group w; at each site of colour c with colour rank k and
+ * sweep t, the Philox word of counter (k >> 2, t, w, 5 << 28 | c << 27 |
+ * instance), word k & 3, seeds x -> 1664525 x + 1013904223 mod 2^32, and
+ * replica 32 w + b takes the (b + 1)-th output as its uniform u in the
+ * Metropolis rule u <= T(dE) (Eq. (8), as in metropolis_sweeps). The same
+ * Metropolis chain as metropolis_sweeps with other random numbers. Inside the
+ * kernel a site update serves 32 replicas with bitwise neighbour counting.
+ * Requirements (else GBMC_ERR_ARG): 2D ferromagnet, int8 layout, L a multiple
+ * of 16, 9 L^2 / 2 bytes of shared memory per 32 replicas (L <= 208). The
+ * sweep counter advances by n_sweeps. */
+enum { GBMC_RNG_PHILOX = 0, GBMC_RNG_MSC = 1 };
+gbmc_status metropolis_sweeps_msc(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_sweeps);
+
+/* Swendsen-Wang cluster updates of a ferromagnet (Sec. 3.3, its three steps),
+ * every copy in place, update u using counter t = the lattice's sweep counter
+ * + u (which advances by n_updates):
+ *  1. forward bond b = dim i + mu (mu = axis) is active iff s_i = s_j and its
+ *     Philox word (counter (b >> 2, t, replica, 6 << 28 | instance), word
+ *     b & 3) is <= ceil((1 - exp(-2 beta)) 2^32) - 1 ("r < p" of the paper as
+ *     an integer comparison);
+ *  2. clusters = connected components of the active bonds, named by their
+ *     smallest site index (a lock-free union-find on the GPU);
+ *  3. the cluster named r flips iff the top bit of the Philox word of counter
+ *     (r >> 2, t, replica, 7 << 28 | instance), word r & 3, is 1.
+ * E_series_dev / M_series_dev: NULL or device int32 [n_updates][n_copies] (E
+ * and M after each update); labels_dev: NULL or device int32 [n_copies][N],
+ * the cluster name of every site in the last update. A lazily allocated
+ * workspace of 5 bytes per site and copy stays with the lattice. Requirements
+ * (else GBMC_ERR_ARG): ferromagnet (dim 2 or 3), int8 layout. */
+gbmc_status swendsen_wang(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_updates,
+                          int32_t *E_series_dev, int32_t *M_series_dev, int32_t *labels_dev);
+
 /* Energy E = -sum_<ij> J_ij s_i s_j (Eq. (7), forward bonds) and magnetisation
  * M = sum_i s_i of every copy, into device int32 arrays [n_copies]. */
 gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, int32_t *M_dev);
@@ -269,6 +304,9 @@ typedef struct {
     int32_t resample;        /* GBMC_RESAMPLE_MULTINOMIAL (0, constant R) or GBMC_RESAMPLE_NEAREST */
     uint32_t initial_replicas; /* GBMC_RESAMPLE_NEAREST: R_0 (0 = n_replicas); the lattices'
                                   n_replicas is then the capacity of each population */
+    int32_t sweep_rng;       /* GBMC_RNG_PHILOX (0): per-site Philox words (metropolis_sweeps);
+                                GBMC_RNG_MSC: multi-spin-coded sweeps (metropolis_sweeps_msc) */
+    int32_t pad;
 } gbmc_pa_config;
 
 /* Per-population record of one annealing step (after its sweeps). */

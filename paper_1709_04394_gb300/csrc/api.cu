@@ -4,6 +4,7 @@
 // resampling weights of Eq. (13)) and enqueues the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -49,12 +50,12 @@ std::atomic<uint64_t> g_launches{0};
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
-    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_COUNT
+    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
-                                          "bitpack_halfsweep", "sweep_dcb"};
+                                          "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang"};
 
 // Interior size of the tiles of large 2D lattices (window = kTile + 16).
 constexpr uint32_t kTile = 128;
@@ -134,6 +135,8 @@ struct gbmc_lattice {
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
     uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
+    uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags and union-find forest
+    uint32_t* sw_parent;
     uint32_t t;        // sweep counter
     gbmc_pa* run;      // annealing run using this lattice
 };
@@ -183,6 +186,7 @@ struct gbmc_pa {
     uint32_t step = 0;     // steps enqueued
     bool adaptive = false;
     bool nearest = false;  // nearest-integer resampling, variable populations
+    bool msc = false;      // multi-spin-coded sweeps
     uint32_t R0 = 0;       // its initial (and expected) population
     gbmc_pa_stats* stats = nullptr;  // device [S+1][P]
     SchedOut* sched_dev = nullptr;   // [kMaxJobs]
@@ -329,6 +333,36 @@ SweepJob base_job(const gbmc_lattice* l, const Tuning& tu) {
     J.e_lo = -(int32_t)(l->d.dim * l->N);
     J.nbins = (uint32_t)(l->d.dim * l->N / 2 + 1);
     return J;
+}
+
+// Multi-spin-coded sweeps: supported lattices and groups of 32 per CTA (the
+// count that fills the last wave of CTAs best).
+bool msc_ok(const gbmc_lattice* l) {
+    return l->d.dim == 2 && l->d.model == GBMC_ISING_FM && l->d.layout == GBMC_INT8 && l->d.L % 16 == 0 &&
+           msc_smem_bytes((uint32_t)l->N, 1) <= kSmemLimit;
+}
+
+uint32_t msc_groups(const gbmc_ctx* ctx, const gbmc_lattice* l) {
+    const uint64_t groups = (uint64_t)l->d.n_instances * ((l->d.n_replicas + 31) / 32);
+    uint32_t G = msc_pick_groups((uint32_t)l->N, groups, ctx->sm_count);
+    const uint32_t need = (l->d.n_replicas + 31) / 32;
+    return G > need ? need : G;
+}
+
+// One multi-spin-coded sweep launch of P's jobs (their rpc = 32 G).
+gbmc_status launch_msc_jobs(gbmc_ctx* ctx, SweepLaunch& P, uint32_t G) {
+    uint32_t total = 0;
+    for (int j = 0; j < P.njobs; ++j) {
+        P.jobs[j].rpc = 32 * G;
+        P.jobs[j].ctas_per_inst = (P.jobs[j].R + 32 * G - 1) / (32 * G);
+        P.cta_begin[j] = total;
+        total += P.jobs[j].n_inst * P.jobs[j].ctas_per_inst;
+    }
+    P.cta_begin[P.njobs] = total;
+    P.total = total;
+    ProfScope ps_(ctx, PK_SWEEP_MSC);
+    CUDA_TRY(launch_sweep_msc(P, total, G, ctx->stream));
+    return GBMC_OK;
 }
 
 // Enqueues one resident sweep launch of P's jobs. force_persistent: -1 takes
@@ -625,6 +659,8 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->jbits) cudaFree(l->jbits);
     if (l->jsplit) cudaFree(l->jsplit);
     if (l->alt) cudaFree(l->alt);
+    if (l->sw_bonds) cudaFree(l->sw_bonds);
+    if (l->sw_parent) cudaFree(l->sw_parent);
     delete l;
     return GBMC_OK;
 }
@@ -806,6 +842,83 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
     return GBMC_OK;
 }
 
+gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t n_updates, int32_t* E_series,
+                          int32_t* M_series, int32_t* labels) {
+    if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!beta_ok(beta, l->d.dim)) return fail(GBMC_ERR_ARG, "beta must satisfy 0 <= 4*dim*beta <= 700 (got %g)", beta);
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice is owned by an annealing run");
+    if (l->d.model != GBMC_ISING_FM || l->d.layout != GBMC_INT8)
+        return fail(GBMC_ERR_ARG, "Swendsen-Wang updates need a ferromagnet in the int8 layout");
+    if (l->N > 0x7FFFFFFFull) return fail(GBMC_ERR_ARG, "lattice too large for 32-bit cluster names");
+    if (n_updates == 0) return GBMC_OK;
+    if ((uint64_t)l->t + n_updates > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "update counter would wrap");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (!l->sw_bonds) {
+        cudaError_t e = cudaMalloc(&l->sw_bonds, l->N * l->ncopies);
+        if (e == cudaSuccess) e = cudaMalloc(&l->sw_parent, 4 * l->N * l->ncopies);
+        if (e != cudaSuccess) {
+            cudaFree(l->sw_bonds);
+            l->sw_bonds = nullptr;
+            l->sw_parent = nullptr;
+            return fail(GBMC_ERR_OOM, "cudaMalloc(Swendsen-Wang workspace): %s", cudaGetErrorString(e));
+        }
+    }
+    SwLaunch P;
+    std::memset(&P, 0, sizeof(P));
+    P.spins = l->cur;
+    P.bonds = l->sw_bonds;
+    P.parent = l->sw_parent;
+    P.err = ctx->words + 1;
+    P.seed = l->d.seed;
+    // T_bond = ceil(p 2^32) - 1, p = 1 - exp(-2 beta): "r < p" as an integer comparison
+    P.T_bond = (long long)std::ceil(std::ldexp(1.0 - std::exp(-2.0 * beta), 32)) - 1;
+    P.L = (uint32_t)l->d.L;
+    P.N = (uint32_t)l->N;
+    P.dim = (uint32_t)l->d.dim;
+    P.R = l->d.n_replicas;
+    P.inst_base = l->d.instance_base;
+    for (uint32_t u = 0; u < n_updates; ++u) {
+        P.t = l->t + u;
+        P.labels = u + 1 == n_updates ? labels : nullptr;
+        {
+            ProfScope ps_(ctx, PK_SW);
+            CUDA_TRY(launch_sw_update(P, l->ncopies, ctx->stream));
+        }
+        if (E_series || M_series) {
+            ProfScope ps_(ctx, PK_OBS);
+            CUDA_TRY(launch_observables(l->cur, l->jbits, l->d.dim, (uint32_t)l->d.L, l->d.n_instances,
+                                        l->d.n_replicas, E_series ? E_series + (uint64_t)u * l->ncopies : nullptr,
+                                        M_series ? M_series + (uint64_t)u * l->ncopies : nullptr, ctx->stream));
+        }
+    }
+    l->t += n_updates;
+    return GBMC_OK;
+}
+
+gbmc_status metropolis_sweeps_msc(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t n_sweeps) {
+    if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (!beta_ok(beta, l->d.dim)) return fail(GBMC_ERR_ARG, "beta must satisfy 0 <= 4*dim*beta <= 700 (got %g)", beta);
+    if (l->run) return fail(GBMC_ERR_STATE, "lattice is owned by an annealing run");
+    if (!msc_ok(l))
+        return fail(GBMC_ERR_ARG, "multi-spin-coded sweeps need a 2D ferromagnet, int8 layout, L %% 16 == 0, L <= 208");
+    if (n_sweeps == 0) return GBMC_OK;
+    if ((uint64_t)l->t + n_sweeps > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "sweep counter would wrap");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const Tuning tu = tune(l, false);
+    SweepJob J = base_job(l, tu);
+    thresholds(beta, J.thr);
+    J.nsweeps = n_sweeps;
+    SweepLaunch P;
+    std::memset(&P, 0, sizeof(P));
+    P.jobs[0] = J;
+    P.njobs = 1;
+    P.dim = 2;
+    gbmc_status st = launch_msc_jobs(ctx, P, msc_groups(ctx, l));
+    if (st != GBMC_OK) return st;
+    l->t += n_sweeps;
+    return GBMC_OK;
+}
+
 gbmc_status metropolis_sweeps_dcb(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t n_rounds, uint32_t k,
                                   uint32_t tile, int32_t* E_series, int32_t* M_series) {
     if (!ctx || !l) return fail(GBMC_ERR_ARG, "NULL argument");
@@ -959,7 +1072,14 @@ static gbmc_status pa_sweep_launch(gbmc_pa* pa, bool first) {
         }
         P.jobs[P.njobs++] = J;
     }
-    gbmc_status st = launch_jobs(pa->ctx, P, tus);
+    gbmc_status st;
+    if (pa->msc) {
+        uint32_t G = 4;
+        for (auto* pl : act) G = std::min(G, msc_groups(pa->ctx, pl->lat));
+        st = launch_msc_jobs(pa->ctx, P, G);
+    } else {
+        st = launch_jobs(pa->ctx, P, tus);
+    }
     if (st != GBMC_OK) return st;
     if (!first) {
         for (size_t li = 0; li < act.size(); ++li) {
@@ -1034,6 +1154,9 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
         return fail(GBMC_ERR_ARG, "unknown resampling law %d", cfg->resample);
     const bool nearest = cfg->resample == GBMC_RESAMPLE_NEAREST;
     if (nearest && adaptive) return fail(GBMC_ERR_ARG, "nearest-integer resampling needs a fixed schedule");
+    if (cfg->sweep_rng != GBMC_RNG_PHILOX && cfg->sweep_rng != GBMC_RNG_MSC)
+        return fail(GBMC_ERR_ARG, "unknown sweep random-number scheme %d", cfg->sweep_rng);
+    const bool msc = cfg->sweep_rng == GBMC_RNG_MSC;
     if (adaptive) {
         if (!(cfg->beta_f > 0.0) || !(cfg->dbeta_max > 0.0)) return fail(GBMC_ERR_ARG, "adaptive schedules need beta_f > 0 and dbeta_max > 0");
         if (!(cfg->target_overlap > 0.0 && cfg->target_overlap < 1.0)) return fail(GBMC_ERR_ARG, "target_overlap must lie in (0, 1)");
@@ -1052,6 +1175,8 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
             return fail(GBMC_ERR_ARG, "lattices of one run share dim and model");
         if (l->d.layout != GBMC_INT8)
             return fail(GBMC_ERR_ARG, "population annealing runs on the int8 layout (lattice %u is bit-packed)", i);
+        if (msc && !msc_ok(l))
+            return fail(GBMC_ERR_ARG, "multi-spin-coded sweeps need 2D ferromagnets with L %% 16 == 0, L <= 208");
         if (adaptive && l->d.n_instances != 1)
             return fail(GBMC_ERR_ARG, "adaptive schedules anneal one population per lattice (n_instances = 1)");
         if (l->d.n_replicas != l0->d.n_replicas && nearest)
@@ -1082,6 +1207,7 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     pa->S = cfg->n_steps;
     pa->adaptive = adaptive;
     pa->nearest = nearest;
+    pa->msc = msc;
     pa->R0 = cfg->initial_replicas ? cfg->initial_replicas : l0->d.n_replicas;
     pa->lats.resize(n_lattices);
     gbmc_status st = GBMC_OK;

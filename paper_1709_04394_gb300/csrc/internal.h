@@ -105,6 +105,26 @@ cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t 
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);
 
+// Multi-spin-coded sweeps (2D ferromagnet, L % 16 == 0): jobs with rpc = 32 G
+// replicas per CTA; G in 1..4 groups of 32.
+size_t msc_smem_bytes(uint32_t N, uint32_t G);
+uint32_t msc_pick_groups(uint32_t N, uint64_t groups, int sms);
+cudaError_t launch_sweep_msc(const SweepLaunch& P, uint32_t n_ctas, uint32_t G, cudaStream_t s);
+
+// Swendsen-Wang update (Sec. 3.3) of `copies` copies of a ferromagnet, in place.
+struct SwLaunch {
+    int8_t* spins;            // [copies][N]
+    uint8_t* bonds;           // [copies][N] bit mu: forward bond along mu active
+    uint32_t* parent;         // [copies][N] union-find forest
+    int32_t* labels;          // [copies][N] cluster name (smallest site) of every site, or null
+    unsigned int* err;        // raised if a hook loop ran out of its cap
+    uint64_t seed;
+    uint64_t copy0;
+    long long T_bond;         // active iff parallel and u <= T_bond (-1: never)
+    uint32_t L, N, dim, R, inst_base, t;
+};
+cudaError_t launch_sw_update(const SwLaunch& P, uint64_t copies, cudaStream_t s);
+
 // ---- population annealing resampling (Sec. 5.4, Eq. (13)) ----
 struct PaLattice {
     const int32_t* E;         // [n_inst*R] current energies

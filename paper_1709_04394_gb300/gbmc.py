@@ -26,6 +26,7 @@ GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
 GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
 GBMC_LAUNCH_AUTO, GBMC_LAUNCH_GRID, GBMC_LAUNCH_PERSISTENT = 0, 1, 2
 GBMC_RESAMPLE_MULTINOMIAL, GBMC_RESAMPLE_NEAREST = 0, 1
+GBMC_RNG_PHILOX, GBMC_RNG_MSC = 0, 1
 
 
 class GbmcError(RuntimeError):
@@ -65,7 +66,8 @@ class PaConfig(C.Structure):
     _fields_ = [("theta", C.c_uint32), ("n_steps", C.c_uint32), ("schedule", C.c_int32), ("init", C.c_int32),
                 ("beta_f", C.c_double), ("betas", C.c_void_p), ("target_overlap", C.c_double),
                 ("dbeta_max", C.c_double), ("mlp_params", C.c_void_p), ("overlap_lo", C.c_double),
-                ("overlap_hi", C.c_double), ("resample", C.c_int32), ("initial_replicas", C.c_uint32)]
+                ("overlap_hi", C.c_double), ("resample", C.c_int32), ("initial_replicas", C.c_uint32),
+                ("sweep_rng", C.c_int32), ("pad", C.c_int32)]
 
 
 class PaStats(C.Structure):
@@ -117,6 +119,8 @@ def load():
             "lattice_couplings_out": ([p, p, p, C.c_size_t], st),
             "metropolis_sweeps": ([p, p, C.c_double, C.c_uint32, p, p], st),
             "metropolis_sweeps_dcb": ([p, p, C.c_double, C.c_uint32, C.c_uint32, C.c_uint32, p, p], st),
+            "metropolis_sweeps_msc": ([p, p, C.c_double, C.c_uint32], st),
+            "swendsen_wang": ([p, p, C.c_double, C.c_uint32, p, p, p], st),
             "observables": ([p, p, p, p], st),
             "gbmc_autotune": ([p, p, C.c_double, C.c_uint32, C.POINTER(Tuning)], st),
             "gbmc_set_tuning": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(Tuning)], st),
@@ -273,6 +277,14 @@ def metropolis_sweeps_dcb(ctx, lat, beta: float, n_rounds: int, k: int, tile: in
                                         _ptr(M_series)))
 
 
+def metropolis_sweeps_msc(ctx, lat, beta: float, n_sweeps: int):
+    _check(load().metropolis_sweeps_msc(ctx, lat, float(beta), n_sweeps))
+
+
+def swendsen_wang(ctx, lat, beta: float, n_updates: int, E_series=None, M_series=None, labels=None):
+    _check(load().swendsen_wang(ctx, lat, float(beta), n_updates, _ptr(E_series), _ptr(M_series), _ptr(labels)))
+
+
 def observables(ctx, lat, E=None, M=None):
     _check(load().observables(ctx, lat, _ptr(E), _ptr(M)))
 
@@ -294,7 +306,7 @@ def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_
 
 def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=1.0, betas=None, init=True,
               target_overlap=0.85, dbeta_max=0.05, mlp_params=None, overlap_lo=0.83, overlap_hi=0.90,
-              resample=GBMC_RESAMPLE_MULTINOMIAL, initial_replicas=0):
+              resample=GBMC_RESAMPLE_MULTINOMIAL, initial_replicas=0, sweep_rng=GBMC_RNG_PHILOX):
     arr = (C.c_void_p * len(lattices))(*[l.value if isinstance(l, C.c_void_p) else l for l in lattices])
     keep = []
     bptr = None
@@ -308,7 +320,7 @@ def pa_create(ctx, lattices, theta, n_steps, schedule=GBMC_SCHED_LINEAR, beta_f=
         keep.append(m)
         mptr = m.ctypes.data
     cfg = PaConfig(theta, n_steps, schedule, int(bool(init)), beta_f, bptr, target_overlap, dbeta_max, mptr,
-                   overlap_lo, overlap_hi, resample, initial_replicas)
+                   overlap_lo, overlap_hi, resample, initial_replicas, sweep_rng, 0)
     h = C.c_void_p()
     _check(load().pa_create(ctx, arr, len(lattices), C.byref(cfg), C.byref(h)))
     return h

@@ -116,11 +116,13 @@ def test_pa_step_by_step_equals_run(ctx):
     gbmc.lattice_free(l2)
 
 
-def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps, n_samples, seed):
+def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps, n_samples, seed,
+                             sweep_rng=gbmc.GBMC_RNG_PHILOX):
     """Full-size population: exact check of the resampling (oracle on the whole
     energy array) and of theta sweeps on sampled slots, for the first steps."""
     lat = gbmc.lattice_init(ctx, dim, L, model=model, n_instances=I, n_replicas=R, seed=seed)
-    pa = gbmc.pa_create(ctx, [lat], theta, S, beta_f=beta_f)
+    pa = gbmc.pa_create(ctx, [lat], theta, S, beta_f=beta_f, sweep_rng=sweep_rng)
+    sweeps = oracle.msc_sweeps if sweep_rng == gbmc.GBMC_RNG_MSC else oracle.sweeps
     N = L ** dim
     betas = oracle.linear_betas(beta_f, S)
     E = np.empty(I * R, dtype=np.int32)
@@ -146,7 +148,7 @@ def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps
         for _ in range(n_samples):
             i, slot = int(rng.integers(I)), int(rng.integers(R))
             s = prev[i, par[i, slot]].copy()
-            oracle.sweeps(dim, L, s, Js[i], betas[step], seed, i, slot, (step - 1) * theta, theta)
+            sweeps(dim, L, s, Js[i], betas[step], seed, i, slot, (step - 1) * theta, theta)
             np.testing.assert_array_equal(cur[i, slot], s)
             assert E.reshape(I, R)[i, slot] == oracle.observables(dim, L, s, Js[i])[0]
     gbmc.pa_free(pa)
