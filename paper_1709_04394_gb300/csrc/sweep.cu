@@ -289,26 +289,26 @@ __device__ __forceinline__ void resident_unit(const SweepLaunch& P, uint32_t uni
 // (Separate instantiations: the claim loop costs the grid form registers.)
 template <int DIM, bool EA, bool SWAR, bool ROWWISE, bool PERSISTENT>
 __global__ void __launch_bounds__(256) k_sweep_resident(const __grid_constant__ SweepLaunch P) {
-    if (!PERSISTENT) {
+    if constexpr (!PERSISTENT) {
         resident_unit<DIM, EA, SWAR, ROWWISE>(P, blockIdx.x);
-        return;
-    }
-    __shared__ uint32_t s_unit[2];
-    for (uint32_t it = 0;; ++it) {
-        // alternate slots: a unit without replicas returns with no barrier, so
-        // the next claim must not overwrite the slot slower threads still read
-        if (threadIdx.x == 0) s_unit[it & 1u] = atomicAdd(P.work, 1u);
-        // also orders the previous unit's store loop before the next load
-        __syncthreads();
-        const uint32_t u = s_unit[it & 1u];
-        if (u >= P.total) break;
-        resident_unit<DIM, EA, SWAR, ROWWISE>(P, u);
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(P.work + 1, 1u) == gridDim.x - 1) {
-            atomicExch(P.work, 0u);
-            atomicExch(P.work + 1, 0u);
+    } else {
+        __shared__ uint32_t s_unit[2];
+        for (uint32_t it = 0;; ++it) {
+            // alternate slots: a unit without replicas returns with no barrier, so
+            // the next claim must not overwrite the slot slower threads still read
+            if (threadIdx.x == 0) s_unit[it & 1u] = atomicAdd(P.work, 1u);
+            // also orders the previous unit's store loop before the next load
+            __syncthreads();
+            const uint32_t u = s_unit[it & 1u];
+            if (u >= P.total) break;
+            resident_unit<DIM, EA, SWAR, ROWWISE>(P, u);
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(P.work + 1, 1u) == gridDim.x - 1) {
+                atomicExch(P.work, 0u);
+                atomicExch(P.work + 1, 0u);
+            }
         }
     }
 }
