@@ -23,7 +23,7 @@ def lib():
     return gbmc.load()
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_boundary_entry_points():
     names = declared_functions()
     for n in ("lattice_init", "metropolis_sweeps", "observables", "pa_step", "pa_run", "pa_create",
               "gbmc_create", "gbmc_last_error"):
