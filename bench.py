@@ -262,13 +262,16 @@ def run_gpu(args, w, ws, rank, local):
             kw["sweep_rng"] = gbmc.GBMC_RNG_MSC
         pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True, **kw)
 
-        def step(k):
-            gbmc.pa_reset(ctx, pa, True, seed0 + k)
+        def step(k, graph=False):
+            # graph: the whole run replayed as one CUDA graph, captured on first
+            # use; the seed is part of the captured launches, so it stays fixed
+            gbmc.pa_reset(ctx, pa, True, seed0 if graph else seed0 + k)
+            run = gbmc.pa_run_graph if graph else gbmc.pa_run
             if "nearest" not in w:
-                gbmc.pa_run(ctx, pa)
+                run(ctx, pa)
                 return site_updates_per_step(w)
             # variable populations: count the updates the run made (sizes R_1..R_S)
-            stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
+            stats, _ = run(ctx, pa, capacity=w["S"] + 1)
             return sum(int(stats[1:, p]["n_replicas"].sum()) * l[1] ** l[0] * w["theta"]
                        for p, l in enumerate(w["lattices"]))
     else:
@@ -276,12 +279,12 @@ def run_gpu(args, w, ws, rank, local):
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0, layout=w.get("layout", 0))
         lats = [lat]
 
-        def step(k):
+        def step(k, graph=False):
             sweep_lattice(gbmc, ctx, lat, w)
             return site_updates_per_step(w)
 
     for k in range(args.warmup):
-        step(k)
+        step(k, args.graph)
     torch.cuda.synchronize()
 
     def timed(first, profile):
@@ -294,7 +297,8 @@ def run_gpu(args, w, ws, rank, local):
         e0.record(stream)
         upd = 0
         for k in range(args.steps):
-            upd += step(first + k)
+            # the instrumented pass times every launch on the stream path
+            upd += step(first + k, args.graph and not profile)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(dist, ws)
@@ -532,6 +536,9 @@ def main():
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
     ap.add_argument("--workload", default="pa-ising2d-L64", choices=sorted(WORKLOADS) + ["pa-learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="population annealing workloads: replay each timed run as one CUDA graph (fixed "
+                         "seed; per-kernel times still come from the stream path)")
     ap.add_argument("--sweep-launch", default="auto", choices=sorted(SWEEP_LAUNCH),
                     help="resident sweep kernel: one CTA per unit (grid), CTAs claiming units (persistent), "
                          "or the autotuned / batch default (auto)")
@@ -560,7 +567,8 @@ def main():
               "l2_flush": "inputs larger than L2 (2 x 409.6 MB population)" if w["kind"] == "pa"
               else "none: 16 MiB lattice is L2-resident (single-lattice case)",
               "parallelism": "replicas only: independent populations per rank" if ws > 1 else "single GPU",
-              "sweep_launch": args.sweep_launch}
+              "sweep_launch": args.sweep_launch,
+              "cuda_graph": bool(args.graph)}
 
     if args.impl == "reference":
         # the CPU oracle as it stands, on the host cores, bounded sample per step

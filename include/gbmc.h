@@ -23,8 +23,11 @@
  *    t = 0, s = +1 if the word's top bit is 0. Resampling draw k (purpose 2):
  *    q = k>>1, t = annealing step, r = 0, 64-bit value (w[2l+1]<<32)|w[2l],
  *    l = k&1. Couplings (purpose 3): bond b = 3*site + mu, q = b>>2, word b&3,
- *    t = r = 0, J = +1 if the top bit is 0. These numbers depend only on these
- *    indices, never on how the work is spread over the GPU (Sec. 4).
+ *    t = r = 0, J = +1 if the top bit is 0. Parallel-tempering exchanges
+ *    (purpose 4), multi-spin-coded sweeps (purpose 5) and Swendsen-Wang bonds
+ *    and cluster coins (purposes 6 and 7) are defined at their entry points.
+ *    These numbers depend only on these indices, never on how the work is
+ *    spread over the GPU (Sec. 4).
  *  - Metropolis acceptance (Sec. 3.1, Eq. (8)): a site with dE <= 0 flips;
  *    otherwise it flips iff its 32-bit word u satisfies u <= T(dE), with
  *    T(dE) = ceil(exp(-beta dE) * 2^32) - 1 computed in fp64 on the host, i.e.
@@ -116,7 +119,9 @@ typedef struct {
 } gbmc_kernel_time;
 gbmc_status gbmc_profile(gbmc_ctx *ctx, int32_t enable);
 gbmc_status gbmc_profile_read(gbmc_ctx *ctx, gbmc_kernel_time *out, uint32_t capacity, uint32_t *n_out);
-/* Number of kernels this library has enqueued in this process so far. */
+/* Number of kernels this library has enqueued in this process so far (a
+ * replayed CUDA graph of pa_run_graph counts its kernel nodes at each launch,
+ * not when it is captured). */
 uint64_t gbmc_kernel_launches(void);
 
 /* ------------------------------------------------------------------------ */

@@ -199,6 +199,7 @@ struct gbmc_pa {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture_stream = nullptr;  // capture cannot use the legacy default stream
     std::vector<uint64_t> graph_key;
+    uint64_t graph_kernels = 0;             // kernel nodes of the captured run
     std::vector<int8_t*> graph_end_cur;
     std::vector<uint32_t> graph_end_t;
 };
@@ -1624,12 +1625,16 @@ gbmc_status pa_run_graph(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, 
         ctx->fused = false;
         ctx->stream = pa->capture_stream;
         cudaGraph_t g = nullptr;
+        const uint64_t launches0 = g_launches.load();
         cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
         gbmc_status st = GBMC_OK;
         if (ce == cudaSuccess) {
             while (st == GBMC_OK && !pa_finished(pa)) st = pa_enqueue_fixed(pa);
             ce = cudaStreamEndCapture(ctx->stream, &g);
         }
+        // kernels recorded in the graph run only when it is launched: count them then
+        pa->graph_kernels = g_launches.load() - launches0;
+        g_launches.fetch_sub(pa->graph_kernels);
         ctx->stream = user_stream;
         ctx->prof = prof;
         ctx->fused = fused;
@@ -1660,6 +1665,7 @@ gbmc_status pa_run_graph(gbmc_ctx* ctx, gbmc_pa* pa, gbmc_pa_stats* stats_host, 
         pa->graph_key = key;
     }
     CUDA_TRY(cudaGraphLaunch(pa->graph, ctx->stream));
+    g_launches.fetch_add(pa->graph_kernels);
     for (size_t i = 0; i < pa->lats.size(); ++i) {
         pa->lats[i].lat->cur = pa->graph_end_cur[i];
         pa->lats[i].lat->t = pa->graph_end_t[i];

@@ -191,15 +191,20 @@ def test_graph_run_equals_stream_run_and_replays(ctx):
     b = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=12)
     pa_a, ref = _run_gpu(ctx, [a], theta, S)
     pa_b = gbmc.pa_create(ctx, [b], theta, S)
+    incs = []
     for rep in range(3):
         if rep:
             gbmc.pa_reset(ctx, pa_b, True, 0)
+        n0 = gbmc.gbmc_kernel_launches()
         got, n = gbmc.pa_run_graph(ctx, pa_b, capacity=S + 1)
+        incs.append(gbmc.gbmc_kernel_launches() - n0)
         assert n == S
         np.testing.assert_array_equal(got["sumE"], ref["sumE"])
         np.testing.assert_array_equal(got["lnZ"], ref["lnZ"])
         np.testing.assert_array_equal(spins_out(ctx, b), spins_out(ctx, a))
         assert gbmc.lattice_info(b).sweep_counter == gbmc.lattice_info(a).sweep_counter
+    # every replay counts the graph's kernel nodes (resampling phases, sweeps, records), the capture none
+    assert incs[0] == incs[1] == incs[2] >= 3 * S, incs
     with pytest.raises(gbmc.GbmcError):
         gbmc.pa_run_graph(ctx, pa_b)  # not at step 0
     # a new seed is captured anew and matches the oracle
