@@ -64,7 +64,13 @@ def _load():
         lib.orc_resample_nearest.argtypes = [u32, p, dbl, u32, u32, u64, u32, u32, p, p]
         lib.orc_resample_nearest.restype = dbl
         lib.orc_pa_run_nearest.argtypes = [i32, i32, p, u64, u32, u32, u32, u32, p, u32, p, i32,
-                                           p, p, p, p, p, p, i32]
+                                           p, p, p, p, p, p, i32, i32]
+        lib.orc_exp_neg.argtypes = [dbl]
+        lib.orc_exp_neg.restype = dbl
+        lib.orc_poisson.argtypes = [dbl, u64]
+        lib.orc_poisson.restype = u32
+        lib.orc_resample_poisson.argtypes = [u32, p, dbl, u32, u32, u64, u32, u32, p, p]
+        lib.orc_resample_poisson.restype = dbl
         lib.orc_pa_run_nearest.restype = i32
         lib.orc_children_order.argtypes = [u32, p, p]
         lib.orc_pt_run.argtypes = [i32, i32, p, u64, u32, u32, p, u32, u32, u32, u32, p, p, p, p]
@@ -271,7 +277,29 @@ def pa_run(dim, L, seed, instance, R, betas, theta, J=None, spins=None, keep_ene
     return out
 
 
-def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None, msc=False):
+def exp_neg(x):
+    """e^{-x} of reading R20 (IEEE-exact sequence, not libm)."""
+    return float(_load().orc_exp_neg(float(x)))
+
+
+def poisson(tau, U64):
+    """Poisson(tau) count by inversion from the 64-bit uniform U64 (reading R20)."""
+    return int(_load().orc_poisson(float(tau), int(U64)))
+
+
+def resample_poisson(E, dbeta, R0, cap, seed, instance, step):
+    """Poisson resampling counts (variable population), the new population size
+    (None if some tau > 700) and ln Q of one annealing step (reading R20)."""
+    lib = _load()
+    E = np.ascontiguousarray(E, dtype=np.int64)
+    counts = np.empty(E.size, dtype=np.uint32)
+    Rn = np.zeros(1, dtype=np.uint64)
+    lnQ = lib.orc_resample_poisson(E.size, _ptr(E), float(dbeta), R0, cap, seed, instance, step, _ptr(counts),
+                                   _ptr(Rn))
+    return counts, (None if int(Rn[0]) == 2 ** 64 - 1 else int(Rn[0])), lnQ
+
+
+def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None, msc=False, poisson=False):
     """Population annealing with nearest-integer resampling and a variable
     population (at most cap replicas). Returns a dict of per-step arrays
     (lnQ, lnZ, sumE, nrep), the final population (its first nrep[-1] rows)
@@ -289,7 +317,8 @@ def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None, msc=Fa
     E = np.zeros(cap, dtype=np.int64)
     parents = np.zeros(cap, dtype=np.uint32)
     rc = lib.orc_pa_run_nearest(dim, L, _ptr(Jc), seed, instance, R0, cap, S, _ptr(betas), theta, _ptr(spins), 1,
-                                _ptr(lnQ), _ptr(lnZ), _ptr(sumE), _ptr(nrep), _ptr(E), _ptr(parents), int(bool(msc)))
+                                _ptr(lnQ), _ptr(lnZ), _ptr(sumE), _ptr(nrep), _ptr(E), _ptr(parents), int(bool(msc)),
+                                int(bool(poisson)))
     n = int(nrep[S]) if rc == 0 else 0
     return dict(lnQ=lnQ, lnZ=lnZ, sumE=sumE, nrep=nrep, ok=rc == 0, spins=spins.reshape(cap, N)[:n],
                 E=E[:n], parents=parents[:n], betas=betas)

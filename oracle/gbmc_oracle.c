@@ -46,6 +46,7 @@
  *  R17 nearest-integer resampling, variable population: see
  *      orc_resample_nearest.
  *  R19 Swendsen-Wang (Sec. 3.3): see orc_sw_update.
+ *  R20 Poisson resampling: see orc_exp_neg, orc_poisson, orc_resample_poisson.
  *  R18 multi-spin coding across replicas (Sec. 5.4): replicas 32 w .. 32 w +
  *      31 share, at each site and visit, one Philox word (purpose MSC 5,
  *      counter (k >> 2, t, w, c3), word k & 3) that seeds an LCG; replica
@@ -464,6 +465,80 @@ double orc_resample_nearest(uint32_t R_prev, const int64_t *E, double dbeta, uin
     return lnQ;
 }
 
+/* e^{-x} for x >= 0 (reading R20) by Cody and Waite's range reduction,
+ * x = k ln2 + r with k = floor(x / ln2 + 1/2), |r| <= ln2 / 2, ln2 split into
+ * a head with a 32-bit mantissa (so k * head is exact) and the remainder, then
+ * e^{-r} from its Taylor series to degree 20 by Horner's rule, s <- 1 - (r/n) s
+ * for n = 20 .. 1, and an exact scaling by 2^-k. Every step is one IEEE fp64
+ * operation (this file is compiled without contraction), so any IEEE machine
+ * computes the same bits. x > 700 gives 0. */
+#define ORC_LN2_HI 0.693147180559890330187045037746429443359375
+#define ORC_LN2_LO 5.4979230187083711552420206887059365096458314e-14
+double orc_exp_neg(double x)
+{
+    if (x > 700.0) return 0.0;
+    double k = floor(x / 0.6931471805599453094172321 + 0.5);
+    double r = (x - k * ORC_LN2_HI) - k * ORC_LN2_LO;
+    double s = 1.0;
+    for (int n = 20; n >= 1; --n) s = 1.0 - (r / (double)n) * s;
+    return ldexp(s, -(int)k);
+}
+
+/* Poisson(tau) count by inversion (reading R20): u = the top 53 bits of U64
+ * as a fraction; n is the least count with u < F(n), the cumulative Poisson
+ * probabilities built term by term (p_0 = e^{-tau}, p_n = p_{n-1} (tau / n));
+ * past the mode, a term too small to change F ends the search (u within
+ * rounding of 1). Returns UINT32_MAX if tau > 700 (e^{-tau} underflows). */
+uint32_t orc_poisson(double tau, uint64_t U64)
+{
+    if (tau > 700.0) return UINT32_MAX;
+    double u = (double)(U64 >> 11) * 0x1.0p-53;
+    double p = orc_exp_neg(tau), F = p;
+    uint32_t n = 0;
+    while (u >= F && n < 100000u) {
+        n += 1;
+        p = p * (tau / (double)n);
+        double Fn = F + p;
+        if (Fn == F && (double)n > tau) break; /* the sum has saturated below u */
+        F = Fn;
+    }
+    return n;
+}
+
+/* Sec. 5.4 step 2 with Poisson resampling and a variable population (reading
+ * R20): replica j gets Poisson(tau_j) copies, tau_j = R0 W_j / C as in
+ * orc_resample_nearest (in fp64: the rounded products R0 W_j and sums C);
+ * the count's uniform is replica j's resampling word. Returns ln Q_i; -1 in
+ * *R_new's place (UINT64_MAX) if some tau_j > 700. */
+double orc_resample_poisson(uint32_t R_prev, const int64_t *E, double dbeta, uint32_t R0, uint32_t cap,
+                            uint64_t seed, uint32_t instance, uint32_t step, uint32_t *counts, uint64_t *R_new)
+{
+    int64_t Emin;
+    double lnQ = orc_lnQ(R_prev, E, dbeta, &Emin);
+    int s = 63 - orc_ceil_log2(cap);
+    uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * R_prev);
+    uint64_t C = 0;
+    for (uint32_t j = 0; j < R_prev; ++j) {
+        W[j] = (uint64_t)floor(ldexp(exp(-(dbeta * (double)(E[j] - Emin))), s));
+        C += W[j];
+    }
+    uint64_t total = 0;
+    int bad = 0;
+    for (uint32_t j = 0; j < R_prev; ++j) {
+        double tau = (double)((uint64_t)R0 * W[j]) / (double)C;
+        uint32_t n = orc_poisson(tau, orc_resample_u64(seed, instance, step, j));
+        if (n == UINT32_MAX) {
+            bad = 1;
+            n = 0;
+        }
+        counts[j] = n;
+        total += n;
+    }
+    free(W);
+    *R_new = bad ? UINT64_MAX : total;
+    return lnQ;
+}
+
 /* Children of parent j occupy consecutive slots, parents in increasing order. */
 void orc_children_order(uint32_t R, const uint32_t *counts, uint32_t *parent_of_slot)
 {
@@ -560,11 +635,12 @@ void orc_pa_run(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instanc
  * step i. Per step: lnQ, lnZ, sum E over the population and its size R_i;
  * E_final[cap] / parents_last[cap] for the last step's first R_S slots.
  * Returns 0, or -1 (outputs up to that step valid) if a step would need more
- * than cap replicas or would leave none. msc != 0: multi-spin-coded sweeps. */
+ * than cap replicas or would leave none. msc != 0: multi-spin-coded sweeps;
+ * poisson != 0: Poisson instead of nearest-integer counts (reading R20). */
 int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t instance, uint32_t R0,
                        uint32_t cap, uint32_t S, const double *betas, uint32_t theta, int8_t *spins, int init,
                        double *lnQ_out, double *lnZ_out, int64_t *sumE_out, uint32_t *nrep_out,
-                       int64_t *E_final, uint32_t *parents_last, int msc)
+                       int64_t *E_final, uint32_t *parents_last, int msc, int poisson)
 {
     int64_t N = orc_nsites(dim, L);
     int64_t *E = (int64_t *)malloc(sizeof(int64_t) * cap);
@@ -585,7 +661,8 @@ int orc_pa_run_nearest(int dim, int L, const int8_t *J, uint64_t seed, uint32_t 
         if (i > 0) {
             double dbeta = betas[i] - betas[i - 1];
             uint64_t Rn;
-            lnQ = orc_resample_nearest(R, E, dbeta, R0, cap, seed, instance, i, counts, &Rn);
+            lnQ = poisson ? orc_resample_poisson(R, E, dbeta, R0, cap, seed, instance, i, counts, &Rn)
+                          : orc_resample_nearest(R, E, dbeta, R0, cap, seed, instance, i, counts, &Rn);
             if (Rn > cap || Rn == 0) {  /* outgrown the capacity, or died out */
                 rc = -1;
                 break;
