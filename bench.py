@@ -196,6 +196,9 @@ WORKLOADS = {
     # R_0 = 10^5, capacity 1.05 10^5 (Sec. 5.4, Eq. (13) with R_{i-1})
     "pa-ising2d-L64-nearest": dict(kind="pa", lattices=[(2, 64, FM, 1, 105000)], S=100, theta=10, beta_f=1.0,
                                    nearest=100000),
+    # the same with Poisson resampling
+    "pa-ising2d-L64-poisson": dict(kind="pa", lattices=[(2, 64, FM, 1, 105000)], S=100, theta=10, beta_f=1.0,
+                                   nearest=100000, poisson=True),
     # the default workload with multi-spin-coded sweeps (32 replicas per word, LCG uniforms)
     "pa-ising2d-L64-msc": dict(kind="pa", lattices=[(2, 64, FM, 1, 100000)], S=100, theta=10, beta_f=1.0, msc=True),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
@@ -257,7 +260,8 @@ def run_gpu(args, w, ws, rank, local):
             result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
                                 "row_walk": tuned.row_walk, "persistent": tuned.persistent,
                                 "candidates": tuned.n_candidates}
-        kw = dict(resample=gbmc.GBMC_RESAMPLE_NEAREST, initial_replicas=w["nearest"]) if "nearest" in w else {}
+        law = gbmc.GBMC_RESAMPLE_POISSON if w.get("poisson") else gbmc.GBMC_RESAMPLE_NEAREST
+        kw = dict(resample=law, initial_replicas=w["nearest"]) if "nearest" in w else {}
         if w.get("msc"):
             kw["sweep_rng"] = gbmc.GBMC_RNG_MSC
         pa = gbmc.pa_create(ctx, lats, w["theta"], w["S"], beta_f=w["beta_f"], init=True, **kw)
@@ -490,9 +494,10 @@ def cpu_oracle_sample(w):
         t0 = time.perf_counter()
         if "nearest" in w:
             Rs = min(Rs, w["nearest"])
-            r = oracle.pa_run_nearest(dim, L, 1, 0, Rs, Rs + Rs // 10 + 16, betas, w["theta"], J=J)
+            r = oracle.pa_run_nearest(dim, L, 1, 0, Rs, Rs + Rs // 10 + 16, betas, w["theta"], J=J,
+                                      poisson=bool(w.get("poisson")))
             upd = int(r["nrep"][1:].sum()) * L ** dim * w["theta"]
-            name = "pa_run_nearest"
+            name = "pa_run_nearest (Poisson counts)" if w.get("poisson") else "pa_run_nearest"
         else:
             oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J, msc=bool(w.get("msc")))
             upd = Rs * L ** dim * w["theta"] * steps

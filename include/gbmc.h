@@ -283,8 +283,18 @@ gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tu
  *    would need more slots than the capacity keeps the first `capacity`
  *    children, and the next gbmc_sync / pa_step / pa_run returns
  *    GBMC_ERR_STATE (the run is then invalid); so does a step that leaves a
- *    population empty. Fixed schedules only. */
-enum { GBMC_RESAMPLE_MULTINOMIAL = 0, GBMC_RESAMPLE_NEAREST = 1 };
+ *    population empty. Fixed schedules only.
+ *  POISSON: as NEAREST, but replica j gets Poisson(tau_j) copies, tau_j =
+ *    double(R_0 W_j) / double(C) (correctly rounded fp64), drawn by inversion
+ *    from u = the top 53 bits of U64_j: the least n with u < F(n), F summed
+ *    term by term from p_0 = e^{-tau} with p_n = p_{n-1} (tau / n), stopping
+ *    early once past the mode a term no longer changes F. e^{-tau} comes from
+ *    a fixed sequence of correctly rounded operations (Cody-Waite reduction
+ *    by ln2, Taylor series to degree 20), not from a math library, so the
+ *    counts are reproducible on any IEEE machine. A mean tau_j > 500 is drawn
+ *    as the sum of m = ceil(tau_j / 500) Poisson(tau_j / m) counts, piece p
+ *    from the resampling word of replica j with counter field r = p. */
+enum { GBMC_RESAMPLE_MULTINOMIAL = 0, GBMC_RESAMPLE_NEAREST = 1, GBMC_RESAMPLE_POISSON = 2 };
 
 enum {
     GBMC_SCHED_LINEAR = 0,    /* beta_i = (beta_f * i) / n_steps, i = 0..n_steps */
@@ -306,8 +316,8 @@ typedef struct {
     const float *mlp_params; /* GBMC_SCHED_MLP: host fp32 parameters, gbmc_mlp_param_count() */
     double overlap_lo;       /* GBMC_SCHED_MLP: accept a proposal if lo <= overlap <= hi */
     double overlap_hi;
-    int32_t resample;        /* GBMC_RESAMPLE_MULTINOMIAL (0, constant R) or GBMC_RESAMPLE_NEAREST */
-    uint32_t initial_replicas; /* GBMC_RESAMPLE_NEAREST: R_0 (0 = n_replicas); the lattices'
+    int32_t resample;        /* GBMC_RESAMPLE_MULTINOMIAL (0, constant R), _NEAREST or _POISSON */
+    uint32_t initial_replicas; /* NEAREST / POISSON: R_0 (0 = n_replicas); the lattices'
                                   n_replicas is then the capacity of each population */
     int32_t sweep_rng;       /* GBMC_RNG_PHILOX (0): per-site Philox words (metropolis_sweeps);
                                 GBMC_RNG_MSC: multi-spin-coded sweeps (metropolis_sweeps_msc) */

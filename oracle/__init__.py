@@ -289,14 +289,14 @@ def poisson(tau, U64):
 
 def resample_poisson(E, dbeta, R0, cap, seed, instance, step):
     """Poisson resampling counts (variable population), the new population size
-    (None if some tau > 700) and ln Q of one annealing step (reading R20)."""
+    and ln Q of one annealing step (reading R20)."""
     lib = _load()
     E = np.ascontiguousarray(E, dtype=np.int64)
     counts = np.empty(E.size, dtype=np.uint32)
     Rn = np.zeros(1, dtype=np.uint64)
     lnQ = lib.orc_resample_poisson(E.size, _ptr(E), float(dbeta), R0, cap, seed, instance, step, _ptr(counts),
                                    _ptr(Rn))
-    return counts, (None if int(Rn[0]) == 2 ** 64 - 1 else int(Rn[0])), lnQ
+    return counts, int(Rn[0]), lnQ
 
 
 def pa_run_nearest(dim, L, seed, instance, R0, cap, betas, theta, J=None, msc=False, poisson=False):

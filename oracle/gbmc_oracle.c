@@ -467,7 +467,8 @@ double orc_resample_nearest(uint32_t R_prev, const int64_t *E, double dbeta, uin
 
 /* e^{-x} for x >= 0 (reading R20) by Cody and Waite's range reduction,
  * x = k ln2 + r with k = floor(x / ln2 + 1/2), |r| <= ln2 / 2, ln2 split into
- * a head with a 32-bit mantissa (so k * head is exact) and the remainder, then
+ * a head whose last 11 mantissa bits are zero (so k * head is exact for the
+ * k < 2^11 that occur) and the remainder, then
  * e^{-r} from its Taylor series to degree 20 by Horner's rule, s <- 1 - (r/n) s
  * for n = 20 .. 1, and an exact scaling by 2^-k. Every step is one IEEE fp64
  * operation (this file is compiled without contraction), so any IEEE machine
@@ -505,11 +506,31 @@ uint32_t orc_poisson(double tau, uint64_t U64)
     return n;
 }
 
+/* The Poisson(tau) copies of replica j (reading R20): tau <= 500 from its
+ * resampling word; a larger tau as the sum of m = ceil(tau / 500) independent
+ * Poisson(tau / m) counts, piece p drawn from the resampling word of the same
+ * replica with counter field r = p (the plain word is p = 0). */
+static uint32_t orc_poisson_copies(double tau, uint64_t seed, uint32_t instance, uint32_t step, uint32_t j)
+{
+    if (tau <= 500.0) return orc_poisson(tau, orc_resample_u64(seed, instance, step, j));
+    uint32_t m = (uint32_t)ceil(tau / 500.0);
+    double part = tau / (double)m;
+    uint32_t n = 0;
+    for (uint32_t p = 0; p < m; ++p) {
+        uint32_t ctr[4] = {j >> 1, step, p, orc_c3(ORC_PURPOSE_RESAMPLE, 0u, instance)};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t out[4];
+        orc_philox4x32_10(ctr, key, out);
+        unsigned l = j & 1u;
+        n += orc_poisson(part, ((uint64_t)out[2 * l + 1] << 32) | (uint64_t)out[2 * l]);
+    }
+    return n;
+}
+
 /* Sec. 5.4 step 2 with Poisson resampling and a variable population (reading
  * R20): replica j gets Poisson(tau_j) copies, tau_j = R0 W_j / C as in
- * orc_resample_nearest (in fp64: the rounded products R0 W_j and sums C);
- * the count's uniform is replica j's resampling word. Returns ln Q_i; -1 in
- * *R_new's place (UINT64_MAX) if some tau_j > 700. */
+ * orc_resample_nearest (in fp64: the rounded product R0 W_j and sum C).
+ * Returns ln Q_i. */
 double orc_resample_poisson(uint32_t R_prev, const int64_t *E, double dbeta, uint32_t R0, uint32_t cap,
                             uint64_t seed, uint32_t instance, uint32_t step, uint32_t *counts, uint64_t *R_new)
 {
@@ -523,19 +544,13 @@ double orc_resample_poisson(uint32_t R_prev, const int64_t *E, double dbeta, uin
         C += W[j];
     }
     uint64_t total = 0;
-    int bad = 0;
     for (uint32_t j = 0; j < R_prev; ++j) {
         double tau = (double)((uint64_t)R0 * W[j]) / (double)C;
-        uint32_t n = orc_poisson(tau, orc_resample_u64(seed, instance, step, j));
-        if (n == UINT32_MAX) {
-            bad = 1;
-            n = 0;
-        }
-        counts[j] = n;
-        total += n;
+        counts[j] = orc_poisson_copies(tau, seed, instance, step, j);
+        total += counts[j];
     }
     free(W);
-    *R_new = bad ? UINT64_MAX : total;
+    *R_new = total;
     return lnQ;
 }
 

@@ -185,7 +185,8 @@ struct gbmc_pa {
     uint32_t S = 0;        // steps of a fixed schedule; step cap of an adaptive one
     uint32_t step = 0;     // steps enqueued
     bool adaptive = false;
-    bool nearest = false;  // nearest-integer resampling, variable populations
+    bool nearest = false;  // nearest-integer or Poisson resampling, variable populations
+    bool poisson = false;  // Poisson counts
     bool msc = false;      // multi-spin-coded sweeps
     uint32_t R0 = 0;       // its initial (and expected) population
     gbmc_pa_stats* stats = nullptr;  // device [S+1][P]
@@ -1023,7 +1024,7 @@ static PaLattice pa_params(gbmc_pa* pa, PaLat& pl, uint32_t step) {
         P.nprev = step == 0 ? nullptr : pl.nrep + (uint64_t)((step - 1) & 1u) * I;
         P.overflow = pa->ctx->words + 4;
         P.R0 = pa->R0;
-        P.nearest = 1;
+        P.nearest = pa->poisson ? 2 : 1;
     }
     return P;
 }
@@ -1151,10 +1152,12 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     if (cfg->theta == 0) return fail(GBMC_ERR_ARG, "theta must be >= 1");
     if (sched == GBMC_SCHED_LIST && !cfg->betas) return fail(GBMC_ERR_ARG, "betas required for a list schedule");
     if (sched == GBMC_SCHED_MLP && !cfg->mlp_params) return fail(GBMC_ERR_ARG, "mlp_params required for the MLP schedule");
-    if (cfg->resample != GBMC_RESAMPLE_MULTINOMIAL && cfg->resample != GBMC_RESAMPLE_NEAREST)
+    if (cfg->resample != GBMC_RESAMPLE_MULTINOMIAL && cfg->resample != GBMC_RESAMPLE_NEAREST &&
+        cfg->resample != GBMC_RESAMPLE_POISSON)
         return fail(GBMC_ERR_ARG, "unknown resampling law %d", cfg->resample);
-    const bool nearest = cfg->resample == GBMC_RESAMPLE_NEAREST;
-    if (nearest && adaptive) return fail(GBMC_ERR_ARG, "nearest-integer resampling needs a fixed schedule");
+    // both variable-population laws share the live-slot machinery
+    const bool nearest = cfg->resample != GBMC_RESAMPLE_MULTINOMIAL;
+    if (nearest && adaptive) return fail(GBMC_ERR_ARG, "variable-population resampling needs a fixed schedule");
     if (cfg->sweep_rng != GBMC_RNG_PHILOX && cfg->sweep_rng != GBMC_RNG_MSC)
         return fail(GBMC_ERR_ARG, "unknown sweep random-number scheme %d", cfg->sweep_rng);
     const bool msc = cfg->sweep_rng == GBMC_RNG_MSC;
@@ -1208,6 +1211,7 @@ gbmc_status pa_create(gbmc_ctx* ctx, gbmc_lattice* const* lattices, uint32_t n_l
     pa->S = cfg->n_steps;
     pa->adaptive = adaptive;
     pa->nearest = nearest;
+    pa->poisson = cfg->resample == GBMC_RESAMPLE_POISSON;
     pa->msc = msc;
     pa->R0 = cfg->initial_replicas ? cfg->initial_replicas : l0->d.n_replicas;
     pa->lats.resize(n_lattices);

@@ -153,7 +153,7 @@ struct PaLattice {
     uint32_t* nnext;          // [n_inst] R_i (written by the placement), or null
     unsigned int* overflow;   // raised when children exceed the capacity
     uint32_t R0;              // target population
-    int32_t nearest;          // 1: nearest-integer law instead of multinomial draws
+    int32_t nearest;          // 1: nearest-integer law, 2: Poisson law (instead of multinomial draws)
 };
 
 constexpr uint32_t kScanChunk = 2048;  // replicas per resampling chunk (512 threads x 4)

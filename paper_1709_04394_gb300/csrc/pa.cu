@@ -39,10 +39,12 @@ __device__ __forceinline__ uint32_t live_prev(const PaLattice& P, uint32_t inst)
     return P.nprev ? __ldcg(P.nprev + inst) : P.R;
 }
 
-// 64-bit uniform of resampling draw (or replica) k of population `inst`.
-__device__ __forceinline__ unsigned long long resample_u64(const PaLattice& P, uint32_t inst, uint32_t k) {
+// 64-bit uniform of resampling draw (or replica) k of population `inst`;
+// r > 0: the extra pieces of a large Poisson mean.
+__device__ __forceinline__ unsigned long long resample_u64(const PaLattice& P, uint32_t inst, uint32_t k,
+                                                           uint32_t r = 0u) {
     const uint4 w = philox4x32_10(
-        make_uint4(k >> 1, P.step, 0u, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
+        make_uint4(k >> 1, P.step, r, c3_word(kPurposeResample, 0u, P.inst_base + inst)),
         (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     return (k & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
 }
@@ -169,6 +171,63 @@ __device__ __forceinline__ void phase_nearest(const PaLattice& P, uint64_t g) {
     P.counts[base + j] = (uint32_t)n0 + (x < rem ? 1u : 0u);
 }
 
+// e^{-x}, x >= 0, in a fixed sequence of correctly rounded fp64 operations
+// (so host and device agree bit for bit): Cody and Waite's reduction x = k ln2
+// + r, |r| <= ln2/2, with ln2 = head + tail (the head's last 11 mantissa bits
+// zero, so k * head is exact), e^{-r} by Horner's rule on its Taylor series to
+// degree 20 (s <- 1 - (r/n) s, n = 20..1), then exact scaling by 2^-k; 0 for
+// x > 700.
+__device__ __forceinline__ double exp_neg_ieee(double x) {
+    if (x > 700.0) return 0.0;
+    const double k = floor(__dadd_rn(__ddiv_rn(x, 0.6931471805599453094172321), 0.5));
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, 0.693147180559890330187045037746429443359375)),
+                               __dmul_rn(k, 5.4979230187083711552420206887059365096458314e-14));
+    double s = 1.0;
+#pragma unroll 1
+    for (int n = 20; n >= 1; --n) s = __dsub_rn(1.0, __dmul_rn(__ddiv_rn(r, (double)n), s));
+    return ldexp(s, -(int)k);
+}
+
+// Poisson(tau) copies by inversion from the 64-bit uniform U: the least n with
+// u < F(n), u = the top 53 bits of U as a fraction, F built term by term; a
+// term that no longer changes F past the mode ends the search (tau <= 500
+// here, so e^{-tau} is a normal number).
+__device__ __forceinline__ uint32_t poisson_count(double tau, unsigned long long U) {
+    if (tau > 700.0) return 0xFFFFFFFFu;
+    const double u = __dmul_rn(__ull2double_rn(U >> 11), 1.1102230246251565404236316680908203125e-16);
+    double p = exp_neg_ieee(tau), F = p;
+    uint32_t n = 0;
+    while (u >= F && n < 100000u) {
+        n += 1;
+        p = __dmul_rn(p, __ddiv_rn(tau, (double)n));
+        const double Fn = __dadd_rn(F, p);
+        if (Fn == F && (double)n > tau) break;
+        F = Fn;
+    }
+    return n;
+}
+
+// Poisson copies of replica g: Poisson(tau_j), tau_j = R0 W_j / C in fp64; a
+// mean above 500 as the sum of m = ceil(tau / 500) Poisson(tau / m) pieces,
+// piece p from the replica's resampling word with counter field r = p.
+__device__ __forceinline__ void phase_poisson(const PaLattice& P, uint64_t g) {
+    const uint32_t inst = (uint32_t)(g / P.R), j = (uint32_t)(g - (uint64_t)inst * P.R);
+    if (j >= live_prev(P, inst)) return;
+    const uint64_t base = (uint64_t)inst * P.R;
+    const unsigned long long W = __ldcg(P.cloc + base + j) - ((j % kScanChunk) ? __ldcg(P.cloc + base + j - 1) : 0ull);
+    const unsigned long long C = __ldcg(P.cpre + (uint64_t)inst * (P.nchunks + 1) + P.nchunks);
+    const double tau = __ddiv_rn(__ull2double_rn((unsigned long long)P.R0 * W), __ull2double_rn(C));
+    uint32_t n = 0;
+    if (tau <= 500.0) {
+        n = poisson_count(tau, resample_u64(P, inst, j));
+    } else {
+        const uint32_t m = (uint32_t)ceil(__ddiv_rn(tau, 500.0));
+        const double part = __ddiv_rn(tau, (double)m);
+        for (uint32_t p = 0; p < m; ++p) n += poisson_count(part, resample_u64(P, inst, j, p));
+    }
+    P.counts[base + j] = n;
+}
+
 // Exclusive scan of the counts within one chunk, chunk total.
 __device__ __forceinline__ void phase_count_scan(const PaLattice& P, uint32_t inst, uint32_t chunk, uint32_t* sh) {
     const uint64_t base = (uint64_t)inst * P.R;
@@ -279,7 +338,8 @@ cudaError_t launch_pa_draws(const PaLattice& P, cudaStream_t s) {
 __global__ void __launch_bounds__(256) k_pa_nearest(const __grid_constant__ PaLattice P) {
     const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (g >= (uint64_t)P.n_inst * P.R) return;
-    phase_nearest(P, g);
+    if (P.nearest == 2) phase_poisson(P, g);
+    else phase_nearest(P, g);
 }
 
 cudaError_t launch_pa_nearest(const PaLattice& P, cudaStream_t s) {
@@ -355,7 +415,8 @@ __global__ void __launch_bounds__(kScanThreads) k_pa_resample_fused(const __grid
     if (!grid_barrier(B, target)) return;
     const uint64_t total = (uint64_t)P.n_inst * P.R;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
-        if (P.nearest) phase_nearest(P, g);
+        if (P.nearest == 2) phase_poisson(P, g);
+        else if (P.nearest) phase_nearest(P, g);
         else phase_draw(P, g);
     }
     if (!grid_barrier(B, target)) return;

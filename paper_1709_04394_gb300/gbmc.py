@@ -25,7 +25,7 @@ GBMC_INT8, GBMC_BITPACK = 0, 1
 GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
 GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
 GBMC_LAUNCH_AUTO, GBMC_LAUNCH_GRID, GBMC_LAUNCH_PERSISTENT = 0, 1, 2
-GBMC_RESAMPLE_MULTINOMIAL, GBMC_RESAMPLE_NEAREST = 0, 1
+GBMC_RESAMPLE_MULTINOMIAL, GBMC_RESAMPLE_NEAREST, GBMC_RESAMPLE_POISSON = 0, 1, 2
 GBMC_RNG_PHILOX, GBMC_RNG_MSC = 0, 1
 
 

@@ -1,6 +1,6 @@
-"""GPU parity: population annealing with nearest-integer resampling and a
-variable population size (Sec. 5.4, Eq. (13) with R_{i-1}) against the CPU
-oracle. Population sizes, exact energy sums, the live spins, energies and
+"""GPU parity: population annealing with nearest-integer or Poisson
+resampling and a variable population size (Sec. 5.4, Eq. (13) with R_{i-1})
+against the CPU oracle. Population sizes, exact energy sums, the live spins, energies and
 parents are compared bit for bit; ln Q and ln Z to a relative 1e-12."""
 import math
 
@@ -15,6 +15,8 @@ pytestmark = pytest.mark.gpu
 
 RTOL = 1e-12
 NEAREST = gbmc.GBMC_RESAMPLE_NEAREST
+POISSON = gbmc.GBMC_RESAMPLE_POISSON
+LAWS = [NEAREST, POISSON]
 
 
 def _compare(stats, ref, pop, N):
@@ -37,14 +39,15 @@ def _live_state(ctx, pa, lat, li, n_inst, cap, nrep):
     return [(sp[i, :nrep[i]], E[i, :nrep[i]], par[i, :nrep[i]]) for i in range(n_inst)]
 
 
-@pytest.mark.parametrize("L,R0,cap,S,theta", [(16, 600, 700, 6, 2), (8, 50, 80, 8, 3), (32, 2100, 2300, 4, 2)])
-def test_pa_nearest_2d_matches_oracle(ctx, L, R0, cap, S, theta):
+@pytest.mark.parametrize("law", LAWS)
+@pytest.mark.parametrize("L,R0,cap,S,theta", [(16, 600, 800, 6, 2), (8, 50, 100, 8, 3), (32, 2100, 2500, 4, 2)])
+def test_pa_nearest_2d_matches_oracle(ctx, law, L, R0, cap, S, theta):
     seed = 21 + L
     lat = gbmc.lattice_init(ctx, 2, L, n_replicas=cap, seed=seed)
-    pa = gbmc.pa_create(ctx, [lat], theta, S, resample=NEAREST, initial_replicas=R0)
+    pa = gbmc.pa_create(ctx, [lat], theta, S, resample=law, initial_replicas=R0)
     stats, n = gbmc.pa_run(ctx, pa, capacity=S + 1)
     assert n == S
-    ref = oracle.pa_run_nearest(2, L, seed, 0, R0, cap, oracle.linear_betas(1.0, S), theta)
+    ref = oracle.pa_run_nearest(2, L, seed, 0, R0, cap, oracle.linear_betas(1.0, S), theta, poisson=law == POISSON)
     assert ref["ok"]
     _compare(stats, ref, 0, L * L)
     (sp, E, par), = _live_state(ctx, pa, lat, 0, 1, cap, [ref["nrep"][-1]])
@@ -55,23 +58,24 @@ def test_pa_nearest_2d_matches_oracle(ctx, L, R0, cap, S, theta):
     gbmc.lattice_free(lat)
 
 
+@pytest.mark.parametrize("law", LAWS)
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("mode", [gbmc.GBMC_LAUNCH_GRID, gbmc.GBMC_LAUNCH_PERSISTENT])
-def test_pa_nearest_3d_ea_instances_and_launch_forms(ctx, fused, mode):
-    L, I, R0, cap, S, theta, seed = 4, 3, 300, 360, 6, 2, 5
+def test_pa_nearest_3d_ea_instances_and_launch_forms(ctx, law, fused, mode):
+    L, I, R0, cap, S, theta, seed = 4, 3, 300, 400, 6, 2, 5
     lat = gbmc.lattice_init(ctx, 3, L, model=gbmc.GBMC_EA_PMJ, n_instances=I, n_replicas=cap, seed=seed,
                             instance_base=2)
     gbmc.gbmc_set_resample_mode(ctx, fused)
     gbmc.gbmc_set_sweep_launch(ctx, mode)
     try:
-        pa = gbmc.pa_create(ctx, [lat], theta, S, beta_f=2.0, resample=NEAREST, initial_replicas=R0)
+        pa = gbmc.pa_create(ctx, [lat], theta, S, beta_f=2.0, resample=law, initial_replicas=R0)
         stats, _ = gbmc.pa_run(ctx, pa, capacity=S + 1)
     finally:
         gbmc.gbmc_set_resample_mode(ctx, True)
         gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_AUTO)
     betas = oracle.linear_betas(2.0, S)
-    refs = [oracle.pa_run_nearest(3, L, seed, 2 + i, R0, cap, betas, theta, J=oracle.couplings(L, seed, 2 + i))
-            for i in range(I)]
+    refs = [oracle.pa_run_nearest(3, L, seed, 2 + i, R0, cap, betas, theta, J=oracle.couplings(L, seed, 2 + i),
+                                  poisson=law == POISSON) for i in range(I)]
     for i, ref in enumerate(refs):
         assert ref["ok"]
         _compare(stats, ref, i, L ** 3)
@@ -84,14 +88,16 @@ def test_pa_nearest_3d_ea_instances_and_launch_forms(ctx, fused, mode):
     gbmc.lattice_free(lat)
 
 
-def test_pa_nearest_mixed_batch_and_graph_replay(ctx):
+@pytest.mark.parametrize("law", LAWS)
+def test_pa_nearest_mixed_batch_and_graph_replay(ctx, law):
     S, theta = 5, 2
-    a = gbmc.lattice_init(ctx, 2, 16, n_replicas=500, seed=3, instance_base=0)
-    b = gbmc.lattice_init(ctx, 2, 32, n_replicas=500, seed=3, instance_base=1)
-    pa = gbmc.pa_create(ctx, [a, b], theta, S, resample=NEAREST, initial_replicas=420)
+    a = gbmc.lattice_init(ctx, 2, 16, n_replicas=520, seed=3, instance_base=0)
+    b = gbmc.lattice_init(ctx, 2, 32, n_replicas=520, seed=3, instance_base=1)
+    pa = gbmc.pa_create(ctx, [a, b], theta, S, resample=law, initial_replicas=420)
     stats, _ = gbmc.pa_run(ctx, pa, capacity=S + 1)
     for pop, L in enumerate((16, 32)):
-        ref = oracle.pa_run_nearest(2, L, 3, pop, 420, 500, oracle.linear_betas(1.0, S), theta)
+        ref = oracle.pa_run_nearest(2, L, 3, pop, 420, 520, oracle.linear_betas(1.0, S), theta,
+                                    poisson=law == POISSON)
         assert ref["ok"]
         _compare(stats, ref, pop, L * L)
     first = spins_out(ctx, b).copy()
@@ -107,13 +113,14 @@ def test_pa_nearest_mixed_batch_and_graph_replay(ctx):
     gbmc.lattice_free(b)
 
 
-def test_pa_nearest_full_size_resampling_step_l64(ctx):
+@pytest.mark.parametrize("law", LAWS)
+def test_pa_nearest_full_size_resampling_step_l64(ctx, law):
     # R_0 = 10^5 replicas of L = 64 (capacity 1.05 10^5): the whole resampling
     # of step 3 (counts, R_3, children order) from the library's own energies
     L, R0, cap, seed = 64, 100000, 105000, 9
     betas = oracle.linear_betas(1.0, 100)
     lat = gbmc.lattice_init(ctx, 2, L, n_replicas=cap, seed=seed)
-    pa = gbmc.pa_create(ctx, [lat], 10, 100, resample=NEAREST, initial_replicas=R0)
+    pa = gbmc.pa_create(ctx, [lat], 10, 100, resample=law, initial_replicas=R0)
     rows = [gbmc.pa_step(ctx, pa) for _ in range(2)]
     n2 = int(rows[-1][0]["n_replicas"])
     E = np.empty(cap, dtype=np.int32)
@@ -121,7 +128,8 @@ def test_pa_nearest_full_size_resampling_step_l64(ctx):
     row3 = gbmc.pa_step(ctx, pa)
     par = np.empty(cap, dtype=np.uint32)
     gbmc.pa_parents_out(ctx, pa, 0, par)
-    counts, Rn, lnQ = oracle.resample_nearest(E[:n2].astype(np.int64), betas[3] - betas[2], R0, cap, seed, 0, 3)
+    resample = oracle.resample_poisson if law == POISSON else oracle.resample_nearest
+    counts, Rn, lnQ = resample(E[:n2].astype(np.int64), betas[3] - betas[2], R0, cap, seed, 0, 3)
     assert int(row3[0]["n_replicas"]) == Rn and abs(Rn - R0) < 2000
     np.testing.assert_array_equal(par[:Rn], oracle.children_order(counts))
     assert abs(row3[0]["lnQ"] - lnQ) <= RTOL * abs(lnQ) + 1e-13

@@ -63,8 +63,11 @@ def test_poisson_resampling_counts_have_mean_and_variance_tau():
     assert np.max(np.abs(c.var(0) / tau - 1) / np.sqrt((1 / tau + 2) / n)) < 5
     sizes = c.sum(1)
     assert abs(sizes.mean() - R0) < 5 * math.sqrt(R0 / n)
-    _, Rn, _ = oracle.resample_poisson(np.array([0, -4000], dtype=np.int64), 1.0, 2000, 2048, 2, 1, 1)
-    assert Rn is None  # one replica would expect ~2000 > 700 copies
+    # one replica takes all the weight: tau = 2000 > 500 is drawn as 4 pieces of Poisson(500)
+    sizes = [oracle.resample_poisson(np.array([0, -4000], dtype=np.int64), 1.0, 2000, 4096, 2, 1, st)[1]
+             for st in range(1, 401)]
+    assert abs(np.mean(sizes) - 2000) < 5 * math.sqrt(2000 / 400)
+    assert abs(np.var(sizes) / 2000 - 1) < 5 * math.sqrt(2 / 400)
 
 
 def test_pa_poisson_4x4_matches_enumeration():
