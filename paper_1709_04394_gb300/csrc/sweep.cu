@@ -52,11 +52,11 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
         const uint32_t W = L >> 3, rows = N / L;
         const uint8_t* jbc = EA ? jb + colour * (2u * DIM) * (N >> 1) : nullptr;
         if (ROWWISE) {
-            uint32_t y = wk.y0, z = wk.z0;
-#pragma unroll 4
-            for (uint32_t row = wk.row0; row < rows; row += wk.rstep) {
-                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
-                                             row * W + wk.g0);
+            // rows row and row + rstep in pairs: both units are loaded and updated
+            // before either word is stored (different rows of the colour plane:
+            // neither reads what the other writes), which frees the scheduler to
+            // overlap them
+            auto step = [&](uint32_t& y, uint32_t& z) {
                 if (DIM == 3) {
                     y += wk.dy;
                     z += wk.dz;
@@ -67,7 +67,27 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
                 } else {
                     y += wk.rstep;
                 }
+            };
+            uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * (N >> 1));
+            uint32_t y = wk.y0, z = wk.z0, row = wk.row0;
+#pragma unroll 2
+            for (; row + wk.rstep < rows; row += 2 * wk.rstep) {
+                uint32_t i1, v1, i2, v2;
+                unit_split<DIM, EA, MEASURE, false>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                                    row * W + wk.g0, &i1, &v1);
+                step(y, z);
+                const uint32_t r2 = row + wk.rstep;
+                unit_split<DIM, EA, MEASURE, false>(sp, jbc, L, N, r2, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                                    r2 * W + wk.g0, &i2, &v2);
+                step(y, z);
+                if (flip) {
+                    own[i1] = v1;
+                    own[i2] = v2;
+                }
             }
+            if (row < rows)
+                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                             row * W + wk.g0);
         } else {
             const uint32_t units = N >> 3;
             for (uint32_t uu = first_unit; uu < units; uu += stride) {

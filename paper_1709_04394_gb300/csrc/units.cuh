@@ -114,11 +114,15 @@ __device__ __forceinline__ uint32_t neq4(uint32_t a, uint32_t b) { return (a ^ b
 // base (plane 0 then plane 1, N/2 bytes each); jb: this colour's 2*DIM bond
 // planes (bytes 0x04 where J = -1; order same-j x, shifted x, y-1, y+1, z-1,
 // z+1); tbl: byte-addressed threshold table (entry a at byte 4a).
-template <int DIM, bool EA, bool MEASURE>
+// STORE = false: the new word is returned in *st_idx / *st_val (index into the
+// colour plane) instead of being written, so that a caller can load a second
+// unit before storing the first.
+template <int DIM, bool EA, bool MEASURE, bool STORE = true>
 __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint32_t L, uint32_t N,
                                            uint32_t row, uint32_t y, uint32_t z, uint32_t g, uint32_t colour,
                                            const PhiloxFixed& pf, const uint8_t* tbl, bool doflip, int& e_acc,
-                                           int& m_acc, uint32_t q) {
+                                           int& m_acc, uint32_t q, uint32_t* st_idx = nullptr,
+                                           uint32_t* st_val = nullptr) {
     const uint32_t W = L >> 3, H = N >> 1;
     const uint32_t o = (y + z + colour) & 1u;
     uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * H);
@@ -160,7 +164,12 @@ __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint3
         }
     }
     const uint32_t nw = cur ^ flip;
-    if (doflip) own[rw + g] = nw;
+    if constexpr (STORE) {
+        if (doflip) own[rw + g] = nw;
+    } else {
+        *st_idx = rw + g;
+        *st_val = nw;
+    }
     if (MEASURE) {
         // E contribution -sum s_new h = sum_acc s h - sum_rej s h, s h = 2 DIM - (4a)/2
         const int s_all = (int)__dp4a(a4, 0x01010101u, 0u);
