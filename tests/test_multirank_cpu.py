@@ -32,11 +32,12 @@ def _worker(rank, ws, port, q):
     ws_, rank_, local = bench.dist_env()
     dist = bench.init_dist(ws_, "gloo")
     t = bench.max_over_ranks(dist, ws_, 1.5 * (rank_ + 1))
+    u = bench.sum_over_ranks(dist, ws_, 10.0 * (rank_ + 1))  # site updates of all ranks
     bench.barrier(dist, ws_)
     seed = bench.rank_seed(rank_)
     bases = [bench.rank_instance_base(rank_, i, 4) for i in range(4)]
     r = oracle.pa_run(2, 8, seed, bases[0], 64, oracle.linear_betas(1.0, 3), 2)
-    q.put((rank_, t, seed, bases, int(r["sumE"][-1]), r["spins"].tobytes()))
+    q.put((rank_, t, seed, bases, int(r["sumE"][-1]), r["spins"].tobytes(), u))
     dist.destroy_process_group()
 
 
@@ -54,6 +55,7 @@ def test_two_ranks_gloo_independent_shards_and_max_timing():
         assert p.exitcode == 0
     out.sort()
     assert all(o[1] == 3.0 for o in out)          # max over ranks reached every rank
+    assert all(o[6] == 30.0 for o in out)         # whole-job units: the sum over ranks
     assert out[0][2] != out[1][2]                  # distinct seeds
     assert not set(out[0][3]) & set(out[1][3])     # disjoint instance ids
     assert out[0][5] != out[1][5]                  # different populations
