@@ -52,10 +52,10 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
         const uint32_t W = L >> 3, rows = N / L;
         const uint8_t* jbc = EA ? jb + colour * (2u * DIM) * (N >> 1) : nullptr;
         if (ROWWISE) {
-            // rows row and row + rstep in pairs: both units are loaded and updated
-            // before either word is stored (different rows of the colour plane:
-            // neither reads what the other writes), which frees the scheduler to
-            // overlap them
+            // each thread walks the rows row0, row0 + rstep, ... of its word column;
+            // in 2D four rows at a time: all four units are loaded and updated
+            // before any word is stored (different rows of the colour plane: none
+            // reads what another writes), which frees the scheduler to overlap them
             auto step = [&](uint32_t& y, uint32_t& z) {
                 if (DIM == 3) {
                     y += wk.dy;
@@ -70,24 +70,37 @@ __device__ __forceinline__ void half_sweep_copy_m(uint8_t* sp, const uint8_t* jb
             };
             uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * (N >> 1));
             uint32_t y = wk.y0, z = wk.z0, row = wk.row0;
-#pragma unroll 2
-            for (; row + wk.rstep < rows; row += 2 * wk.rstep) {
-                uint32_t i1, v1, i2, v2;
-                unit_split<DIM, EA, MEASURE, false>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
-                                                    row * W + wk.g0, &i1, &v1);
-                step(y, z);
-                const uint32_t r2 = row + wk.rstep;
-                unit_split<DIM, EA, MEASURE, false>(sp, jbc, L, N, r2, y, z, wk.g0, colour, pf, tbl, flip, e, m,
-                                                    r2 * W + wk.g0, &i2, &v2);
-                step(y, z);
-                if (flip) {
-                    own[i1] = v1;
-                    own[i2] = v2;
+            if constexpr (DIM == 3) {
+                // 3D: one unit at a time measured faster (six neighbour words and,
+                // for +-J, six bond words per unit already fill the registers)
+#pragma unroll 4
+                for (; row < rows; row += wk.rstep) {
+                    unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                                 row * W + wk.g0);
+                    step(y, z);
+                }
+            } else {
+#pragma unroll 1
+                for (; row + 3 * wk.rstep < rows; row += 4 * wk.rstep) {
+                    uint32_t ii[4], vv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t rk = row + k * wk.rstep;
+                        unit_split<DIM, EA, MEASURE, false>(sp, jbc, L, N, rk, y, z, wk.g0, colour, pf, tbl, flip, e,
+                                                            m, rk * W + wk.g0, &ii[k], &vv[k]);
+                        step(y, z);
+                    }
+                    if (flip) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) own[ii[k]] = vv[k];
+                    }
+                }
+                for (; row < rows; row += wk.rstep) {
+                    unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
+                                                 row * W + wk.g0);
+                    step(y, z);
                 }
             }
-            if (row < rows)
-                unit_split<DIM, EA, MEASURE>(sp, jbc, L, N, row, y, z, wk.g0, colour, pf, tbl, flip, e, m,
-                                             row * W + wk.g0);
         } else {
             const uint32_t units = N >> 3;
             for (uint32_t uu = first_unit; uu < units; uu += stride) {
