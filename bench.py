@@ -42,6 +42,9 @@ ALG_INT_OPS_PER_SITE_UPDATE = 20.0
 # Multi-spin-coded sweeps: per replica update one LCG step (multiply, add) and
 # one threshold comparison, plus an 80-op Philox call per 4 sites x 32 replicas.
 ALG_INT_OPS_PER_MSC_UPDATE = 3.0 + 80.0 / 128.0
+# Swendsen-Wang: spins read for the bonds, read and written by the flip (1 + 2 B),
+# one 4-byte forest pointer written by the tile labelling and read by the flip
+SW_BYTES_PER_SITE = 11
 
 
 def recorded_traffic(kernel_files, replicas):
@@ -465,6 +468,9 @@ def run_learned(args):
         gbmc.lattice_free(l)
     gbmc.gbmc_destroy(ctx)
     met = lambda sm: sm is not None and max(sm["df_mean"]) <= cfg["bar"]
+    met_all = lambda sm: sm is not None and max(sm["df_max"]) <= cfg["bar"]  # every seed, not just the mean
+    for sm in plain_tried:
+        sm["meets_bar_every_seed"] = met_all(sm)
     line = {"metric": "time to dF<=1e-4 per spin at beta=1, learned-schedule population annealing "
                       "(mixed 2D Ising L=32,64,128,256, R=5e4 each, one run)",
             "value": ml["seconds"] if met(ml) else None, "unit": "s", "higher_is_better": False,
@@ -472,8 +478,9 @@ def run_learned(args):
             "config": {"workload": "pa-learned", **{k: (list(v) if isinstance(v, tuple) else v) for k, v in cfg.items()},
                        "seeds": seeds},
             "mlp": {"seconds": ml["seconds"], "df_mean": ml["df_mean"], "df_max": ml["df_max"],
-                    "steps": ml["steps"], "acceptance": acc, "meets_bar": met(ml)},
-            "bisection": {**bis, "meets_bar": met(bis)},
+                    "steps": ml["steps"], "acceptance": acc, "meets_bar": met(ml),
+                    "meets_bar_every_seed": met_all(ml)},
+            "bisection": {**bis, "meets_bar": met(bis), "meets_bar_every_seed": met_all(bis)},
             "plain_linear": {"cheapest_meeting_bar": plain, "tried": plain_tried},
             "training": {"samples": int(X.shape[0]), "seconds": t_train, "train_run_seconds": train["seconds"]}}
     print(json.dumps(line))
@@ -620,7 +627,7 @@ def main():
         hbm_bytes_per_launch = sum(n * (2 * l[1] ** l[0] + 12) for n, l in zip(live, w["lattices"]))
     elif w.get("sw"):
         upd_per_launch = w["L"] ** w["dim"]                 # one Swendsen-Wang update (three launches)
-        hbm_bytes_per_launch = w["L"] ** w["dim"] * 13      # spins 1+2, bond flags 1+1, forest 4+4 bytes per site
+        hbm_bytes_per_launch = w["L"] ** w["dim"] * SW_BYTES_PER_SITE
     elif "dcb" in w:
         k, tile = w["dcb"]
         upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
@@ -647,7 +654,7 @@ def main():
         # cluster updates: bytes per update against the measured copy bandwidth
         roof = {"bound": "hbm", "kernel": kname, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                "alg_bytes_per_site_update": 13}
+                "alg_bytes_per_site_update": SW_BYTES_PER_SITE}
     line = {
         "metric": metric, "value": value, "unit": "spin-flips/ns", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -855,11 +855,12 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
     if (n_updates == 0) return GBMC_OK;
     if ((uint64_t)l->t + n_updates > 0xFFFFFFFFull) return fail(GBMC_ERR_ARG, "update counter would wrap");
     CUDA_TRY(cudaSetDevice(ctx->device));
-    if (!l->sw_bonds) {
-        cudaError_t e = cudaMalloc(&l->sw_bonds, l->N * l->ncopies);
-        if (e == cudaSuccess) e = cudaMalloc(&l->sw_parent, 4 * l->N * l->ncopies);
+    if (!l->sw_parent) {
+        const bool tiled = sw_tiled((uint32_t)l->d.dim, (uint32_t)l->d.L);
+        cudaError_t e = cudaMalloc(&l->sw_parent, 4 * l->N * l->ncopies);
+        if (e == cudaSuccess && !tiled) e = cudaMalloc(&l->sw_bonds, l->N * l->ncopies);
         if (e != cudaSuccess) {
-            cudaFree(l->sw_bonds);
+            cudaFree(l->sw_parent);
             l->sw_bonds = nullptr;
             l->sw_parent = nullptr;
             return fail(GBMC_ERR_OOM, "cudaMalloc(Swendsen-Wang workspace): %s", cudaGetErrorString(e));

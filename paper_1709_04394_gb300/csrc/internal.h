@@ -124,6 +124,9 @@ struct SwLaunch {
     uint32_t L, N, dim, R, inst_base, t;
 };
 cudaError_t launch_sw_update(const SwLaunch& P, uint64_t copies, cudaStream_t s);
+// Lattices labelled tile by tile (2D: 32 x 32 tiles, 3D: 16 x 8 x 8) need no
+// bond-flag array; the others use the global union-find over stored flags.
+inline bool sw_tiled(uint32_t dim, uint32_t L) { return (dim == 2 && L % 32 == 0) || (dim == 3 && L % 16 == 0); }
 
 // ---- population annealing resampling (Sec. 5.4, Eq. (13)) ----
 struct PaLattice {

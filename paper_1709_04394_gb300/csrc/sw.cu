@@ -19,13 +19,21 @@
 //
 // Tiled labelling (2D L % 32 == 0: 32 x 32 tiles; 3D L % 16 == 0: 16 x 8 x 8),
 // the tile decomposition of Sec. 3.3 with the consolidation done by atomics:
-//  k_sw_local : one CTA per tile computes the tile's bond flags (the same
-//               Philox words as k_sw_bonds), labels the tile's components in
-//               shared memory with the same lock-free union-find, and writes
-//               parent[i] = the smallest site of i's component within the
-//               tile (global index: increasing with the local one);
-//  k_sw_cross : the bonds that leave a tile are united in the global forest.
-// Each component again ends rooted at its smallest site.
+//  k_sw_local      : one CTA per tile computes the tile's bond flags (the same
+//                    Philox words as k_sw_bonds), labels the tile's components
+//                    in shared memory with the same lock-free union-find, and
+//                    writes parent[i] = the smallest site of i's component
+//                    within the tile (global index: increasing with the local one);
+//  k_sw_cross      : one thread per bond that leaves a tile recomputes its
+//                    flag and, if active, unites its ends in the global forest;
+//  k_sw_flip_tiled : one CTA per tile copies the tile's parent pointers to
+//                    shared memory and follows each site's chain there to the
+//                    last node inside the tile; only those end nodes look up
+//                    their root in the global forest and draw the root's coin,
+//                    which every site of the tile then reads from shared memory.
+// Each component again ends rooted at its smallest site (a hook always puts
+// the larger root under the smaller), so the labels and coins do not depend
+// on the order of the unions.
 #include "device.cuh"
 #include "internal.h"
 
@@ -64,21 +72,35 @@ __device__ __forceinline__ uint32_t sw_find(uint32_t* par, uint32_t x) {
 }
 
 // The active flags (bit mu) of the forward bonds of sites i0 .. i0 + 3
-// (i0 % 4 == 0): dim Philox calls cover bonds dim i0 .. dim (i0 + 4) - 1.
+// (i0 % 4 == 0): DIM Philox calls cover bonds DIM i0 .. DIM (i0 + 4) - 1; bond
+// 4 c + k of them belongs to site i0 + (4 c + k) / DIM.
+template <uint32_t DIM>
 __device__ __forceinline__ void sw_bond_flags(const SwLaunch& P, const int8_t* s, uint32_t i0, uint32_t r,
                                               uint32_t c3, uint32_t flags[4]) {
     flags[0] = flags[1] = flags[2] = flags[3] = 0u;
-    for (uint32_t c = 0; c < P.dim; ++c) {
-        const uint32_t q = (P.dim * i0) / 4 + c;
+#pragma unroll
+    for (uint32_t c = 0; c < DIM; ++c) {
+        const uint32_t q = (DIM * i0) / 4 + c;
         const uint4 w = philox4x32_10(make_uint4(q, P.t, r, c3), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t b = 4 * q + k, i = b / P.dim, mu = b - i * P.dim;
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t n = (4 * c + k) / DIM, mu = (4 * c + k) % DIM, i = i0 + n;
             const uint32_t u = k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
-            const uint32_t j = sw_forward(i, mu, P.L, P.dim);
-            if (s[i] == s[j] && (long long)u <= P.T_bond) flags[i - i0] |= 1u << mu;
+            const uint32_t j = sw_forward(i, mu, P.L, DIM);
+            if (s[i] == s[j] && (long long)u <= P.T_bond) flags[n] |= 1u << mu;
         }
     }
+}
+
+// Whether forward bond mu of site i is active: the same Philox word as in
+// sw_bond_flags (bond b = dim i + mu, call b >> 2, word b & 3).
+__device__ __forceinline__ bool sw_bond_active(const SwLaunch& P, const int8_t* s, uint32_t i, uint32_t mu,
+                                               uint32_t r, uint32_t c3) {
+    const uint32_t b = P.dim * i + mu, j = sw_forward(i, mu, P.L, P.dim);
+    if (s[i] != s[j]) return false;
+    const uint4 w = philox4x32_10(make_uint4(b >> 2, P.t, r, c3), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    const uint32_t u = (b & 3u) == 0 ? w.x : (b & 3u) == 1 ? w.y : (b & 3u) == 2 ? w.z : w.w;
+    return (long long)u <= P.T_bond;
 }
 
 // Lock-free union of a and b in forest par (global or shared memory).
@@ -103,6 +125,7 @@ __device__ __forceinline__ void sw_unite(uint32_t* par, uint32_t a, uint32_t b, 
     }
 }
 
+template <uint32_t DIM>
 __global__ void __launch_bounds__(256) k_sw_bonds(const __grid_constant__ SwLaunch P) {
     const uint64_t copy = P.copy0 + blockIdx.y;
     const uint32_t i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -113,7 +136,7 @@ __global__ void __launch_bounds__(256) k_sw_bonds(const __grid_constant__ SwLaun
     const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
     const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
     uint32_t flags[4];
-    sw_bond_flags(P, s, i0, r, c3, flags);
+    sw_bond_flags<DIM>(P, s, i0, r, c3, flags);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         bonds[i0 + k] = (uint8_t)flags[k];
@@ -129,13 +152,14 @@ __device__ __forceinline__ SwTile sw_tile(uint32_t dim) {
     return dim == 2 ? SwTile{32u, 32u, 1u} : SwTile{16u, 8u, 8u};
 }
 
+template <uint32_t DIM>
 __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaunch P) {
     __shared__ uint32_t lp[1024];
     const uint64_t copy = P.copy0 + blockIdx.y;
     const int8_t* s = P.spins + copy * P.N;
     const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
     const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
-    const SwTile T = sw_tile(P.dim);
+    const SwTile T = sw_tile(DIM);
     const uint32_t ntx = P.L / T.tx, nty = P.L / T.ty;
     const uint32_t bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
     // thread t: local sites l = 4t .. 4t+3 (consecutive x in one tile row)
@@ -143,43 +167,75 @@ __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaun
     const uint32_t lx = l0 % T.tx, ly = (l0 / T.tx) % T.ty, lz = l0 / (T.tx * T.ty);
     const uint32_t i0 = ((bz * T.tz + lz) * P.L + by * T.ty + ly) * P.L + bx * T.tx + lx;
     uint32_t flags[4];
-    sw_bond_flags(P, s, i0, r, c3, flags);
+    sw_bond_flags<DIM>(P, s, i0, r, c3, flags);
+    // runs along x: a site starts a run at x == 0 or where the bond from its
+    // left neighbour is inactive. Each site's first parent is the start of its
+    // run (a tile row spans TPR lanes of one warp: its run starts form one
+    // 32-bit mask), so only the bonds along y (and z) go through the union-find.
+    constexpr uint32_t TPR = (DIM == 2 ? 32u : 16u) / 4u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t left = __shfl_up_sync(0xffffffffu, flags[3] & 1u, 1);  // bond into this thread's first site
+    uint32_t starts = (lx == 0 || !left) ? 1u : 0u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) lp[l0 + k] = l0 + k;
+    for (int k = 1; k < 4; ++k) starts |= (flags[k - 1] & 1u) ? 0u : 1u << k;
+    starts <<= 4 * (lane % TPR);
+#pragma unroll
+    for (uint32_t o = 1; o < TPR; o <<= 1) starts |= __shfl_xor_sync(0xffffffffu, starts, o);
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)  // bit 0 (x == 0) is always set
+        lp[l0 + k] = l0 - lx + 31u - __clz(starts & ((2u << (lx + k)) - 1u));
     __syncthreads();
-    // bonds inside the tile: unite in shared memory
+    // bonds along y and z inside the tile: unite in shared memory
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const uint32_t l = l0 + k, x = lx + k;
-        if ((flags[k] & 1u) && x + 1 < T.tx) sw_unite<false>(lp, l, l + 1, P.err);
+        const uint32_t l = l0 + k;
         if ((flags[k] & 2u) && ly + 1 < T.ty) sw_unite<false>(lp, l, l + T.tx, P.err);
         if ((flags[k] & 4u) && lz + 1 < T.tz) sw_unite<false>(lp, l, l + T.tx * T.ty, P.err);
     }
     __syncthreads();
-    uint32_t* par = P.parent + copy * P.N;
-    uint8_t* bonds = P.bonds + copy * P.N;
+    uint32_t g[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t root = sw_find<false>(lp, l0 + k);
         const uint32_t rx = root % T.tx, ry = (root / T.tx) % T.ty, rz = root / (T.tx * T.ty);
-        par[i0 + k] = ((bz * T.tz + rz) * P.L + by * T.ty + ry) * P.L + bx * T.tx + rx;
-        bonds[i0 + k] = (uint8_t)flags[k];
+        g[k] = ((bz * T.tz + rz) * P.L + by * T.ty + ry) * P.L + bx * T.tx + rx;
     }
+    // i0 % 4 == 0, N % 4 == 0 and the forest is a cudaMalloc block: 16-byte aligned
+    *reinterpret_cast<uint4*>(P.parent + copy * P.N + i0) = make_uint4(g[0], g[1], g[2], g[3]);
 }
 
-// Bonds that leave their tile, united in the global forest.
+// The bonds that leave their tile: e < N / tx are the sites with x % tx == tx - 1
+// (bond along x), then N / ty sites with y % ty == ty - 1 (along y), then in 3D
+// N / tz sites with z % tz == tz - 1 (along z).
+__host__ __device__ __forceinline__ uint32_t sw_cross_count(uint32_t N, uint32_t dim) {
+    return dim == 2 ? N / 32 + N / 32 : N / 16 + N / 8 + N / 8;
+}
+
 __global__ void __launch_bounds__(256) k_sw_cross(const __grid_constant__ SwLaunch P) {
     const uint64_t copy = P.copy0 + blockIdx.y;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    const uint8_t f = P.bonds[copy * P.N + i];
-    if (!f) return;
+    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sw_cross_count(P.N, P.dim)) return;
     const SwTile T = sw_tile(P.dim);
-    const uint32_t x = i % P.L, y = (i / P.L) % P.L, z = i / (P.L * P.L);
-    uint32_t* par = P.parent + copy * P.N;
-    if ((f & 1u) && x % T.tx == T.tx - 1) sw_unite<true>(par, i, sw_forward(i, 0, P.L, P.dim), P.err);
-    if ((f & 2u) && y % T.ty == T.ty - 1) sw_unite<true>(par, i, sw_forward(i, 1, P.L, P.dim), P.err);
-    if ((f & 4u) && z % T.tz == T.tz - 1) sw_unite<true>(par, i, sw_forward(i, 2, P.L, P.dim), P.err);
+    const uint32_t L = P.L, LL = L * L;
+    uint32_t i, mu;
+    if (e < P.N / T.tx) {  // (row, tile column) -> x = tx c + tx - 1
+        const uint32_t nc = L / T.tx, row = e / nc;
+        i = row * L + (e - row * nc) * T.tx + T.tx - 1;
+        mu = 0;
+    } else if ((e -= P.N / T.tx) < P.N / T.ty) {  // (z, tile row k, x) -> y = ty k + ty - 1
+        const uint32_t nk = L / T.ty, x = e % L, rest = e / L, k = rest % nk, z = rest / nk;
+        i = (z * L + k * T.ty + T.ty - 1) * L + x;
+        mu = 1;
+    } else {  // (tile layer k, y, x) -> z = tz k + tz - 1
+        e -= P.N / T.ty;
+        const uint32_t k = e / LL;
+        i = (k * T.tz + T.tz - 1) * LL + (e - k * LL);
+        mu = 2;
+    }
+    const int8_t* s = P.spins + copy * P.N;
+    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    if (sw_bond_active(P, s, i, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst)))
+        sw_unite<true>(P.parent + copy * P.N, i, sw_forward(i, mu, L, P.dim), P.err);
 }
 
 __global__ void __launch_bounds__(256) k_sw_union(const __grid_constant__ SwLaunch P) {
@@ -207,6 +263,75 @@ __global__ void __launch_bounds__(256) k_sw_flip(const __grid_constant__ SwLaunc
     if (P.labels) P.labels[copy * P.N + i] = (int32_t)root;
 }
 
+__device__ __forceinline__ uint32_t sw_coin(const SwLaunch& P, uint32_t root, uint32_t r, uint32_t c3) {
+    const uint4 w = philox4x32_10(make_uint4(root >> 2, P.t, r, c3), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    const uint32_t word = (root & 3u) == 0 ? w.x : (root & 3u) == 1 ? w.y : (root & 3u) == 2 ? w.z : w.w;
+    return word >> 31;
+}
+
+__global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ SwLaunch P) {
+    __shared__ uint32_t tpar[1024];   // the tile's parent pointers (global site indices)
+    __shared__ uint32_t troot[1024];  // root of each end node
+    __shared__ uint8_t tcoin[1024];   // its coin (1: the cluster flips)
+    const uint64_t copy = P.copy0 + blockIdx.y;
+    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    const SwTile T = sw_tile(P.dim);
+    const uint32_t L = P.L, ntx = L / T.tx, nty = L / T.ty;
+    const uint32_t bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
+    const uint32_t l0 = 4 * threadIdx.x;
+    const uint32_t lx = l0 % T.tx, ly = (l0 / T.tx) % T.ty, lz = l0 / (T.tx * T.ty);
+    const uint32_t i0 = ((bz * T.tz + lz) * L + by * T.ty + ly) * L + bx * T.tx + lx;
+    uint32_t* par = P.parent + copy * P.N;
+    const uint4 p4 = __ldcg(reinterpret_cast<const uint4*>(par + i0));
+    tpar[l0] = p4.x;
+    tpar[l0 + 1] = p4.y;
+    tpar[l0 + 2] = p4.z;
+    tpar[l0 + 3] = p4.w;
+    __syncthreads();
+    // each site's chain inside the tile (pointers strictly decrease until a
+    // root, so at most 1024 steps) ends at node `end`: a root, or a node whose
+    // parent lies in another tile
+    uint32_t end[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t cl = l0 + k, cg = i0 + k;
+        for (uint32_t n = 0; n < 1024; ++n) {
+            const uint32_t p = tpar[cl];
+            if (p == cg) break;
+            const uint32_t px = p % L, py = (p / L) % L, pz = p / (L * L);
+            if (px / T.tx != bx || py / T.ty != by || pz / T.tz != bz) break;
+            cl = ((pz - bz * T.tz) * T.ty + (py - by * T.ty)) * T.tx + (px - bx * T.tx);
+            cg = p;
+        }
+        end[k] = cl;
+    }
+    // end nodes: the root in the global forest and its coin
+    const uint32_t c3 = c3_word(kPurposeSwFlip, 0u, P.inst_base + inst);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (end[k] != l0 + k) continue;
+        const uint32_t p = tpar[l0 + k];
+        const uint32_t root = p == i0 + k ? p : sw_find<true>(par, p);
+        troot[l0 + k] = root;
+        tcoin[l0 + k] = (uint8_t)sw_coin(P, root, r, c3);
+    }
+    __syncthreads();
+    // i0 % 4 == 0 and the spin buffer is 16-byte aligned: one word per thread
+    uint32_t* sw = reinterpret_cast<uint32_t*>(P.spins + copy * P.N + i0);
+    uint32_t w = *sw;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!tcoin[end[k]]) continue;
+        const uint32_t b = (uint32_t)(uint8_t)(-(int8_t)(w >> (8 * k)));
+        w = (w & ~(0xFFu << (8 * k))) | (b << (8 * k));
+    }
+    *sw = w;
+    if (P.labels) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) P.labels[copy * P.N + i0 + k] = (int32_t)troot[end[k]];
+    }
+}
+
 cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s) {
     if (P0.N % 4 != 0) return cudaErrorInvalidValue;
     for (uint64_t c0 = 0; c0 < copies; c0 += 65535) {
@@ -214,17 +339,23 @@ cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s
         P.copy0 = c0;
         const uint32_t nc = (uint32_t)((copies - c0) < 65535 ? (copies - c0) : 65535);
         const uint32_t quads = P.N / 4;
-        const bool tiled = (P.dim == 2 && P.L % 32 == 0) || (P.dim == 3 && P.L % 16 == 0);
+        const bool tiled = sw_tiled(P.dim, P.L);
         cudaError_t e;
         if (tiled) {
-            k_sw_local<<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            if (P.dim == 2) k_sw_local<2><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            else k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            k_sw_cross<<<dim3((P.N + 255) / 256, nc), 256, 0, s>>>(P);
+            k_sw_cross<<<dim3((sw_cross_count(P.N, P.dim) + 255) / 256, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_sw_flip_tiled<<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            continue;
         } else {
-            k_sw_bonds<<<dim3((quads + 255) / 256, nc), 256, 0, s>>>(P);
+            if (P.dim == 2) k_sw_bonds<2><<<dim3((quads + 255) / 256, nc), 256, 0, s>>>(P);
+            else k_sw_bonds<3><<<dim3((quads + 255) / 256, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             k_sw_union<<<dim3((P.N + 255) / 256, nc), 256, 0, s>>>(P);
