@@ -614,8 +614,9 @@ def main():
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
     kname = ("sweep_msc" if w.get("msc") else "sweep_resident") if w["kind"] == "pa" else \
-        ("bitpack_halfsweep" if w.get("layout", 0) == 1 else
-         ("sweep_dcb" if "dcb" in w else ("swendsen_wang" if w.get("sw") else "sweep_tiles")))
+        (("bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep") if w.get("layout", 0) == 1 else
+         ("sweep_dcb" if "dcb" in w else ("swendsen_wang" if w.get("sw") else
+                                          ("sweep_strips" if "sweep_strips" in prof else "sweep_tiles"))))
     n_l, t_l = prof.get(kname, (0, 0.0))
     if w.get("sw"):
         n_l //= 3  # one update = bond, union and flip launches
@@ -632,6 +633,12 @@ def main():
         k, tile = w["dcb"]
         upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
         hbm_bytes_per_launch = w["L"] ** 2 // 2 * ((tile + 16) ** 2 + tile ** 2) // tile ** 2  # window in, tile out
+    elif kname == "sweep_strips":
+        upd_per_launch = w["L"] ** w["dim"] * w["sweeps"]  # every sweep of the call in one launch
+        hbm_bytes_per_launch = 2 * w["L"] ** w["dim"]      # the int8 lattice read and written once
+    elif kname == "bitpack_strips":
+        upd_per_launch = w["L"] ** w["dim"] * w["sweeps"]  # every sweep of the call in one launch
+        hbm_bytes_per_launch = w["L"] ** w["dim"] // 4     # the packed lattice read and written once
     elif w.get("layout", 0) == 1:
         upd_per_launch = w["L"] ** w["dim"] // 2          # one colour per launch
         hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 16  # read both planes, write one (bits)

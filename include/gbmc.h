@@ -94,13 +94,22 @@ gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
  * lattice class says so or when several lattices share a launch, else grid.
  * Every form gives bit-identical results. Persistent launches of one context
  * share its counter, so a context's work must stay on one stream (no two of
- * its sweep launches in flight at once). Unknown mode: GBMC_ERR_ARG. */
+ * its sweep launches in flight at once). 2D ferromagnets too large for one
+ * thread block's shared memory (int8: L % 256 == 0, L <= 4096; bit-packed:
+ * L % 1024 == 0) with at most (SM count / 8) copies: AUTO and PERSISTENT run
+ * all sweeps of a metropolis_sweeps call without E/M series as one cooperative
+ * launch, each thread block keeping a strip of rows in shared memory and
+ * trading its first and last rows with its neighbours through global memory
+ * after every half-sweep (bounded waits; GBMC_ERR_TIMEOUT if one runs out);
+ * GRID uses the per-launch kernels (halo tiles of up to 4 sweeps, resp. one
+ * launch per half-sweep). Unknown mode: GBMC_ERR_ARG. */
 enum { GBMC_LAUNCH_AUTO = 0, GBMC_LAUNCH_GRID = 1, GBMC_LAUNCH_PERSISTENT = 2 };
 gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
-/* Test aid for the bounded grid barriers of the fused resampling: each
- * barrier waits for `phantom_arrivals` CTAs more than the launch has (so with
- * 1 the wait can only end by running out of its budget) and gives up after
- * `budget_cycles` SM cycles (default 2e9). A wait that runs out makes the
+/* Test aid for the bounded waits: each grid barrier of the fused resampling
+ * waits for `phantom_arrivals` CTAs more than the launch has, and each
+ * neighbour wait of the strip-resident sweeps for that many half-sweeps more
+ * (so with 1 a wait can only end by running out of its budget); waits give up
+ * after `budget_cycles` SM cycles (default 2e9). A wait that runs out makes the
  * kernel return early and the next synchronising call (gbmc_sync, pa_run,
  * pa_step with statistics) return GBMC_ERR_TIMEOUT; the context stays usable.
  * Pass (0, 2000000000) to restore the defaults. */

@@ -50,12 +50,17 @@ std::atomic<uint64_t> g_launches{0};
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
-    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_COUNT
+    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
-                                          "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang"};
+                                          "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
+                                          "bitpack_strips", "sweep_strips"};
+
+// Device words of a context: 8 flags and counters, then the progress
+// counters of strip-resident sweeps (one per CTA, one CTA per SM).
+constexpr size_t kCtxWords = 8 + 1024;
 
 // Interior size of the tiles of large 2D lattices (window = kTile + 16).
 constexpr uint32_t kTile = 128;
@@ -72,8 +77,9 @@ struct gbmc_ctx {
     cudaStream_t stream;
     int sm_count;
     unsigned int* words = nullptr;  // device [barrier counter, error flag, unit claims, finished CTAs,
-                                    //         population overflow flag, 3 spare]
+                                    //         population overflow flag, 3 spare, strip progress[1024]]
     bool fused = true;              // one cooperative resampling launch per lattice and step
+    bool coop = false;              // the device supports cooperative launches
     int32_t launch_mode = GBMC_LAUNCH_AUTO;  // grid or persistent resident sweeps
     uint32_t phantom = 0;           // test hook: extra barrier arrivals to wait for
     long long budget = 2000000000;  // cycles a barrier wait may last (about 1 s)
@@ -444,13 +450,14 @@ gbmc_status gbmc_create(gbmc_ctx** out, int device, void* cuda_stream) {
     int coop = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     c->fused = coop != 0;
+    c->coop = coop != 0;
     {
-        cudaError_t e = cudaMalloc(&c->words, 8 * sizeof(unsigned int));
+        cudaError_t e = cudaMalloc(&c->words, kCtxWords * sizeof(unsigned int));
         if (e != cudaSuccess) {
             delete c;
             return fail(GBMC_ERR_OOM, "cudaMalloc(context words): %s", cudaGetErrorString(e));
         }
-        e = cudaMemset(c->words, 0, 8 * sizeof(unsigned int));
+        e = cudaMemset(c->words, 0, kCtxWords * sizeof(unsigned int));
         if (e != cudaSuccess) {
             cudaFree(c->words);
             delete c;
@@ -756,6 +763,36 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
     if (l->d.layout == GBMC_BITPACK) {
         uint32_t thr[3];
         thresholds(beta, thr);
+        uint32_t Gc = 0, rmax = 0, threads = 0;
+        size_t smem = 0;
+        if (!E_series && !M_series && ctx->launch_mode != GBMC_LAUNCH_GRID && ctx->coop && n_sweeps <= 0x40000000u &&
+            ctx->sm_count <= (int)(kCtxWords - 8) &&
+            bp_strips_shape((uint32_t)l->d.L, l->ncopies, ctx->sm_count, Gc, rmax, threads, smem)) {
+            // every sweep of the call in one cooperative launch, strips resident in shared memory
+            BpStrips S;
+            std::memset(&S, 0, sizeof(S));
+            S.P = (uint32_t*)l->cur;
+            S.progress = ctx->words + 8;
+            S.err = ctx->words + 1;
+            S.budget = ctx->budget;
+            S.seed = l->d.seed;
+            S.L = (uint32_t)l->d.L;
+            S.Gc = Gc;
+            S.rmax = rmax;
+            S.R = l->d.n_replicas;
+            S.inst_base = l->d.instance_base;
+            S.t0 = l->t;
+            S.n_half = 2 * n_sweeps;
+            S.T4 = thr[0];
+            S.T8 = thr[1];
+            S.phantom = ctx->phantom;
+            {
+                ProfScope ps_(ctx, PK_BP_STRIPS);
+                CUDA_TRY(launch_bp_strips(S, l->ncopies, threads, smem, ctx->sm_count, ctx->stream));
+            }
+            l->t += n_sweeps;
+            return GBMC_OK;
+        }
         for (uint32_t s = 0; s < n_sweeps; ++s) {
             for (uint32_t colour = 0; colour < 2; ++colour) {
                 ProfScope ps_(ctx, PK_BP_HALFSWEEP);
@@ -776,6 +813,13 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
     const Tuning tu = tune(l);
     SweepJob J = base_job(l, tu);
     thresholds(beta, J.thr);
+    // strips of rows resident in shared memory for the whole call (large 2D ferromagnets, no E/M series)
+    uint32_t sGc = 0, srmax = 0, sthreads = 0;
+    size_t ssmem = 0;
+    const bool strips = !tu.resident && l->d.dim == 2 && l->d.model == GBMC_ISING_FM && !E_series && !M_series &&
+                        ctx->launch_mode != GBMC_LAUNCH_GRID && ctx->coop && n_sweeps <= 0x40000000u &&
+                        ctx->sm_count <= (int)(kCtxWords - 8) &&
+                        strips_shape((uint32_t)l->d.L, l->ncopies, ctx->sm_count, sGc, srmax, sthreads, ssmem);
     if (tu.resident) {
         SweepLaunch P;
         std::memset(&P, 0, sizeof(P));
@@ -789,6 +833,27 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
         P.swar = (l->d.L % 8) == 0;
         gbmc_status st = launch_jobs(ctx, P, std::vector<Tuning>{tu});
         if (st != GBMC_OK) return st;
+    } else if (strips) {
+        // large 2D lattices: every sweep of the call in one cooperative launch, strips resident in shared memory
+        StripLaunch S;
+        std::memset(&S, 0, sizeof(S));
+        S.spins = l->cur;
+        S.progress = ctx->words + 8;
+        S.err = ctx->words + 1;
+        S.budget = ctx->budget;
+        S.seed = l->d.seed;
+        S.L = (uint32_t)l->d.L;
+        S.Gc = sGc;
+        S.rmax = srmax;
+        S.R = l->d.n_replicas;
+        S.inst_base = l->d.instance_base;
+        S.t0 = l->t;
+        S.n_half = 2 * n_sweeps;
+        S.phantom = ctx->phantom;
+        S.thr[0] = J.thr[0];
+        S.thr[1] = J.thr[1];
+        ProfScope ps_(ctx, PK_SWEEP_STRIPS);
+        CUDA_TRY(launch_sweep_strips(S, l->ncopies, sthreads, ssmem, ctx->sm_count, ctx->stream));
     } else if (l->d.dim == 2 && l->d.model == GBMC_ISING_FM && l->d.L % kTile == 0) {
         // large 2D lattices: shared-memory tiles with halos, up to 4 sweeps per launch
         if (!l->alt) {

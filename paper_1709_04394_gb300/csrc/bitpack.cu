@@ -9,8 +9,23 @@
 // other plane in rows y-1, y, y+1 and that word shifted by one bit; the
 // number of unsatisfied bonds a (0..4) is summed bit-sliced (a0 + 2 a1 + 4 a2)
 // and a site flips iff a >= 2, or a = 1 and u <= T(4), or a = 0 and u <= T(8).
+//
+// Two sweep kernels:
+//  k_bp_halfsweep : one launch per half-sweep, one thread per word of the plane
+//                   (any L % 64 == 0, any number of copies);
+//  k_bp_strips    : all sweeps of a call in one cooperative launch. Each CTA
+//                   keeps a strip of rows of both planes in shared memory for the
+//                   whole run, with one halo row above and below. After each
+//                   half-sweep it writes only its first and last rows back to
+//                   global memory (updated first, then published by a progress
+//                   counter) and, before the next one, reads its two neighbours'
+//                   boundary rows once their counters show them. Each half-sweep
+//                   reads the other plane as the previous half-sweep left it, so
+//                   the result is that of the per-half-sweep launches.
+#include "bits.cuh"
 #include "device.cuh"
 #include "internal.h"
+#include "strips.cuh"
 
 namespace gbmc {
 
@@ -131,6 +146,31 @@ __device__ __forceinline__ void bp_neighbours(const uint32_t* oth, uint32_t L, u
     }
 }
 
+// The new value of the word s (32 sites of one colour) given its neighbour
+// words; q0 = the Philox counter q of its first site (colour rank k = y L/2 +
+// 32 w + b of bit b, q = k / 4).
+__device__ __forceinline__ uint32_t bp_word_update(uint32_t s, uint32_t up, uint32_t dn, uint32_t same, uint32_t side,
+                                                   const PhiloxFixed& pf, uint32_t q0, uint32_t T4, uint32_t T8) {
+    const uint32_t d1 = s ^ up, d2 = s ^ dn, d3 = s ^ same, d4 = s ^ side;  // 1 = unsatisfied bond
+    // bit-sliced a = d1 + d2 + d3 + d4 = a0 + 2 a1 + 4 a2
+    const uint32_t s1 = d1 ^ d2, c1 = d1 & d2, s2 = d3 ^ d4, c2 = d3 & d4;
+    const uint32_t a0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t a1 = c1 ^ c2 ^ c3, a2 = (c1 & c2) | (c3 & (c1 ^ c2));
+    const uint32_t ge2 = a1 | a2;            // dE <= 0: always flips
+    const uint32_t eq1 = a0 & ~ge2;          // dE = 4
+    const uint32_t eq0 = ~(a0 | ge2);        // dE = 8
+    uint32_t r4 = 0, r8 = 0;                 // bit b of the word at bit 31 - b
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint4 v = philox_q(pf, q0 + i);
+        accept_bits(r4, r8, T4, T8, v.x);
+        accept_bits(r4, r8, T4, T8, v.y);
+        accept_bits(r4, r8, T4, T8, v.z);
+        accept_bits(r4, r8, T4, T8, v.w);
+    }
+    return s ^ (ge2 | (eq1 & __brev(r4)) | (eq0 & __brev(r8)));
+}
+
 // One half-sweep of colour c over every copy: one thread per word of plane c.
 __global__ void __launch_bounds__(256) k_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R,
                                                       uint32_t inst_base, uint32_t colour, uint32_t t, uint32_t k0,
@@ -149,29 +189,8 @@ __global__ void __launch_bounds__(256) k_bp_halfsweep(uint32_t* P, uint32_t L, u
     const uint32_t o = (y + colour) & 1u;
     uint32_t up, dn, same, side;
     bp_neighbours(oth, L, Wr, y, w, o, up, dn, same, side);
-    const uint32_t s = own[rw];
-    const uint32_t d1 = s ^ up, d2 = s ^ dn, d3 = s ^ same, d4 = s ^ side;  // 1 = unsatisfied bond
-    // bit-sliced a = d1 + d2 + d3 + d4 = a0 + 2 a1 + 4 a2
-    const uint32_t s1 = d1 ^ d2, c1 = d1 & d2, s2 = d3 ^ d4, c2 = d3 & d4;
-    const uint32_t a0 = s1 ^ s2, c3 = s1 & s2;
-    const uint32_t a1 = c1 ^ c2 ^ c3, a2 = (c1 & c2) | (c3 & (c1 ^ c2));
-    const uint32_t ge2 = a1 | a2;            // dE <= 0: always flips
-    const uint32_t eq1 = a0 & ~ge2;          // dE = 4
-    const uint32_t eq0 = ~(a0 | ge2);        // dE = 8
     const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, inst_base + inst), k0, k1);
-    // colour rank of bit b: k = y L/2 + 32 w + b -> q = y L/8 + 8 w + b/4
-    const uint32_t q0 = y * (L >> 3) + 8 * w;
-    uint32_t m4 = 0, m8 = 0;
-#pragma unroll
-    for (uint32_t i = 0; i < 8; ++i) {
-        const uint4 v = philox_q(pf, q0 + i);
-        m4 |= ((uint32_t)(v.x <= T4) | ((uint32_t)(v.y <= T4) << 1) | ((uint32_t)(v.z <= T4) << 2) |
-               ((uint32_t)(v.w <= T4) << 3)) << (4 * i);
-        m8 |= ((uint32_t)(v.x <= T8) | ((uint32_t)(v.y <= T8) << 1) | ((uint32_t)(v.z <= T8) << 2) |
-               ((uint32_t)(v.w <= T8) << 3)) << (4 * i);
-    }
-    const uint32_t flip = ge2 | (eq1 & m4) | (eq0 & m8);
-    own[rw] = s ^ flip;
+    own[rw] = bp_word_update(own[rw], up, dn, same, side, pf, y * (L >> 3) + 8 * w, T4, T8);
 }
 
 cudaError_t launch_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base,
@@ -183,6 +202,124 @@ cudaError_t launch_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32
                                                     (uint32_t)(seed >> 32), T4, T8);
     count_launch();
     return cudaGetLastError();
+}
+
+// ---- strip-resident sweeps ----
+
+constexpr uint32_t kBpStripThreads = 1024;
+
+__global__ void __launch_bounds__(kBpStripThreads, 1) k_bp_strips(const __grid_constant__ BpStrips S) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int s_ok;
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t L = S.L, Wr = L >> 6;
+    const uint32_t copy = blockIdx.x / S.Gc, g = blockIdx.x - copy * S.Gc;
+    const uint32_t y0 = (uint32_t)((uint64_t)g * L / S.Gc), y1 = (uint32_t)((uint64_t)(g + 1) * L / S.Gc);
+    const uint32_t rs = y1 - y0;  // >= 2
+    const uint32_t inst = copy / S.R, r = copy - inst * S.R;
+    const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
+    const uint32_t ps = (S.rmax + 2) * Wr;  // words per plane in shared memory
+    uint32_t* gp = S.P + (uint64_t)copy * 2 * L * Wr;
+    // local row lr: 0 = the row above the strip, 1..rs = rows y0..y1-1, rs+1 = the row below
+    const uint32_t yu = y0 == 0 ? L - 1 : y0 - 1, yd = y1 == L ? 0 : y1;
+    auto grow = [&](uint32_t lr) { return lr == 0 ? yu : (lr == rs + 1 ? yd : y0 + lr - 1); };
+    for (uint32_t k = tid; k < 2 * (rs + 2) * Wr; k += B) {
+        const uint32_t c = k / ((rs + 2) * Wr), rem = k - c * (rs + 2) * Wr, lr = rem / Wr, w = rem - lr * Wr;
+        sm[c * ps + lr * Wr + w] = __ldcg(gp + ((uint64_t)c * L + grow(lr)) * Wr + w);
+    }
+    __syncthreads();  // all loads done before this CTA publishes anything
+    const unsigned int* pu = S.progress + copy * S.Gc + (g == 0 ? S.Gc - 1 : g - 1);
+    const unsigned int* pd = S.progress + copy * S.Gc + (g + 1 == S.Gc ? 0 : g + 1);
+    // Warps 0 .. nb/32 - 1 (thread k < nb) own the first and last rows: thread
+    // k < Wr word k of row 1, thread Wr + w word w of row rs. Each also
+    // refreshes the one halo word its update reads (row 0, resp. rs + 1), so
+    // only these warps wait for the neighbours, on named barrier 1; the other
+    // warps go straight to the interior rows.
+    const uint32_t nb = 2 * Wr, total = rs * Wr;
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    for (uint32_t h = 0; h < S.n_half; ++h) {
+        const uint32_t c = h & 1u;
+        uint32_t* own = sm + c * ps;
+        const uint32_t* oth = sm + (c ^ 1u) * ps;
+        const PhiloxFixed pf = philox_fix(S.t0 + (h >> 1), r, c3_word(kPurposeMetro, c, S.inst_base + inst), k0, k1);
+        auto update = [&](uint32_t lr, uint32_t w) {
+            const uint32_t y = y0 + lr - 1, o = (y + c) & 1u;
+            const uint32_t* orow = oth + lr * Wr;
+            const uint32_t same = orow[w];
+            const uint32_t side = o ? __funnelshift_r(same, orow[w + 1 == Wr ? 0 : w + 1], 1)   // bits j+1
+                                    : __funnelshift_l(orow[w == 0 ? Wr - 1 : w - 1], same, 1);  // bits j-1
+            const uint32_t v = bp_word_update(own[lr * Wr + w], oth[(lr - 1) * Wr + w], oth[(lr + 1) * Wr + w], same,
+                                              side, pf, y * (L >> 3) + 8 * w, S.T4, S.T8);
+            own[lr * Wr + w] = v;
+            return v;
+        };
+        if (tid < nb) {
+            const uint32_t lr = tid < Wr ? 1 : rs, w = tid < Wr ? tid : tid - Wr;
+            if (h > 0) {
+                // the neighbours' boundary rows of the other plane from half-sweep h - 1
+                if (tid == 0 && !strip_wait(pu, pd, h + S.phantom, S.err, S.budget)) s_ok = 0;
+                asm volatile("bar.sync 1, %0;" ::"r"(nb) : "memory");
+                const uint32_t hr = tid < Wr ? 0 : rs + 1;
+                sm[(c ^ 1u) * ps + hr * Wr + w] = __ldcg(gp + ((uint64_t)(c ^ 1u) * L + grow(hr)) * Wr + w);
+            }
+            if (s_ok) gp[((uint64_t)c * L + y0 + lr - 1) * Wr + w] = update(lr, w);
+            // the boundary warps meet; one fence then orders all their stores
+            asm volatile("bar.sync 1, %0;" ::"r"(nb) : "memory");
+            if (tid == 0 && s_ok) {
+                __threadfence();
+                atomicExch(S.progress + blockIdx.x, h + 1u);
+            }
+        }
+        for (uint32_t k = tid + (tid < nb ? B : 0u); k < total; k += B) {  // k >= nb: B >= nb by the launch shape
+            const uint32_t kk = k - nb, lr = 2 + kk / Wr;
+            update(lr, kk - (lr - 2) * Wr);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+    }
+    for (uint32_t k = tid; k < 2 * total; k += B) {
+        const uint32_t c = k / total, rem = k - c * total, lr = 1 + rem / Wr, w = rem - (lr - 1) * Wr;
+        gp[((uint64_t)c * L + y0 + lr - 1) * Wr + w] = sm[c * ps + lr * Wr + w];
+    }
+}
+
+bool bp_strips_shape(uint32_t L, uint64_t copies, int sm_count, uint32_t& Gc, uint32_t& rmax, uint32_t& threads,
+                     size_t& smem) {
+    // L % 1024 == 0: the 2 L/64 words of a strip's first and last rows are whole
+    // warps (they meet on a named barrier); at least 8 strips per copy, one per SM
+    if (L % 1024 != 0 || copies == 0 || sm_count < 8 || copies > (uint64_t)sm_count / 8) return false;
+    const uint32_t Wr = L >> 6;
+    Gc = (uint32_t)((uint64_t)sm_count / copies);
+    if (Gc > L / 2) Gc = L / 2;  // two rows or more per strip
+    rmax = (L + Gc - 1) / Gc;
+    const uint32_t words = rmax * Wr, iters = (words + kBpStripThreads - 1) / kBpStripThreads;
+    threads = ((words + iters - 1) / iters + 31) / 32 * 32;
+    smem = 2ull * (rmax + 2) * Wr * sizeof(uint32_t);
+    if (2 * Wr > threads || smem > 200u * 1024u) return false;
+    int fit = 0;
+    if (cudaFuncSetAttribute(k_bp_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_bp_strips, (int)threads, smem) != cudaSuccess)
+        return false;
+    return fit >= 1;
+}
+
+cudaError_t launch_bp_strips(const BpStrips& S, uint64_t copies, uint32_t threads, size_t smem, int sm_count,
+                             cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_bp_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bp_strips, (int)threads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = copies * S.Gc;
+    if (per_sm < 1 || grid > (uint64_t)per_sm * sm_count) return cudaErrorCooperativeLaunchTooLarge;
+    e = cudaMemsetAsync(S.progress, 0, grid * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    BpStrips Sc = S;
+    void* args[] = {&Sc};
+    e = cudaLaunchCooperativeKernel((const void*)k_bp_strips, dim3((uint32_t)grid), dim3(threads), args, smem, s);
+    count_launch();
+    return e;
 }
 
 // E and M of every copy: E = -sum over odd sites of s_i h_i = -(4 N/2 - 2 sum a_i),

@@ -78,6 +78,23 @@ cudaError_t launch_bp_pack(const int8_t* src, uint32_t* P, uint32_t L, uint64_t 
 cudaError_t launch_bp_unpack(const uint32_t* P, int8_t* dst, uint32_t L, uint64_t copies, cudaStream_t s);
 cudaError_t launch_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R, uint32_t inst_base,
                                 uint64_t seed, uint32_t colour, uint32_t t, uint32_t T4, uint32_t T8, cudaStream_t s);
+// All half-sweeps of a call in one cooperative launch, strips of rows resident
+// in shared memory (bitpack.cu). progress: copies * Gc counters, zeroed by the
+// launch; a wait that outlasts `budget` cycles raises *err and the kernel
+// returns. phantom: extra half-sweeps a wait asks for (0 in production; tests
+// set 1 to make a wait run out).
+struct BpStrips {
+    uint32_t* P;
+    unsigned int* progress;
+    unsigned int* err;
+    long long budget;
+    uint64_t seed;
+    uint32_t L, Gc, rmax, R, inst_base, t0, n_half, T4, T8, phantom;
+};
+bool bp_strips_shape(uint32_t L, uint64_t copies, int sm_count, uint32_t& Gc, uint32_t& rmax, uint32_t& threads,
+                     size_t& smem);
+cudaError_t launch_bp_strips(const BpStrips& S, uint64_t copies, uint32_t threads, size_t smem, int sm_count,
+                             cudaStream_t s);
 cudaError_t launch_bp_observables(const uint32_t* P, uint32_t L, uint64_t copies, int32_t* E, int32_t* M,
                                   cudaStream_t s);
 
@@ -98,6 +115,22 @@ struct TileLaunch {
 };
 size_t tile_smem_bytes(uint32_t T);
 cudaError_t launch_sweep_tiles(const TileLaunch& P, uint64_t copies, cudaStream_t s);
+// Strip-resident sweeps of large 2D ferromagnets, int8 layout (tiles.cu): all
+// half-sweeps of a call in one cooperative launch, the same protocol and
+// fields as BpStrips (thr = T(4), T(8)).
+struct StripLaunch {
+    int8_t* spins;
+    unsigned int* progress;
+    unsigned int* err;
+    long long budget;
+    uint64_t seed;
+    uint32_t L, Gc, rmax, R, inst_base, t0, n_half, phantom;
+    uint32_t thr[2];
+};
+bool strips_shape(uint32_t L, uint64_t copies, int sm_count, uint32_t& Gc, uint32_t& rmax, uint32_t& threads,
+                  size_t& smem);
+cudaError_t launch_sweep_strips(const StripLaunch& S, uint64_t copies, uint32_t threads, size_t smem, int sm_count,
+                                cudaStream_t s);
 // Double checkerboard (Fig. 5 right): the tiles of coarse colour P.coarse, each
 // swept P.nsweeps times in place (src == dst); T in {32, 64, 128}, L % 2T == 0.
 cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t s);

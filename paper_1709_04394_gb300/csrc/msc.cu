@@ -20,6 +20,7 @@
 // apart, which the padding spreads over all 32 banks.
 #include <climits>
 
+#include "bits.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -31,18 +32,6 @@ constexpr uint32_t kMscThreads = 256;
 
 __device__ __forceinline__ uint32_t pad(uint32_t i) { return i + (i >> 3); }
 
-// r4 = 2 r4 + [u <= T4], r8 = 2 r8 + [u <= T8]: the carry of T - u (set iff
-// no borrow, i.e. u <= T) shifted in by an add-with-carry, two instructions
-// per comparison.
-__device__ __forceinline__ void accept_bits(uint32_t& r4, uint32_t& r8, uint32_t T4, uint32_t T8, uint32_t u) {
-    asm("{\n\t.reg .u32 t;\n\t"
-        "sub.cc.u32 t, %2, %4;\n\t"
-        "addc.u32 %0, %0, %0;\n\t"
-        "sub.cc.u32 t, %3, %4;\n\t"
-        "addc.u32 %1, %1, %1;\n\t}"
-        : "+r"(r4), "+r"(r8)
-        : "r"(T4), "r"(T8), "r"(u));
-}
 __host__ __device__ __forceinline__ uint32_t padded_words(uint32_t N) { return N + (N >> 3); }
 
 // 3 CTAs per SM: the register cap (80) measured faster than the 100 registers

@@ -1,9 +1,11 @@
 // tiles.cu -- checkerboard Metropolis sweeps of 2D ferromagnets too large for
-// one CTA's shared memory (Sec. 3.1): halo tiles that reproduce the plain
-// two-phase sweeps exactly, and the double checkerboard of Fig. 5 (right)
-// with k sweeps per tile load.
+// one CTA's shared memory (Sec. 3.1): strips of rows resident in shared memory
+// for a whole call and halo tiles, both reproducing the plain two-phase sweeps
+// exactly, and the double checkerboard of Fig. 5 (right) with k sweeps per
+// tile load.
 #include "device.cuh"
 #include "internal.h"
+#include "strips.cuh"
 #include "units.cuh"
 
 namespace gbmc {
@@ -104,6 +106,161 @@ cudaError_t launch_sweep_tiles(const TileLaunch& P, uint64_t copies, cudaStream_
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ---- strip-resident sweeps of large 2D lattices ----
+constexpr uint32_t kStripThreads = 1024;
+// All sweeps of a call in one cooperative launch: CTA g of a copy keeps rows
+// [y0, y1) of the copy, plus the row above and the row below, as colour planes
+// in shared memory for the whole run. After each half-sweep only its first and
+// last rows go back to global memory (updated first, then published through a
+// progress counter); before the next one the CTA reads its neighbours' first
+// and last rows once their counters show them. Each half-sweep sees the other
+// colour as the previous half-sweep left it: the plain two-phase sweeps of
+// the whole lattice, in place, with no halo recomputation.
+
+// Thread t keeps word column t % W and walks rows t / W + 1, + B/W, ...; the
+// first and last rows (1 and rs) come first each half-sweep, then the others.
+// Before the end of a half-sweep each thread with boundary units waits for the
+// neighbours' half-sweep and refreshes the halo words its next units read, so
+// the half-sweep needs one CTA-wide barrier.
+__global__ void __launch_bounds__(kStripThreads, 1) k_sweep_strips(const __grid_constant__ StripLaunch S) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ __align__(16) uint32_t s_tbl[8];
+    __shared__ int s_ok;
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t L = S.L, W = L >> 3;  // words per plane row = 8-site chunks per lattice row
+    const uint32_t copy = blockIdx.x / S.Gc, g = blockIdx.x - copy * S.Gc;
+    const uint32_t y0 = (uint32_t)((uint64_t)g * L / S.Gc), y1 = (uint32_t)((uint64_t)(g + 1) * L / S.Gc);
+    const uint32_t rs = y1 - y0;  // >= 2
+    const uint32_t inst = copy / S.R, r = copy - inst * S.R;
+    const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
+    const uint32_t NL = (S.rmax + 2) * L, ps = NL >> 3;  // bytes of both planes; words per plane
+    uint32_t* pl = reinterpret_cast<uint32_t*>(smem);
+    int8_t* gs = S.spins + (uint64_t)copy * L * L;
+    // local row lr: 0 = the row above the strip, 1..rs = rows y0..y1-1, rs+1 = the row below
+    const uint32_t yu = y0 == 0 ? L - 1 : y0 - 1, yd = y1 == L ? 0 : y1;
+    auto grow = [&](uint32_t lr) { return lr == 0 ? yu : (lr == rs + 1 ? yd : y0 + lr - 1); };
+    // the even columns of row y have colour y & 1
+    for (uint32_t idx = tid; idx < (rs + 2) * W; idx += B) {
+        const uint32_t lr = idx / W, gy = grow(lr);
+        const uint2 v = __ldcg(reinterpret_cast<const uint2*>(gs + (uint64_t)gy * L) + (idx - lr * W));
+        const uint32_t pe = gy & 1u;
+        pl[pe * ps + idx] = __byte_perm(v.x, v.y, 0x6420);
+        pl[(pe ^ 1u) * ps + idx] = __byte_perm(v.x, v.y, 0x7531);
+    }
+    if (tid < 8) {
+        const int d = 2 - (int)tid;
+        s_tbl[tid] = d <= 0 ? 0xFFFFFFFFu : (d == 1 ? S.thr[0] : S.thr[1]);
+    }
+    if (tid == 0) s_ok = 1;
+    __syncthreads();  // all loads done before this CTA publishes anything
+    const uint8_t* tbl = reinterpret_cast<const uint8_t*>(s_tbl);
+    const unsigned int* pu = S.progress + copy * S.Gc + (g == 0 ? S.Gc - 1 : g - 1);
+    const unsigned int* pd = S.progress + copy * S.Gc + (g + 1 == S.Gc ? 0 : g + 1);
+    // unit_split walks rows of an L-wide lattice: pass it a row index with the
+    // parity of the global row that never wraps (2 or 3 above the local row)
+    const uint32_t ydelta = 2 + ((y0 + 1) & 1u);
+    const uint32_t nb = 2 * W, total = rs * W, w = tid % W, rstep = B / W;
+    const uint32_t nbth = nb < B ? nb : B;  // threads with boundary units
+    int e = 0, m = 0;
+    for (uint32_t h = 0; h < S.n_half; ++h) {
+        const uint32_t c = h & 1u;
+        const PhiloxFixed pf = philox_fix(S.t0 + (h >> 1), r, c3_word(kPurposeMetro, c, S.inst_base + inst), k0, k1);
+        auto update = [&](uint32_t lr, uint32_t wc) {
+            unit_split<2, false, false>(smem, nullptr, L, NL, lr, lr + ydelta, 0, wc, c, pf, tbl, true, e, m,
+                                        (y0 + lr - 1) * W + wc);
+        };
+        // boundary unit k < W: word k of row 1 (next to halo row 0); W + w: word
+        // w of row rs (next to rs + 1)
+        if (tid < nb) {
+            for (uint32_t k = tid; k < nb; k += B) {
+                const uint32_t lr = k < W ? 1 : rs, wk = k < W ? k : k - W;
+                update(lr, wk);
+                const uint32_t gy = y0 + lr - 1, pe = gy & 1u;
+                const uint32_t ev = pl[pe * ps + lr * W + wk], od = pl[(pe ^ 1u) * ps + lr * W + wk];
+                uint2 v;
+                v.x = __byte_perm(ev, od, 0x5140);
+                v.y = __byte_perm(ev, od, 0x7362);
+                reinterpret_cast<uint2*>(gs + (uint64_t)gy * L)[wk] = v;
+            }
+            // the boundary threads (whole warps) meet; one fence then orders all their stores
+            asm volatile("bar.sync 1, %0;" ::"r"(nbth) : "memory");
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(S.progress + blockIdx.x, h + 1u);
+            }
+        }
+        // interior rows 2 .. rs - 1. After the first two passes (the neighbours
+        // publish at the start of their half-sweep), the halo words the next
+        // half-sweep's boundary units read: this plane as the neighbours left it
+        // after this half-sweep, each fetched by the thread that uses it (the
+        // halo rows of this plane are not read in this half-sweep)
+        uint32_t lr = 2 + tid / W;
+        for (uint32_t i = 0; i < 2 && lr < rs; ++i, lr += rstep) update(lr, w);
+        if (tid < nb && h + 1 < S.n_half) {
+            // lane 0 of each warp polls (W % 32 == 0: whole warps here, in step)
+            int ok = 1;
+            if ((tid & 31u) == 0) ok = strip_wait(pu, pd, h + 1 + S.phantom, S.err, S.budget);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) s_ok = 0;
+            for (uint32_t k = tid; k < nb; k += B) {
+                const uint32_t hr = k < W ? 0 : rs + 1, wk = k < W ? k : k - W, gy = grow(hr);
+                const uint2 v = __ldcg(reinterpret_cast<const uint2*>(gs + (uint64_t)gy * L) + wk);
+                pl[c * ps + hr * W + wk] = __byte_perm(v.x, v.y, (gy & 1u) == c ? 0x6420 : 0x7531);
+            }
+        }
+        for (; lr < rs; lr += rstep) update(lr, w);
+        __syncthreads();
+        if (!s_ok) return;
+    }
+    for (uint32_t idx = tid; idx < total; idx += B) {
+        const uint32_t lr = 1 + idx / W, wk = idx - (lr - 1) * W, gy = y0 + lr - 1, pe = gy & 1u;
+        const uint32_t ev = pl[pe * ps + lr * W + wk], od = pl[(pe ^ 1u) * ps + lr * W + wk];
+        uint2 v;
+        v.x = __byte_perm(ev, od, 0x5140);
+        v.y = __byte_perm(ev, od, 0x7362);
+        reinterpret_cast<uint2*>(gs + (uint64_t)gy * L)[wk] = v;
+    }
+}
+
+bool strips_shape(uint32_t L, uint64_t copies, int sm_count, uint32_t& Gc, uint32_t& rmax, uint32_t& threads,
+                  size_t& smem) {
+    // L % 256 == 0: a plane row is whole warps' worth of words (W % 32 == 0), so
+    // a warp's threads share their rows; at least 8 strips per copy, one per SM
+    if (L % 256 != 0 || copies == 0 || sm_count < 8 || copies > (uint64_t)sm_count / 8) return false;
+    const uint32_t W = L >> 3;
+    if (W > kStripThreads) return false;
+    Gc = (uint32_t)((uint64_t)sm_count / copies);
+    if (Gc > L / 2) Gc = L / 2;
+    rmax = (L + Gc - 1) / Gc;
+    // whole rows per pass: a thread keeps one word column
+    const uint32_t rows = kStripThreads / W < rmax ? kStripThreads / W : rmax;
+    threads = rows * W;
+    smem = (size_t)(rmax + 2) * L;
+    if (smem > 200u * 1024u) return false;
+    int fit = 0;
+    if (cudaFuncSetAttribute(k_sweep_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_sweep_strips, (int)threads, smem) != cudaSuccess)
+        return false;
+    return fit >= 1;
+}
+
+cudaError_t launch_sweep_strips(const StripLaunch& S, uint64_t copies, uint32_t threads, size_t smem, int sm_count,
+                                cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_strips, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_strips, (int)threads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = copies * S.Gc;
+    if (per_sm < 1 || grid > (uint64_t)per_sm * sm_count) return cudaErrorCooperativeLaunchTooLarge;
+    e = cudaMemsetAsync(S.progress, 0, grid * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    StripLaunch Sc = S;
+    void* args[] = {&Sc};
+    e = cudaLaunchCooperativeKernel((const void*)k_sweep_strips, dim3((uint32_t)grid), dim3(threads), args, smem, s);
+    count_launch();
+    return e;
 }
 
 // ---- double checkerboard with k hits per tile (Sec. 3.1, Fig. 5 right) ----

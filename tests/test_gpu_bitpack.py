@@ -47,6 +47,45 @@ def test_packed_sweeps_match_oracle(ctx, L, I, R, n, beta):
     gbmc.lattice_free(lat)
 
 
+@pytest.mark.parametrize("L,I,R,n,beta", [(1024, 1, 1, 5, 0.4406868), (1024, 1, 3, 3, 0.8), (2048, 2, 1, 4, 0.3),
+                                          (4096, 1, 1, 3, 0.4406868), (1024, 1, 20, 2, 0.4406868)])
+def test_packed_strip_resident_sweeps_match_oracle(ctx, L, I, R, n, beta):
+    # no E/M series: L % 1024 == 0 runs every sweep of the call in one launch
+    # (strips of rows in shared memory) when at most SMs / 8 copies; 20 copies
+    # take the per-half-sweep launches
+    seed = 11 + L
+    lat = gbmc.lattice_init(ctx, 2, L, n_instances=I, n_replicas=R, seed=seed, instance_base=2, layout=BP)
+    gbmc.lattice_set_sweep_counter(lat, 9)
+    n0 = gbmc.gbmc_kernel_launches()
+    gbmc.metropolis_sweeps(ctx, lat, beta, n)
+    gbmc.metropolis_sweeps(ctx, lat, beta, 1)  # continues the counters
+    launches = gbmc.gbmc_kernel_launches() - n0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert launches == (2 if I * R <= sms // 8 else 2 * (n + 1))
+    got = spins_out(ctx, lat)
+    for i in range(I):
+        for r in range(R):
+            s = oracle.init_spins(2, L, seed, 2 + i, r, True)
+            oracle.sweeps(2, L, s, None, beta, seed, 2 + i, r, 9, n + 1)
+            np.testing.assert_array_equal(got[i * R + r], s)
+    gbmc.lattice_free(lat)
+
+
+def test_packed_strips_equal_per_half_sweep_launches(ctx):
+    L, n = 4096, 6
+    a = gbmc.lattice_init(ctx, 2, L, seed=4, layout=BP)
+    b = gbmc.lattice_init(ctx, 2, L, seed=4, layout=BP)
+    gbmc.metropolis_sweeps(ctx, a, 0.4406868, n)
+    gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_GRID)
+    try:
+        gbmc.metropolis_sweeps(ctx, b, 0.4406868, n)
+    finally:
+        gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_AUTO)
+    np.testing.assert_array_equal(spins_out(ctx, a), spins_out(ctx, b))
+    gbmc.lattice_free(a)
+    gbmc.lattice_free(b)
+
+
 def test_packed_equals_int8_layout(ctx):
     L, R, n = 256, 3, 12
     a = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=8, layout=BP)

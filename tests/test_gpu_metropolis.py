@@ -107,14 +107,21 @@ def test_sweeps_match_oracle(ctx, dim, L, model, n_inst, R, beta, n):
     gbmc.lattice_free(lat)
 
 
+@pytest.mark.parametrize("mode", [gbmc.GBMC_LAUNCH_AUTO, gbmc.GBMC_LAUNCH_GRID])
 @pytest.mark.parametrize("L,n,chunks", [(512, 6, (6,)), (512, 3, (1, 2)), (4096, 2, (2,)), (384, 9, (4, 5)),
                                         (768, 2, (2,)), (520, 2, (2,))])
-def test_large_lattice_paths_match_oracle(ctx, L, n, chunks):
-    # lattices too large for shared memory: tiled sweeps (L % 128 == 0, up to 4 sweeps
-    # per launch, any chunking) or global half-sweeps; L = 4096 is the benchmark size
+def test_large_lattice_paths_match_oracle(ctx, L, n, chunks, mode):
+    # lattices too large for shared memory, L % 128 == 0: strips of rows resident
+    # in shared memory for a whole call (AUTO) or tiled sweeps (GRID: up to 4
+    # sweeps per launch, any chunking); else global half-sweeps. L = 4096 is the
+    # benchmark size
     lat = gbmc.lattice_init(ctx, 2, L, seed=1)
-    for c in chunks:
-        gbmc.metropolis_sweeps(ctx, lat, BETA_C, c)
+    gbmc.gbmc_set_sweep_launch(ctx, mode)
+    try:
+        for c in chunks:
+            gbmc.metropolis_sweeps(ctx, lat, BETA_C, c)
+    finally:
+        gbmc.gbmc_set_sweep_launch(ctx, gbmc.GBMC_LAUNCH_AUTO)
     E, M = device_i32(1), device_i32(1)
     gbmc.observables(ctx, lat, E, M)
     got = spins_out(ctx, lat)[0]
@@ -122,6 +129,24 @@ def test_large_lattice_paths_match_oracle(ctx, L, n, chunks):
     oracle.sweeps(2, L, s, None, BETA_C, 1, 0, 0, 0, n)
     np.testing.assert_array_equal(got, s)
     assert (int(E[0]), int(M[0])) == oracle.observables(2, L, s)
+    gbmc.lattice_free(lat)
+
+
+@pytest.mark.parametrize("L,I,R,n,beta", [(1024, 1, 3, 4, 0.6), (2048, 2, 1, 3, 0.3), (4096, 1, 2, 2, 0.2)])
+def test_strip_resident_sweeps_several_copies(ctx, L, I, R, n, beta):
+    # one launch per call, strips of every copy side by side; counters continue
+    lat = gbmc.lattice_init(ctx, 2, L, n_instances=I, n_replicas=R, seed=21, instance_base=5)
+    gbmc.lattice_set_sweep_counter(lat, 3)
+    n0 = gbmc.gbmc_kernel_launches()
+    gbmc.metropolis_sweeps(ctx, lat, beta, n - 1)
+    gbmc.metropolis_sweeps(ctx, lat, beta, 1)
+    assert gbmc.gbmc_kernel_launches() - n0 == 2
+    got = spins_out(ctx, lat)
+    for i in range(I):
+        for r in range(R):
+            s = oracle.init_spins(2, L, 21, 5 + i, r, True)
+            oracle.sweeps(2, L, s, None, beta, 21, 5 + i, r, 3, n)
+            np.testing.assert_array_equal(got[i * R + r], s)
     gbmc.lattice_free(lat)
 
 

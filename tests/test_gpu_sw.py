@@ -19,6 +19,9 @@ pytestmark = pytest.mark.gpu
     (2, 32, 1, 2, 3, 0.0),      # beta = 0: every site its own cluster
     (3, 8, 1, 3, 4, 0.2216544),
     (3, 16, 1, 1, 2, 0.3),
+    (2, 96, 1, 1, 3, 0.4406868),  # 3 x 3 tiles: L not a power of two
+    (2, 64, 1, 2, 3, 1.5),        # ordered: clusters span every tile
+    (3, 32, 1, 1, 2, 0.5),        # 3D tiles, ordered
 ])
 def test_sw_matches_oracle(ctx, dim, L, I, R, n, beta):
     seed = 41 + L
