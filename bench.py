@@ -204,6 +204,11 @@ WORKLOADS = {
                                    nearest=100000, poisson=True),
     # the default workload with multi-spin-coded sweeps (32 replicas per word, LCG uniforms)
     "pa-ising2d-L64-msc": dict(kind="pa", lattices=[(2, 64, FM, 1, 100000)], S=100, theta=10, beta_f=1.0, msc=True),
+    # parallel tempering (Sec. 5.1, Eq. (10)) of the 3D +-J spin glass L=8: 1024 instances x 32
+    # temperatures (beta 0.2 .. 3.0, geometric), theta = 10 sweeps between exchange rounds,
+    # 100 rounds per step
+    "pt-ea3d-L8": dict(kind="pt", dim=3, L=8, model=EA, I=1024, T=32, beta_lo=0.2, beta_hi=3.0, theta=10,
+                       rounds=100),
     # mixed 2D batch in one launch: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4), (256, 10^4)
     "pa-mixed-2d": dict(kind="pa", lattices=[(2, 32, FM, 1, 100000), (2, 64, FM, 1, 50000),
                                              (2, 128, FM, 1, 20000), (2, 256, FM, 1, 10000)],
@@ -222,7 +227,15 @@ def copies(lat):
 def site_updates_per_step(w):
     if w["kind"] == "pa":
         return sum(copies(l) * l[1] ** l[0] for l in w["lattices"]) * w["theta"] * w["S"]
+    if w["kind"] == "pt":
+        return w["I"] * w["T"] * w["L"] ** w["dim"] * w["theta"] * w["rounds"]
     return w["L"] ** w["dim"] * w["sweeps"]
+
+
+def pt_betas(w):
+    import numpy as np
+
+    return np.geomspace(w["beta_lo"], w["beta_hi"], w["T"])
 
 
 def sweep_lattice(gbmc, ctx, lat, w):
@@ -281,6 +294,15 @@ def run_gpu(args, w, ws, rank, local):
             stats, _ = run(ctx, pa, capacity=w["S"] + 1)
             return sum(int(stats[1:, p]["n_replicas"].sum()) * l[1] ** l[0] * w["theta"]
                        for p, l in enumerate(w["lattices"]))
+    elif w["kind"] == "pt":
+        lat = gbmc.lattice_init(ctx, w["dim"], w["L"], model=w["model"], n_instances=w["I"], n_replicas=w["T"],
+                                seed=seed0, instance_base=rank * w["I"])
+        lats = [lat]
+        pts = [gbmc.pt_create(ctx, lat, pt_betas(w), w["theta"])]
+
+        def step(k, graph=False):
+            gbmc.pt_step(ctx, pts[0], w["rounds"])
+            return site_updates_per_step(w)
     else:
         N = w["L"] ** w["dim"]
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], n_replicas=1, seed=seed0, layout=w.get("layout", 0))
@@ -353,6 +375,17 @@ def run_gpu(args, w, ws, rank, local):
             gbmc.pa_reset(ctx, pa, False, seed0 + 500 + k)
             stats, _ = gbmc.pa_run(ctx, pa, capacity=w["S"] + 1)
             d2h_stats = stats.nbytes
+        elif w["kind"] == "pt":
+            # a fresh run on the copied-in configurations; the temperature map,
+            # swap counts and energies come back with the spins
+            gbmc.pt_free(pts[0])
+            pts[0] = gbmc.pt_create(ctx, lats[0], pt_betas(w), w["theta"])
+            gbmc.pt_step(ctx, pts[0], w["rounds"])
+            rep = torch.empty(w["I"] * w["T"], dtype=torch.int32, pin_memory=True)
+            acc = torch.empty(w["I"] * (w["T"] - 1), dtype=torch.int32, pin_memory=True)
+            Eh = torch.empty(w["I"] * w["T"], dtype=torch.int32, pin_memory=True)
+            gbmc.pt_state_out(ctx, pts[0], rep, acc, Eh)
+            d2h_stats = 4 * (rep.numel() + acc.numel() + Eh.numel())
         else:
             sweep_lattice(gbmc, ctx, lats[0], w)
             d2h_stats = 0
@@ -363,6 +396,8 @@ def run_gpu(args, w, ws, rank, local):
     result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e)
     if w["kind"] == "pa":
         gbmc.pa_free(pa)
+    if w["kind"] == "pt":
+        gbmc.pt_free(pts[0])
     for l in lats:
         gbmc.lattice_free(l)
     gbmc.gbmc_destroy(ctx)
@@ -512,6 +547,15 @@ def cpu_oracle_sample(w):
         dt = time.perf_counter() - t0
         desc = "oracle %s: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
                "theta=%d" % (name, dim, L, Rs, w.get("nearest", R), steps, w["S"], w["theta"])
+    elif w["kind"] == "pt":
+        rounds = 20
+        J = oracle.couplings(w["L"], 1, 0) if w["model"] == EA else None
+        t0 = time.perf_counter()
+        oracle.pt_run(w["dim"], w["L"], 1, 0, pt_betas(w), w["theta"], rounds, J=J)
+        dt = time.perf_counter() - t0
+        upd = w["T"] * w["L"] ** w["dim"] * w["theta"] * rounds
+        desc = "oracle pt_run: one instance (of %d), %d temperatures, %d of %d rounds, theta=%d" % (
+            w["I"], w["T"], rounds, w["rounds"], w["theta"])
     elif w.get("sw"):
         s = oracle.init_spins(w["dim"], w["L"], 1, 0, 0, True)
         t0 = time.perf_counter()
@@ -572,12 +616,15 @@ def main():
         w["dcb"] = (k, args.dcb_tile or w["dcb"][1])
         w["sweeps"] = max(1, w["sweeps"] // k) * k
     ws, rank, local = dist_env()
-    metric = "spin-flips/ns (checkerboard Metropolis site updates per ns, whole annealing runs incl. resampling)" \
-        if w["kind"] == "pa" else "spin-flips/ns (checkerboard Metropolis site updates per ns)"
+    metric = {"pa": "spin-flips/ns (checkerboard Metropolis site updates per ns, whole annealing runs incl. "
+                    "resampling)",
+              "pt": "spin-flips/ns (checkerboard Metropolis site updates per ns, parallel tempering incl. "
+                    "exchange rounds)"}.get(w["kind"], "spin-flips/ns (checkerboard Metropolis site updates per ns)")
     upd = site_updates_per_step(w)
     config = {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
-              "l2_flush": "inputs larger than L2 (2 x 409.6 MB population)" if w["kind"] == "pa"
-              else "none: 16 MiB lattice is L2-resident (single-lattice case)",
+              "l2_flush": {"pa": "inputs larger than L2 (2 x 409.6 MB population)",
+                           "pt": "none: 16.8 MB of copies, L2-resident between rounds"}.get(
+                  w["kind"], "none: 16 MiB lattice is L2-resident (single-lattice case)"),
               "parallelism": "replicas only: independent populations per rank" if ws > 1 else "single GPU",
               "sweep_launch": args.sweep_launch,
               "cuda_graph": bool(args.graph)}
@@ -613,7 +660,7 @@ def main():
     upd_step = res["upd_local"] / args.steps  # this rank's updates per step (variable populations: measured)
     prof = res["prof"]
     # dominant kernel: the sweep kernel of the workload
-    kname = ("sweep_msc" if w.get("msc") else "sweep_resident") if w["kind"] == "pa" else \
+    kname = ("sweep_msc" if w.get("msc") else "sweep_resident") if w["kind"] in ("pa", "pt") else \
         (("bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep") if w.get("layout", 0) == 1 else
          ("sweep_dcb" if "dcb" in w else ("swendsen_wang" if w.get("sw") else
                                           ("sweep_strips" if "sweep_strips" in prof else "sweep_tiles"))))
@@ -626,6 +673,9 @@ def main():
         live = [upd_step / (w["S"] * w["theta"] * l[1] ** l[0]) if "nearest" in w else copies(l) for l in w["lattices"]]
         upd_per_launch = sum(n * l[1] ** l[0] for n, l in zip(live, w["lattices"])) * w["theta"]
         hbm_bytes_per_launch = sum(n * (2 * l[1] ** l[0] + 12) for n, l in zip(live, w["lattices"]))
+    elif w["kind"] == "pt":
+        upd_per_launch = w["I"] * w["T"] * w["L"] ** w["dim"] * w["theta"]  # theta sweeps of every copy
+        hbm_bytes_per_launch = w["I"] * w["T"] * 2 * w["L"] ** w["dim"]
     elif w.get("sw"):
         upd_per_launch = w["L"] ** w["dim"]                 # one Swendsen-Wang update (three launches)
         hbm_bytes_per_launch = w["L"] ** w["dim"] * SW_BYTES_PER_SITE

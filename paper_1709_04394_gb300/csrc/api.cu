@@ -50,13 +50,13 @@ std::atomic<uint64_t> g_launches{0};
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
-    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_COUNT
+    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
                                           "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
-                                          "bitpack_strips", "sweep_strips"};
+                                          "bitpack_strips", "sweep_strips", "pt_exchange"};
 
 // Device words of a context: 8 flags and counters, then the progress
 // counters of strip-resident sweeps (one per CTA, one CTA per SM).
@@ -2103,6 +2103,7 @@ gbmc_status pt_step(gbmc_ctx* ctx, gbmc_pt* pt, uint32_t n_steps) {
         X.n_inst = l->d.n_instances;
         X.inst_base = l->d.instance_base;
         X.round = pt->round++;
+        ProfScope ps_(ctx, PK_PT_EXCHANGE);
         CUDA_TRY(launch_pt_exchange(X, ctx->stream));
     }
     return GBMC_OK;

@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the CPU oracle on a bounded sample) prints
-one JSON line with the keys the result contract names, for a PA workload and
-a single-lattice workload."""
+one JSON line with the keys the result contract names, for a PA workload, a
+single-lattice workload and parallel tempering."""
 import json
 import os
 import subprocess
@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("workload", ["ising2d-L4096-sw", "pa-ising2d-L64-nearest"])
+@pytest.mark.parametrize("workload", ["ising2d-L4096-sw", "pa-ising2d-L64-nearest", "pt-ea3d-L8"])
 def test_reference_arm_json_line(workload):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", workload,
                         "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT)
