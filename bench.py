@@ -298,6 +298,10 @@ def run_gpu(args, w, ws, rank, local):
         lat = gbmc.lattice_init(ctx, w["dim"], w["L"], model=w["model"], n_instances=w["I"], n_replicas=w["T"],
                                 seed=seed0, instance_base=rank * w["I"])
         lats = [lat]
+        tuned = gbmc.gbmc_autotune(ctx, lat, float(pt_betas(w)[w["T"] // 2]), w["theta"])
+        result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
+                            "row_walk": tuned.row_walk, "persistent": tuned.persistent,
+                            "candidates": tuned.n_candidates}
         pts = [gbmc.pt_create(ctx, lat, pt_betas(w), w["theta"])]
 
         def step(k, graph=False):

@@ -253,9 +253,9 @@ gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, 
 /* Launch-shape autotuner for the shared-memory sweep kernel (lattices whose
  * copy fits in one CTA's shared memory). Candidate shapes -- threads per copy
  * (powers of two), copies per CTA, row-wise or flat walk over the words of a
- * colour plane -- are timed with CUDA events on a scratch copy of up to 32768
- * replicas of instance 0 (n_sweeps sweeps at beta, the lattice itself is left
- * unchanged), then the fastest of them once more as a persistent launch, and
+ * colour plane -- are timed with CUDA events on a scratch copy of the first
+ * (up to 32768) copies of the lattice, swept as one instance (n_sweeps sweeps
+ * at beta, the lattice itself is left unchanged), then the fastest of them once more as a persistent launch, and
  * the fastest is recorded for the lattice class (dim, model, L) for the rest
  * of the process. Every shape gives bit-identical results:
  * the random words depend only on (seed, sweep, replica, site). Synchronises.

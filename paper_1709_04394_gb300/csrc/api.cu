@@ -292,8 +292,10 @@ Tuning make_tuning(const gbmc_lattice* l, uint32_t tpr, uint32_t rpc, bool rowwi
     return t;
 }
 
-// Default shape: threads per copy = the power of two covering the copy's
-// units (at most 256), copies per CTA filling 256 threads; or the tuned one.
+// Default shape: threads per copy = the power of two covering a quarter of
+// the copy's units (8..256: about four units per thread and half-sweep, the
+// range the autotuner picks from), copies per CTA filling 256 threads; or the
+// tuned one.
 Tuning tune(const gbmc_lattice* l, bool use_table = true) {
     if (use_table) {
         std::lock_guard<std::mutex> g(g_shape_mu);
@@ -304,7 +306,7 @@ Tuning tune(const gbmc_lattice* l, bool use_table = true) {
     }
     const uint64_t units = units_per_copy(l);
     uint32_t tpr = 8;
-    while (tpr < units && tpr < 256) tpr <<= 1;
+    while (4 * tpr < units && tpr < 256) tpr <<= 1;
     return make_tuning(l, tpr, 256 / tpr, true);
 }
 
@@ -1835,8 +1837,9 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     if (l->d.layout != GBMC_INT8) return GBMC_OK;
     const Tuning def = tune(l, false);
     if (!def.resident) return GBMC_OK;
-    // time on instance 0 with at most 32768 of its replicas, on a scratch copy
-    const uint32_t R = l->d.n_replicas < 32768u ? l->d.n_replicas : 32768u;
+    // time on the first (at most 32768) copies, all instances in order, as one
+    // instance (instance 0's couplings), on a scratch copy
+    const uint32_t R = l->ncopies < 32768u ? (uint32_t)l->ncopies : 32768u;
     const size_t bytes = (size_t)R * l->N;
     int8_t* scratch = nullptr;
     CUDA_TRY(cudaMallocAsync((void**)&scratch, bytes, ctx->stream));
