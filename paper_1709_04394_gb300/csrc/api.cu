@@ -947,6 +947,8 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
     P.dim = (uint32_t)l->d.dim;
     P.R = l->d.n_replicas;
     P.inst_base = l->d.instance_base;
+    if ((P.L & (P.L - 1)) == 0)
+        while ((1u << P.lshift) < P.L) ++P.lshift;
     for (uint32_t u = 0; u < n_updates; ++u) {
         P.t = l->t + u;
         P.labels = u + 1 == n_updates ? labels : nullptr;

@@ -155,6 +155,7 @@ struct SwLaunch {
     uint64_t copy0;
     long long T_bond;         // active iff parallel and u <= T_bond (-1: never)
     uint32_t L, N, dim, R, inst_base, t;
+    uint32_t lshift;          // log2 L when L is a power of two, else 0
 };
 cudaError_t launch_sw_update(const SwLaunch& P, uint64_t copies, cudaStream_t s);
 // Lattices labelled tile by tile (2D: 32 x 32 tiles, 3D: 16 x 8 x 8) need no

@@ -92,11 +92,43 @@ __device__ __forceinline__ void sw_bond_flags(const SwLaunch& P, const int8_t* s
     }
 }
 
-// Whether forward bond mu of site i is active: the same Philox word as in
-// sw_bond_flags (bond b = dim i + mu, call b >> 2, word b & 3).
-__device__ __forceinline__ bool sw_bond_active(const SwLaunch& P, const int8_t* s, uint32_t i, uint32_t mu,
-                                               uint32_t r, uint32_t c3) {
-    const uint32_t b = P.dim * i + mu, j = sw_forward(i, mu, P.L, P.dim);
+// The same flags for sites i0 .. i0 + 3 = x0 .. x0 + 3 of row y, layer z
+// (x0 % 4 == 0, so the four lie in one row): the spins come as 32-bit words
+// (own, right-shifted by one site, row below, layer in front) and bit 1 of
+// byte n of own ^ neighbour says whether site n differs from it (+-1 bytes).
+template <uint32_t DIM>
+__device__ __forceinline__ void sw_bond_flags_row(const SwLaunch& P, const int8_t* s, uint32_t i0, uint32_t x0,
+                                                  uint32_t y, uint32_t z, uint32_t r, uint32_t c3,
+                                                  uint32_t flags[4]) {
+    const uint32_t L = P.L;
+    const uint32_t own = *reinterpret_cast<const uint32_t*>(s + i0);
+    const uint32_t nxt = (uint32_t)(uint8_t)s[i0 - x0 + (x0 + 4 == L ? 0 : x0 + 4)];
+    uint32_t dif[DIM];
+    dif[0] = own ^ ((own >> 8) | (nxt << 24));
+    dif[1] = own ^ *reinterpret_cast<const uint32_t*>(s + (y + 1 == L ? i0 - (L - 1) * L : i0 + L));
+    if constexpr (DIM == 3) {
+        const uint32_t LL = L * L;
+        dif[2] = own ^ *reinterpret_cast<const uint32_t*>(s + (z + 1 == L ? i0 - (L - 1) * LL : i0 + LL));
+    }
+    flags[0] = flags[1] = flags[2] = flags[3] = 0u;
+#pragma unroll
+    for (uint32_t c = 0; c < DIM; ++c) {
+        const uint4 w = philox4x32_10(make_uint4((DIM * i0) / 4 + c, P.t, r, c3), (uint32_t)P.seed,
+                                      (uint32_t)(P.seed >> 32));
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t n = (4 * c + k) / DIM, mu = (4 * c + k) % DIM;
+            const uint32_t u = k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+            if (!((dif[mu] >> (8 * n + 1)) & 1u) && (long long)u <= P.T_bond) flags[n] |= 1u << mu;
+        }
+    }
+}
+
+// Whether forward bond mu of site i, to site j, is active: the same Philox
+// word as in sw_bond_flags (bond b = dim i + mu, call b >> 2, word b & 3).
+__device__ __forceinline__ bool sw_bond_active(const SwLaunch& P, const int8_t* s, uint32_t i, uint32_t j,
+                                               uint32_t mu, uint32_t r, uint32_t c3) {
+    const uint32_t b = P.dim * i + mu;
     if (s[i] != s[j]) return false;
     const uint4 w = philox4x32_10(make_uint4(b >> 2, P.t, r, c3), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     const uint32_t u = (b & 3u) == 0 ? w.x : (b & 3u) == 1 ? w.y : (b & 3u) == 2 ? w.z : w.w;
@@ -167,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaun
     const uint32_t lx = l0 % T.tx, ly = (l0 / T.tx) % T.ty, lz = l0 / (T.tx * T.ty);
     const uint32_t i0 = ((bz * T.tz + lz) * P.L + by * T.ty + ly) * P.L + bx * T.tx + lx;
     uint32_t flags[4];
-    sw_bond_flags<DIM>(P, s, i0, r, c3, flags);
+    sw_bond_flags_row<DIM>(P, s, i0, bx * T.tx + lx, by * T.ty + ly, bz * T.tz + lz, r, c3, flags);
     // runs along x: a site starts a run at x == 0 or where the bond from its
     // left neighbour is inactive. Each site's first parent is the start of its
     // run (a tile row spans TPR lanes of one warp: its run starts form one
@@ -217,25 +249,28 @@ __global__ void __launch_bounds__(256) k_sw_cross(const __grid_constant__ SwLaun
     if (e >= sw_cross_count(P.N, P.dim)) return;
     const SwTile T = sw_tile(P.dim);
     const uint32_t L = P.L, LL = L * L;
-    uint32_t i, mu;
+    uint32_t i, j, mu;
     if (e < P.N / T.tx) {  // (row, tile column) -> x = tx c + tx - 1
-        const uint32_t nc = L / T.tx, row = e / nc;
-        i = row * L + (e - row * nc) * T.tx + T.tx - 1;
+        const uint32_t nc = L / T.tx, row = e / nc, x = (e - row * nc) * T.tx + T.tx - 1;
+        i = row * L + x;
+        j = x + 1 == L ? i - x : i + 1;
         mu = 0;
     } else if ((e -= P.N / T.tx) < P.N / T.ty) {  // (z, tile row k, x) -> y = ty k + ty - 1
-        const uint32_t nk = L / T.ty, x = e % L, rest = e / L, k = rest % nk, z = rest / nk;
-        i = (z * L + k * T.ty + T.ty - 1) * L + x;
+        const uint32_t nk = L / T.ty, rest = e / L, x = e - rest * L, z = rest / nk, y = (rest - z * nk) * T.ty + T.ty - 1;
+        i = (z * L + y) * L + x;
+        j = y + 1 == L ? i - (L - 1) * L : i + L;
         mu = 1;
     } else {  // (tile layer k, y, x) -> z = tz k + tz - 1
         e -= P.N / T.ty;
-        const uint32_t k = e / LL;
-        i = (k * T.tz + T.tz - 1) * LL + (e - k * LL);
+        const uint32_t k = e / LL, z = k * T.tz + T.tz - 1;
+        i = z * LL + (e - k * LL);
+        j = z + 1 == L ? i - (L - 1) * LL : i + LL;
         mu = 2;
     }
     const int8_t* s = P.spins + copy * P.N;
     const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
-    if (sw_bond_active(P, s, i, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst)))
-        sw_unite<true>(P.parent + copy * P.N, i, sw_forward(i, mu, L, P.dim), P.err);
+    if (sw_bond_active(P, s, i, j, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst)))
+        sw_unite<true>(P.parent + copy * P.N, i, j, P.err);
 }
 
 __global__ void __launch_bounds__(256) k_sw_union(const __grid_constant__ SwLaunch P) {
@@ -298,7 +333,17 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
         for (uint32_t n = 0; n < 1024; ++n) {
             const uint32_t p = tpar[cl];
             if (p == cg) break;
-            const uint32_t px = p % L, py = (p / L) % L, pz = p / (L * L);
+            uint32_t px, py, pz;
+            if (P.lshift) {  // L = 2^lshift
+                px = p & (L - 1);
+                py = (p >> P.lshift) & (L - 1);
+                pz = p >> (2 * P.lshift);
+            } else {
+                const uint32_t row = p / L;
+                px = p - row * L;
+                py = row % L;
+                pz = row / L;
+            }
             if (px / T.tx != bx || py / T.ty != by || pz / T.tz != bz) break;
             cl = ((pz - bz * T.tz) * T.ty + (py - by * T.ty)) * T.tx + (px - bx * T.tx);
             cg = p;
