@@ -145,6 +145,20 @@ uint32_t msc_pick_groups(uint32_t N, uint64_t groups, int sms);
 cudaError_t launch_sweep_msc(const SweepLaunch& P, uint32_t n_ctas, uint32_t G, cudaStream_t s);
 
 // Swendsen-Wang update (Sec. 3.3) of `copies` copies of a ferromagnet, in place.
+// (instance, replica) of copy index `copy` with R replicas per instance; a
+// 32-bit division whenever the index fits in 32 bits (a 64-bit one is a long
+// software routine).
+__device__ __forceinline__ void split_copy(uint64_t copy, uint32_t R, uint32_t& inst, uint32_t& r) {
+    if (copy < 0x100000000ull) {
+        const uint32_t c = (uint32_t)copy;
+        inst = c / R;
+        r = c - inst * R;
+    } else {
+        inst = (uint32_t)(copy / R);
+        r = (uint32_t)(copy - (uint64_t)inst * R);
+    }
+}
+
 struct SwLaunch {
     int8_t* spins;            // [copies][N]
     uint8_t* bonds;           // [copies][N] bit mu: forward bond along mu active

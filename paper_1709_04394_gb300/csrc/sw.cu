@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(256) k_sw_bonds(const __grid_constant__ SwLaun
     const int8_t* s = P.spins + copy * P.N;
     uint8_t* bonds = P.bonds + copy * P.N;
     uint32_t* par = P.parent + copy * P.N;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
     uint32_t flags[4];
     sw_bond_flags<DIM>(P, s, i0, r, c3, flags);
@@ -189,7 +190,8 @@ __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaun
     __shared__ uint32_t lp[1024];
     const uint64_t copy = P.copy0 + blockIdx.y;
     const int8_t* s = P.spins + copy * P.N;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
     const SwTile T = sw_tile(DIM);
     const uint32_t ntx = P.L / T.tx, nty = P.L / T.ty;
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(256) k_sw_cross(const __grid_constant__ SwLaun
         mu = 2;
     }
     const int8_t* s = P.spins + copy * P.N;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     if (sw_bond_active(P, s, i, j, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst)))
         sw_unite<true>(P.parent + copy * P.N, i, j, P.err);
 }
@@ -290,7 +293,8 @@ __global__ void __launch_bounds__(256) k_sw_flip(const __grid_constant__ SwLaunc
     if (i >= P.N) return;
     uint32_t* par = P.parent + copy * P.N;
     const uint32_t root = sw_find<true>(par, i);
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     const uint4 w = philox4x32_10(make_uint4(root >> 2, P.t, r, c3_word(kPurposeSwFlip, 0u, P.inst_base + inst)),
                                   (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     const uint32_t word = (root & 3u) == 0 ? w.x : (root & 3u) == 1 ? w.y : (root & 3u) == 2 ? w.z : w.w;
@@ -309,7 +313,8 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
     __shared__ uint32_t troot[1024];  // root of each end node
     __shared__ uint8_t tcoin[1024];   // its coin (1: the cluster flips)
     const uint64_t copy = P.copy0 + blockIdx.y;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     const SwTile T = sw_tile(P.dim);
     const uint32_t L = P.L, ntx = L / T.tx, nty = L / T.ty;
     const uint32_t bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);

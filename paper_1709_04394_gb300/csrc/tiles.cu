@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(256) k_sweep_tiles(const __grid_constant__ Til
     const uint32_t tiles_x = L / T;
     const uint32_t ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
     const uint64_t copy = (uint64_t)P.copy0 + blockIdx.y;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     const int8_t* src = P.src + copy * (uint64_t)L * L;
     int8_t* dst = P.dst + copy * (uint64_t)L * L;
     const uint32_t y0 = (ty * T + L - 8) % L;  // global row of window row 0
@@ -281,7 +282,8 @@ __global__ void __launch_bounds__(NT) k_sweep_dcb(const __grid_constant__ TileLa
     const uint32_t ty = blockIdx.x / half_x;
     const uint32_t tx = 2 * (blockIdx.x - ty * half_x) + ((ty + P.coarse) & 1u);
     const uint64_t copy = (uint64_t)P.copy0 + blockIdx.y;
-    const uint32_t inst = (uint32_t)(copy / P.R), r = (uint32_t)(copy - (uint64_t)inst * P.R);
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
     int8_t* sp = P.dst + copy * (uint64_t)L * L;
     const uint32_t y0 = (ty * T + L - 8) % L;          // global row of window row 0
     const uint32_t xw0 = ((tx * T + L - 8) % L) >> 3;  // global 8-column chunk of window chunk 0
