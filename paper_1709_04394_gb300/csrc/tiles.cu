@@ -120,11 +120,13 @@ constexpr uint32_t kStripThreads = 1024;
 // colour as the previous half-sweep left it: the plain two-phase sweeps of
 // the whole lattice, in place, with no halo recomputation.
 
-// Thread t keeps word column t % W and walks rows t / W + 1, + B/W, ...; the
-// first and last rows (1 and rs) come first each half-sweep, then the others.
-// Before the end of a half-sweep each thread with boundary units waits for the
-// neighbours' half-sweep and refreshes the halo words its next units read, so
-// the half-sweep needs one CTA-wide barrier.
+// Each half-sweep: the threads with boundary units (first and last rows)
+// update them, write them back and meet on a named barrier, after which one
+// thread publishes the half-sweep; then every thread walks its word column
+// (t % W) down the interior rows, B/W rows apart. Two passes into that walk,
+// the boundary threads wait for the neighbours' same half-sweep (lane 0 of
+// each warp polls) and fetch the halo words their next units read. One
+// CTA-wide barrier ends the half-sweep.
 __global__ void __launch_bounds__(kStripThreads, 1) k_sweep_strips(const __grid_constant__ StripLaunch S) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(16) uint32_t s_tbl[8];
