@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kBpStripThreads, 1) k_bp_strips(const __grid_c
         const uint32_t c = k / ((rs + 2) * Wr), rem = k - c * (rs + 2) * Wr, lr = rem / Wr, w = rem - lr * Wr;
         sm[c * ps + lr * Wr + w] = __ldcg(gp + ((uint64_t)c * L + grow(lr)) * Wr + w);
     }
+    if (tid == 0) s_ok = 1;
     __syncthreads();  // all loads done before this CTA publishes anything
     const unsigned int* pu = S.progress + copy * S.Gc + (g == 0 ? S.Gc - 1 : g - 1);
     const unsigned int* pd = S.progress + copy * S.Gc + (g + 1 == S.Gc ? 0 : g + 1);
@@ -236,8 +237,6 @@ __global__ void __launch_bounds__(kBpStripThreads, 1) k_bp_strips(const __grid_c
     // only these warps wait for the neighbours, on named barrier 1; the other
     // warps go straight to the interior rows.
     const uint32_t nb = 2 * Wr, total = rs * Wr;
-    if (tid == 0) s_ok = 1;
-    __syncthreads();
     for (uint32_t h = 0; h < S.n_half; ++h) {
         const uint32_t c = h & 1u;
         uint32_t* own = sm + c * ps;

@@ -174,6 +174,21 @@ __global__ void __launch_bounds__(kStripThreads, 1) k_sweep_strips(const __grid_
             unit_split<2, false, false>(smem, nullptr, L, NL, lr, lr + ydelta, 0, wc, c, pf, tbl, true, e, m,
                                         (y0 + lr - 1) * W + wc);
         };
+        // four rows of the column at a time: all four units are loaded and
+        // updated before any word is stored (rows of one plane: none reads what
+        // another writes)
+        uint32_t* own = pl + c * ps;
+        auto update4 = [&](uint32_t lr) {
+            uint32_t ii[4], vv[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t rk = lr + k * rstep;
+                unit_split<2, false, false, false>(smem, nullptr, L, NL, rk, rk + ydelta, 0, w, c, pf, tbl, true, e,
+                                                   m, (y0 + rk - 1) * W + w, &ii[k], &vv[k]);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) own[ii[k]] = vv[k];
+        };
         // boundary unit k < W: word k of row 1 (next to halo row 0); W + w: word
         // w of row rs (next to rs + 1)
         if (tid < nb) {
@@ -212,6 +227,7 @@ __global__ void __launch_bounds__(kStripThreads, 1) k_sweep_strips(const __grid_
                 pl[c * ps + hr * W + wk] = __byte_perm(v.x, v.y, (gy & 1u) == c ? 0x6420 : 0x7531);
             }
         }
+        for (; lr + 3 * rstep < rs; lr += 4 * rstep) update4(lr);
         for (; lr < rs; lr += rstep) update(lr, w);
         __syncthreads();
         if (!s_ok) return;
