@@ -295,6 +295,8 @@ __global__ void __launch_bounds__(NT) k_sweep_dcb(const __grid_constant__ TileLa
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(16) uint32_t s_tbl[8];
     constexpr uint32_t Wd = T + 16, Wg = Wd >> 3, H = (Wd * Wd) >> 1, Tc = T >> 3;
+    constexpr uint32_t U = T * Tc / NT;  // units per thread and half-sweep (NT is a multiple of Tc)
+    static_assert(NT % Tc == 0 && (T * Tc) % NT == 0 && (U < 4 || U % 4 == 0), "tile / block shape");
     const uint32_t L = P.L, Lw = L >> 3;
     const uint32_t half_x = (L / T) >> 1;
     const uint32_t ty = blockIdx.x / half_x;
@@ -328,12 +330,25 @@ __global__ void __launch_bounds__(NT) k_sweep_dcb(const __grid_constant__ TileLa
     for (uint32_t s = 0; s < 2 * P.nsweeps; ++s) {
         const uint32_t colour = s & 1u, t = P.t0 + (s >> 1);
         const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
-        // interior: window rows [8, 8 + T), chunks [1, 1 + T/8)
-        for (uint32_t u = threadIdx.x; u < T * Tc; u += NT) {
-            const uint32_t rr = u / Tc, g = u - rr * Tc;
-            const uint32_t q = (ty * T + rr) * Lw + tx * Tc + g;
-            unit_split<2, false, false>(smem, nullptr, Wd, Wd * Wd, rr + 8, rr + 8, 0, g + 1, colour, pf, tbl, true,
-                                        e, m, q);
+        // interior: window rows [8, 8 + T), chunks [1, 1 + T/8). Thread t keeps
+        // chunk t % Tc and takes rows t / Tc + i NT/Tc, i < U, four at a time:
+        // all four units are loaded and updated before any word is stored (rows
+        // of one plane: none reads what another writes)
+        uint32_t* own = pl + colour * (H >> 2);
+        const uint32_t g = threadIdx.x % Tc, r0 = threadIdx.x / Tc;
+#pragma unroll
+        for (uint32_t base = 0; base < U; base += 4) {
+            constexpr uint32_t G4 = U < 4 ? U : 4;
+            uint32_t ii[G4], vv[G4];
+#pragma unroll
+            for (uint32_t k = 0; k < G4; ++k) {
+                const uint32_t rr = r0 + (base + k) * (NT / Tc);
+                const uint32_t q = (ty * T + rr) * Lw + tx * Tc + g;
+                unit_split<2, false, false, false>(smem, nullptr, Wd, Wd * Wd, rr + 8, rr + 8, 0, g + 1, colour, pf,
+                                                   tbl, true, e, m, q, &ii[k], &vv[k]);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < G4; ++k) own[ii[k]] = vv[k];
         }
         __syncthreads();
     }
