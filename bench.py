@@ -588,6 +588,24 @@ def cpu_oracle_sample(w):
     return upd / (dt * 1e9), desc, dt
 
 
+def _oracle_worker(w_json):
+    return cpu_oracle_sample(json.loads(w_json))
+
+
+def cpu_oracle_all_cores(w):
+    """The same bounded oracle sample on every host core at once, one process per
+    core started with spawn; returns (aggregate site updates per ns, cores,
+    seconds): the updates of all processes over the longest one's time."""
+    import multiprocessing as mp
+
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_worker, [json.dumps(w)] * n)
+    longest = max(dt for _, _, dt in res)
+    updates = sum(v * dt * 1e9 for v, _, dt in res)
+    return updates / (longest * 1e9), n, longest
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,6 +614,8 @@ def main():
     ap.add_argument("--impl", default="gbmc", choices=["gbmc", "reference"])
     ap.add_argument("--workload", default="pa-ising2d-L64", choices=sorted(WORKLOADS) + ["pa-learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-all-cores", action="store_true",
+                    help="time the oracle on one core only (skip the all-cores run of the same sample)")
     ap.add_argument("--graph", action="store_true",
                     help="population annealing workloads: replay each timed run as one CUDA graph (fixed "
                          "seed; per-kernel times still come from the stream path)")
@@ -747,6 +767,10 @@ def main():
         v, desc, dt = cpu_oracle_sample(w)
         line["cpu_baseline"] = {"value": v, "unit": "spin-flips/ns", "cores": 1, "kind": "oracle", "sample": desc,
                                 "seconds": dt}
+        if not args.no_all_cores:
+            va, na, dta = cpu_oracle_all_cores(w)
+            line["cpu_baseline"]["all_cores"] = {"value": va, "unit": "spin-flips/ns", "cores": na, "seconds": dta,
+                                                 "sample": "the same sample in each of %d processes at once" % na}
     print(json.dumps(line))
 
 

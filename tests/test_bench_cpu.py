@@ -25,3 +25,12 @@ def test_reference_arm_json_line(workload):
     assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == workload
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_all_cores_oracle_timing_runs_one_sample_per_core():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    w = dict(kind="sweeps", dim=2, L=64, sweeps=2, beta=0.44, layout=0)
+    v, cores, seconds = bench.cpu_oracle_all_cores(w)
+    assert cores >= 1 and seconds > 0 and v > 0
