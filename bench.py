@@ -768,9 +768,13 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "spin-flips/ns", "cores": 1, "kind": "oracle", "sample": desc,
                                 "seconds": dt}
         if not args.no_all_cores:
-            va, na, dta = cpu_oracle_all_cores(w)
-            line["cpu_baseline"]["all_cores"] = {"value": va, "unit": "spin-flips/ns", "cores": na, "seconds": dta,
-                                                 "sample": "the same sample in each of %d processes at once" % na}
+            try:
+                va, na, dta = cpu_oracle_all_cores(w)
+                line["cpu_baseline"]["all_cores"] = {
+                    "value": va, "unit": "spin-flips/ns", "cores": na, "seconds": dta,
+                    "sample": "the same sample in each of %d processes at once" % na}
+            except Exception as ex:  # a host without working process pools still gets its line
+                line["cpu_baseline"]["all_cores"] = {"unavailable": "%s: %s" % (type(ex).__name__, ex)}
     print(json.dumps(line))
 
 
