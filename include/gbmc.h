@@ -255,11 +255,14 @@ gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, 
  * (powers of two), copies per CTA, row-wise or flat walk over the words of a
  * colour plane -- are timed with CUDA events on a scratch copy of the first
  * (up to 32768) copies of the lattice, swept as one instance (n_sweeps sweeps
- * at beta, the lattice itself is left unchanged), then the fastest of them once more as a persistent launch, and
- * the fastest is recorded for the lattice class (dim, model, L) for the rest
- * of the process. Every shape gives bit-identical results:
- * the random words depend only on (seed, sweep, replica, site). Synchronises.
- * out->resident = 0 when the lattice uses the global-memory kernel. */
+ * at beta, the lattice itself is left unchanged), then the fastest of them
+ * once more as a persistent launch, and the fastest is recorded for the
+ * lattice class (dim, model, L) for the rest of the process. Untuned classes
+ * use threads per copy = the power of two covering a quarter of a colour's
+ * words (8..256; about four words per thread and half-sweep) in 256-thread
+ * blocks. Every shape gives bit-identical results: the random words depend
+ * only on (seed, sweep, replica, site). Synchronises. out->resident = 0 when
+ * the lattice uses another kernel. */
 typedef struct {
     int32_t resident;
     uint32_t threads_per_copy;
