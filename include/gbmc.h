@@ -95,8 +95,10 @@ gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
  * Every form gives bit-identical results. Persistent launches of one context
  * share its counter, so a context's work must stay on one stream (no two of
  * its sweep launches in flight at once). 2D ferromagnets too large for one
- * thread block's shared memory (int8: L % 256 == 0, L <= 4096; bit-packed:
- * L % 1024 == 0) with at most (SM count / 8) copies: AUTO and PERSISTENT run
+ * thread block's shared memory (int8: L % 256 == 0; bit-packed: L % 1024 ==
+ * 0) with at most (SM count / 8) copies, whose strips of rows (about
+ * L x copies / SM count rows plus two halo rows each) fit in 200 KB of shared
+ * memory (int8 on 152 SMs: L <= 5376 for one copy): AUTO and PERSISTENT run
  * all sweeps of a metropolis_sweeps call without E/M series as one cooperative
  * launch, each thread block keeping a strip of rows in shared memory and
  * trading its first and last rows with its neighbours through global memory
