@@ -34,8 +34,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-N_SMS = 152
-SM_MAX_MHZ = 2070.0
 # Philox4x32-10 per call: 10 rounds x (2 wide products = 4 32-bit multiply
 # halves + 2 three-way xors = 4 xor ops) = 80 integer ops for 4 sites.
 ALG_INT_OPS_PER_SITE_UPDATE = 20.0
@@ -249,7 +247,10 @@ def sweep_lattice(gbmc, ctx, lat, w):
         gbmc.metropolis_sweeps(ctx, lat, w["beta"], w["sweeps"])
 
 
-def run_gpu(args, w, ws, rank, local):
+def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
+    """Warm-up, then the timed region (K steps, uninstrumented), the same K steps
+    again with per-launch CUDA events, and (e2e) the end-to-end pass through
+    the C ABI with host buffers."""
     import torch
 
     from paper_1709_04394_gb300 import build as gbuild
@@ -316,7 +317,11 @@ def run_gpu(args, w, ws, rank, local):
             sweep_lattice(gbmc, ctx, lat, w)
             return site_updates_per_step(w)
 
-    for k in range(args.warmup):
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    props = torch.cuda.get_device_properties(local)
+    result["sm_count"] = props.multi_processor_count
+    for k in range(warmup):
         step(k, args.graph)
     torch.cuda.synchronize()
 
@@ -329,7 +334,7 @@ def run_gpu(args, w, ws, rank, local):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         upd = 0
-        for k in range(args.steps):
+        for k in range(steps):
             # the instrumented pass times every launch on the stream path
             upd += step(first + k, args.graph and not profile)
         e1.record(stream)
@@ -345,20 +350,29 @@ def run_gpu(args, w, ws, rank, local):
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = gbmc.gbmc_kernel_launches()
-    ms_local, _, upd_local = timed(args.warmup, False)
+    ms_local, _, upd_local = timed(warmup, False)
     launches = gbmc.gbmc_kernel_launches() - launches0
     clocks = sampler.stop()
     # the same K steps again with a CUDA event pair around every launch: per-kernel times
-    ms_prof, prof, _ = timed(args.warmup + args.steps, True)
+    ms_prof, prof, upd_prof = timed(warmup + steps, True)
     ms = max_over_ranks(dist, ws, ms_local, device="cuda")
     upd_all = sum_over_ranks(dist, ws, float(upd_local), device="cuda")
     result.update(ms=ms, ms_profiled=ms_prof, prof=prof, launches=launches, clocks=clocks, upd_all=upd_all,
-                  upd_local=upd_local)
+                  upd_local=upd_local, upd_prof=upd_prof, steps=steps, warmup=warmup)
+    if not e2e:
+        if w["kind"] == "pa":
+            gbmc.pa_free(pa)
+        if w["kind"] == "pt":
+            gbmc.pt_free(pts[0])
+        for l in lats:
+            gbmc.lattice_free(l)
+        gbmc.gbmc_destroy(ctx)
+        return result
 
     # end-to-end through the C ABI with host buffers: the population comes in
     # from pinned host memory, and the final population and statistics go back,
     # every step.
-    n_e2e = max(1, min(args.steps, 3))
+    n_e2e = max(1, min(steps, 3))
     hosts_in, hosts_out = [], []
     for i, l in enumerate(lats):
         info = gbmc.lattice_info(l)
@@ -415,7 +429,7 @@ LEARNED = dict(Ls=(32, 64, 128, 256), R=50000, theta=10, beta_f=1.0, target=0.85
                dbeta_max=0.05, cap=4000, bar=1e-4, train_shrink=0.97)
 
 
-def run_learned(args):
+def run_learned(args, seeds=None, plain_steps=None):
     """Time to |f_est - f_exact| <= 1e-4 per spin at beta = 1 for a mixed 2D batch
     (L = 32, 64, 128, 256; R = 5 10^4 each) annealed in one run: plain linear
     schedule (steps doubled until the bar is met), overlap bisection, and the
@@ -425,7 +439,6 @@ def run_learned(args):
     import numpy as np
     import torch
 
-    from oracle import mlp as omlp  # noqa: F401  (parameter count check only)
     from paper_1709_04394_gb300 import build as gbuild
     from paper_1709_04394_gb300 import exact, gbmc
 
@@ -461,7 +474,8 @@ def run_learned(args):
         gbmc.pa_free(pa)
         return dict(seconds=dt, df=df, steps=steps, logs=logs)
 
-    seeds = list(range(101, 101 + args.learned_seeds))
+    seeds = list(range(101, 101 + args.learned_seeds)) if seeds is None else list(seeds)
+    plain_steps = args.plain_steps if plain_steps is None else plain_steps
     # 1. training data from bisection runs of another seed; GPU training
     train = run(gbmc.GBMC_SCHED_BISECTION, 7)
     X, T = [], []
@@ -496,7 +510,7 @@ def run_learned(args):
     acc = float(np.mean([r["kind"] == 2 for run_ in ml_runs for log in run_["logs"] for r in log]))
     plain = None
     plain_tried = []
-    for S in args.plain_steps:
+    for S in plain_steps:
         sm = summary([run(gbmc.GBMC_SCHED_LINEAR, s, S=S) for s in seeds])
         sm["S"] = S
         plain_tried.append(sm)
@@ -522,7 +536,7 @@ def run_learned(args):
             "bisection": {**bis, "meets_bar": met(bis), "meets_bar_every_seed": met_all(bis)},
             "plain_linear": {"cheapest_meeting_bar": plain, "tried": plain_tried},
             "training": {"samples": int(X.shape[0]), "seconds": t_train, "train_run_seconds": train["seconds"]}}
-    print(json.dumps(line))
+    return line
 
 
 def cpu_oracle_sample(w):
@@ -532,25 +546,27 @@ def cpu_oracle_sample(w):
 
     oracle.build()
     if w["kind"] == "pa":
+        # a whole annealing run (every temperature step, beta 0 -> beta_f) of a
+        # reduced population, so that the sample spans the run's range of
+        # acceptance rates; about 1e8 site updates (6-12 s on one core)
         dim, L, model, I, R = w["lattices"][0]
-        Rs = max(1, min(R, (120_000_000 // (L ** dim * w["theta"] * 3))))
-        steps = 3
-        betas = oracle.linear_betas(w["beta_f"], w["S"])[: steps + 1]
+        Rs = max(8, min(R, int(1e8 // (L ** dim * w["theta"] * w["S"]))))
+        betas = oracle.linear_betas(w["beta_f"], w["S"])
         J = oracle.couplings(L, 1, 0) if model == EA else None
         t0 = time.perf_counter()
         if "nearest" in w:
-            Rs = min(Rs, w["nearest"])
             r = oracle.pa_run_nearest(dim, L, 1, 0, Rs, Rs + Rs // 10 + 16, betas, w["theta"], J=J,
                                       poisson=bool(w.get("poisson")))
             upd = int(r["nrep"][1:].sum()) * L ** dim * w["theta"]
             name = "pa_run_nearest (Poisson counts)" if w.get("poisson") else "pa_run_nearest"
         else:
             oracle.pa_run(dim, L, 1, 0, Rs, betas, w["theta"], J=J, msc=bool(w.get("msc")))
-            upd = Rs * L ** dim * w["theta"] * steps
+            upd = Rs * L ** dim * w["theta"] * w["S"]
             name = "pa_run (multi-spin-coded random numbers)" if w.get("msc") else "pa_run"
         dt = time.perf_counter() - t0
-        desc = "oracle %s: dim=%d L=%d, %d replicas (of %d per population), first %d of %d temperature steps, " \
-               "theta=%d" % (name, dim, L, Rs, w.get("nearest", R), steps, w["S"], w["theta"])
+        desc = "oracle %s: dim=%d L=%d, a whole run (all %d temperature steps, beta 0 -> %g, theta=%d) of a " \
+               "population of %d replicas (the workload's has %d); the rate per site update is taken over the " \
+               "whole beta range" % (name, dim, L, w["S"], w["beta_f"], w["theta"], Rs, w.get("nearest", R))
     elif w["kind"] == "pt":
         rounds = 20
         J = oracle.couplings(w["L"], 1, 0) if w["model"] == EA else None
@@ -625,6 +641,9 @@ def main():
     ap.add_argument("--dcb-k", type=int, default=None, help="ising2d-L4096-dcb: sweeps per tile load (default 10)")
     ap.add_argument("--dcb-tile", type=int, default=None, help="ising2d-L4096-dcb: tile size 32, 64 or 128 "
                                                                 "(default 64)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload only: skip the secondary records (configs 2, 4 and the single-seed "
+                         "learned-schedule comparison)")
     ap.add_argument("--learned-seeds", type=int, default=3)
     ap.add_argument("--plain-steps", type=int, nargs="*", default=[250, 500, 1000, 2000, 4000])
     args = ap.parse_args()
@@ -633,7 +652,8 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the time-to-dF comparison is a GPU experiment; "
                                                                   "the oracle reference arm covers the other workloads"}))
             return
-        return run_learned(args)
+        print(json.dumps(run_learned(args)))
+        return
     w = dict(WORKLOADS[args.workload])
     if "dcb" in w and (args.dcb_k or args.dcb_tile):
         k = args.dcb_k or w["dcb"][0]
@@ -644,7 +664,6 @@ def main():
                     "resampling)",
               "pt": "spin-flips/ns (checkerboard Metropolis site updates per ns, parallel tempering incl. "
                     "exchange rounds)"}.get(w["kind"], "spin-flips/ns (checkerboard Metropolis site updates per ns)")
-    upd = site_updates_per_step(w)
     config = {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
               "l2_flush": {"pa": "inputs larger than L2 (2 x 409.6 MB population)",
                            "pt": "none: 16.8 MB of copies, L2-resident between rounds"}.get(
@@ -676,93 +695,25 @@ def main():
         return
 
     res = run_gpu(args, w, ws, rank, local)
+    if not args.no_secondary and args.workload == "pa-ising2d-L64" and not args.graph:
+        secondary = {}
+        for name, (k, wu) in SECONDARY.items():
+            r2 = run_gpu(args, dict(WORKLOADS[name]), ws, rank, local, steps=k, warmup=wu, e2e=False)
+            if rank == 0:
+                secondary[name] = gpu_record(dict(WORKLOADS[name]), name, r2, ws)
     if rank != 0:
         return
-    peaks, peak_src = load_peaks()
-    ms = res["ms"]
-    value = res["upd_all"] / (ms * 1e6)  # site updates per ns, all ranks
-    upd_step = res["upd_local"] / args.steps  # this rank's updates per step (variable populations: measured)
-    prof = res["prof"]
-    # dominant kernel: the sweep kernel of the workload
-    kname = ("sweep_msc" if w.get("msc") else "sweep_resident") if w["kind"] in ("pa", "pt") else \
-        (("bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep") if w.get("layout", 0) == 1 else
-         ("sweep_dcb" if "dcb" in w else ("swendsen_wang" if w.get("sw") else
-                                          ("sweep_strips" if "sweep_strips" in prof else "sweep_tiles"))))
-    n_l, t_l = prof.get(kname, (0, 0.0))
-    if w.get("sw"):
-        n_l //= 3  # one update = bond, union and flip launches
-    avg_ms = t_l / n_l if n_l else float("nan")
-    if w["kind"] == "pa":
-        # variable populations: the mean population of the timed runs
-        live = [upd_step / (w["S"] * w["theta"] * l[1] ** l[0]) if "nearest" in w else copies(l) for l in w["lattices"]]
-        upd_per_launch = sum(n * l[1] ** l[0] for n, l in zip(live, w["lattices"])) * w["theta"]
-        hbm_bytes_per_launch = sum(n * (2 * l[1] ** l[0] + 12) for n, l in zip(live, w["lattices"]))
-    elif w["kind"] == "pt":
-        upd_per_launch = w["I"] * w["T"] * w["L"] ** w["dim"] * w["theta"]  # theta sweeps of every copy
-        hbm_bytes_per_launch = w["I"] * w["T"] * 2 * w["L"] ** w["dim"]
-    elif w.get("sw"):
-        upd_per_launch = w["L"] ** w["dim"]                 # one Swendsen-Wang update (three launches)
-        hbm_bytes_per_launch = w["L"] ** w["dim"] * SW_BYTES_PER_SITE
-    elif "dcb" in w:
-        k, tile = w["dcb"]
-        upd_per_launch = w["L"] ** 2 // 2 * k               # one coarse colour of tiles, k sweeps each
-        hbm_bytes_per_launch = w["L"] ** 2 // 2 * ((tile + 16) ** 2 + tile ** 2) // tile ** 2  # window in, tile out
-    elif kname == "sweep_strips":
-        upd_per_launch = w["L"] ** w["dim"] * w["sweeps"]  # every sweep of the call in one launch
-        hbm_bytes_per_launch = 2 * w["L"] ** w["dim"]      # the int8 lattice read and written once
-    elif kname == "bitpack_strips":
-        upd_per_launch = w["L"] ** w["dim"] * w["sweeps"]  # every sweep of the call in one launch
-        hbm_bytes_per_launch = w["L"] ** w["dim"] // 4     # the packed lattice read and written once
-    elif w.get("layout", 0) == 1:
-        upd_per_launch = w["L"] ** w["dim"] // 2          # one colour per launch
-        hbm_bytes_per_launch = w["L"] ** w["dim"] * 3 // 16  # read both planes, write one (bits)
-    else:
-        upd_per_launch = w["L"] ** w["dim"] * 4            # 4 sweeps per tiled launch
-        hbm_bytes_per_launch = w["L"] ** w["dim"] * 2 * (144 * 144) // (128 * 128)  # window in, interior out
-    alg_ops = ALG_INT_OPS_PER_MSC_UPDATE if w.get("msc") else ALG_INT_OPS_PER_SITE_UPDATE
-    ops = alg_ops * upd_per_launch
-    achieved = ops / (avg_ms * 1e-3) / 1e9  # Gop/s
-    clk = res["clocks"]
-    peak_alu = N_SMS * 4 * 32 * SM_MAX_MHZ * 1e6 / 1e9  # Gop/s: one warp instruction per SMSP per cycle
-    hbm_gbs = hbm_bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    total_ms = sum(t for _, t in prof.values())
-    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
-            "frac": achieved / peak_alu,
-            "peak_source": "derived: 152 SMs x 4 SMSP x 32 lanes x 2070 MHz (one integer warp instruction per SMSP "
-                           "per cycle)",
-            "alg_ops_per_site_update": alg_ops}
-    if w.get("sw"):
-        # cluster updates: bytes per update against the measured copy bandwidth
-        roof = {"bound": "hbm", "kernel": kname, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                "alg_bytes_per_site_update": SW_BYTES_PER_SITE}
-    line = {
-        "metric": metric, "value": value, "unit": "spin-flips/ns", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int8 spins / int32 energies / f64 weights", "data": "synthetic",
-        "config": config,
-        "replica_sweeps_per_s": (res["upd_all"] / (w["lattices"][0][1] ** w["lattices"][0][0]) / (ms * 1e-3))
-        if w["kind"] == "pa" and len(w["lattices"]) == 1 else None,
-        "roofline": {**roof,
-                     "traffic": recorded_traffic(None, copies(w["lattices"][0]))
-                     if args.workload == "pa-ising2d-L64" else None,
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                     "scaled by replicas from profiles/sweep_resident_traffic.json)",
-                     "avg_launch_ms": avg_ms, "launches": n_l,
-                     "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
-                     "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,
-                     "kernel_share": t_l / total_ms if total_ms else None},
-        "kernels": {k: {"launches": n, "total_ms": t} for k, (n, t) in prof.items()},
-        "kernel_times_note": "per-kernel CUDA-event times come from a second, instrumented pass over the same K "
-                             "steps (%.1f ms vs %.1f ms uninstrumented)" % (res["ms_profiled"], ms),
-        "autotuned_shape": res.get("tuning"),
-        "gpu_launches": res["launches"],
-        "clocks": clk,
-    }
+    line = gpu_record(w, args.workload, res, ws)
+    line["metric"] = metric
+    line["config"] = config
+    upd_step = res["upd_local"] / res["steps"]
     e = res["e2e"]
-    e2e_upd = upd_step
-    line["e2e"] = {"value": ws * e2e_upd / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
+    line["e2e"] = {"value": ws * upd_step / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"]}
+    if not args.no_secondary and args.workload == "pa-ising2d-L64" and not args.graph:
+        line["secondary"] = secondary
+        if ws == 1:
+            line["secondary"]["pa-learned"] = run_learned(args, seeds=[101], plain_steps=[2000])
     if not args.no_cpu_baseline:
         v, desc, dt = cpu_oracle_sample(w)
         line["cpu_baseline"] = {"value": v, "unit": "spin-flips/ns", "cores": 1, "kind": "oracle", "sample": desc,
@@ -772,10 +723,126 @@ def main():
                 va, na, dta = cpu_oracle_all_cores(w)
                 line["cpu_baseline"]["all_cores"] = {
                     "value": va, "unit": "spin-flips/ns", "cores": na, "seconds": dta,
-                    "sample": "the same sample in each of %d processes at once" % na}
+                    "sample": "the same sample in each of %d processes at once (aggregate throughput of %d "
+                              "independent runs)" % (na, na)}
             except Exception as ex:  # a host without working process pools still gets its line
                 line["cpu_baseline"]["all_cores"] = {"unavailable": "%s: %s" % (type(ex).__name__, ex)}
     print(json.dumps(line))
+
+
+# Secondary records of the default run: the other configurations of the path,
+# (timed steps, warm-up steps) each, so that the whole default run stays within
+# a few minutes.
+SECONDARY = {
+    "ising2d-L4096": (10, 3),
+    "ising2d-L4096-bitpack": (10, 3),
+    "pa-ea3d-L8": (3, 3),
+    "pa-mixed-2d": (3, 3),
+}
+
+
+def kernel_name(w, prof):
+    """The dominant kernel of a workload (its profiling kind)."""
+    if w["kind"] in ("pa", "pt"):
+        if w.get("msc"):
+            return "sweep_msc"
+        return "sweep_bits" if "sweep_bits" in prof else "sweep_resident"
+    if w.get("layout", 0) == 1:
+        return "bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep"
+    if "dcb" in w:
+        return "sweep_dcb"
+    if w.get("sw"):
+        return "swendsen_wang"
+    return "sweep_strips" if "sweep_strips" in prof else "sweep_tiles"
+
+
+def alg_bytes_per_update(w, kname):
+    """Algorithmic HBM bytes per site update of the dominant kernel."""
+    if w["kind"] == "pa":
+        # per launch each copy is read (through the parent map) and written once, plus E, M, parent
+        tot_upd = sum(copies(l) * l[1] ** l[0] for l in w["lattices"])
+        tot_bytes = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
+        return tot_bytes / (tot_upd * w["theta"])
+    if w["kind"] == "pt":
+        return 2.0 / w["theta"]
+    if w.get("sw"):
+        return float(SW_BYTES_PER_SITE)
+    if "dcb" in w:
+        k, tile = w["dcb"]
+        return ((tile + 16) ** 2 + tile ** 2) / tile ** 2 / k   # window in, tile out, per k sweeps
+    if kname == "sweep_strips":
+        return 2.0 / w["sweeps"]                               # the int8 lattice read and written once per call
+    if kname == "bitpack_strips":
+        return 0.25 / w["sweeps"]                              # the packed lattice read and written once per call
+    if kname == "bitpack_halfsweep":
+        return 3.0 / 8.0                                       # both planes read, one written per half-sweep
+    return 2.0 * (144 * 144) / (128 * 128) / 4                 # halo tiles: window in, interior out, 4 sweeps
+
+
+def gpu_record(w, workload, res, ws):
+    """The bench line of one GPU workload from run_gpu's result (rank 0)."""
+    peaks, peak_src = load_peaks()
+    ms, steps = res["ms"], res["steps"]
+    value = res["upd_all"] / (ms * 1e6)  # site updates per ns, all ranks
+    prof = res["prof"]
+    kname = kernel_name(w, prof)
+    n_l, t_l = prof.get(kname, (0, 0.0))
+    if w.get("sw"):
+        n_l //= 3  # one update = bond, union and flip launches
+    # launches that updated sites: every PA run has one measurement-only launch (step 0)
+    n_sweeping = n_l * w["S"] // (w["S"] + 1) if w["kind"] == "pa" else n_l
+    upd = res["upd_prof"]  # site updates of the profiled pass, all made by the dominant kernel
+    secs = t_l * 1e-3
+    alg_ops = ALG_INT_OPS_PER_MSC_UPDATE if w.get("msc") else ALG_INT_OPS_PER_SITE_UPDATE
+    achieved = alg_ops * upd / secs / 1e9 if secs else float("nan")  # Gop/s
+    hbm_gbs = alg_bytes_per_update(w, kname) * upd / secs / 1e9 if secs else float("nan")
+    clk = res["clocks"]
+    sms = res["sm_count"]
+    max_mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    med_mhz = clk.get("sm_mhz") or max_mhz
+    peak_alu = sms * 4 * 32 * max_mhz * 1e6 / 1e9  # Gop/s: one warp instruction per SMSP per cycle
+    total_ms = sum(t for _, t in prof.values())
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_alu, "unit": "Gop/s",
+            "frac": achieved / peak_alu,
+            "peak_source": "derived: %d SMs (device) x 4 SMSP x 32 lanes x %.0f MHz (maximum SM clock, nvidia-smi) "
+                           "= one integer warp instruction per SMSP per cycle" % (sms, max_mhz),
+            "peak_at_sampled_clock": sms * 4 * 32 * med_mhz * 1e6 / 1e9,
+            "frac_at_sampled_clock": achieved / (sms * 4 * 32 * med_mhz * 1e6 / 1e9),
+            "alg_ops_per_site_update": alg_ops}
+    if w.get("sw"):
+        # cluster updates: bytes per update against the measured copy bandwidth
+        roof = {"bound": "hbm", "kernel": kname, "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, of "
+                                                                          "%s)" % peak_src,
+                "alg_bytes_per_site_update": SW_BYTES_PER_SITE}
+    traffic = None
+    if workload == "pa-ising2d-L64":
+        traffic = recorded_traffic(kname, copies(w["lattices"][0]))
+    return {
+        "metric": "spin-flips/ns", "value": value, "unit": "spin-flips/ns", "n_gpus": ws, "steps": steps,
+        "warmup": res["warmup"], "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8 spins / int32 energies / f64 weights", "data": "synthetic",
+        "config": {"workload": workload, **{k: v for k, v in w.items() if k != "kind"}},
+        "replica_sweeps_per_s": (res["upd_all"] / (w["lattices"][0][1] ** w["lattices"][0][0]) / (ms * 1e-3))
+        if w["kind"] == "pa" and len(w["lattices"]) == 1 else None,
+        "roofline": {**roof,
+                     "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                     "scaled by replicas from the committed ncu record)",
+                     "avg_launch_ms": t_l / n_sweeping if n_sweeping else None, "launches": n_l,
+                     "sweeping_launches": n_sweeping,
+                     "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
+                     "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,
+                     "kernel_share": t_l / total_ms if total_ms else None},
+        "kernels": {k: {"launches": n, "total_ms": t} for k, (n, t) in prof.items()},
+        "kernel_times_note": "per-kernel CUDA-event times come from a second, instrumented pass over the same K "
+                             "steps (%.1f ms vs %.1f ms uninstrumented); roofline.achieved = algorithmic ops of "
+                             "every update the pass made / the dominant kernel's summed launch time" % (
+                                 res["ms_profiled"], ms),
+        "autotuned_shape": res.get("tuning"),
+        "gpu_launches": res["launches"],
+        "clocks": clk,
+    }
 
 
 if __name__ == "__main__":

@@ -480,11 +480,11 @@ gbmc_status mlp_train(gbmc_ctx *ctx, float *params, const float *X, const float 
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free resampling. The paper has no counterpart: this entry point */
-/* exists for callers that cannot allocate device memory -- work being       */
-/* captured into a CUDA graph (where cudaMalloc is not allowed), processes   */
+/* exists for callers that must not allocate device memory -- processes      */
 /* whose device memory belongs to another allocator or pool that must not be */
-/* bypassed, and embedded or real-time drivers that reserve all memory at    */
-/* start-up.                                                                   */
+/* bypassed or fragmented, embedded or real-time drivers that reserve all    */
+/* memory at start-up, and latency-critical code that cannot take the        */
+/* implicit device-wide synchronisation of cudaMalloc / cudaFree.            */
 /* ------------------------------------------------------------------------ */
 /* One resampling step of population annealing for n_instances populations of
  * n_replicas replicas each, identical to the resampling inside pa_step (same
@@ -506,12 +506,16 @@ gbmc_status mlp_train(gbmc_ctx *ctx, float *params, const float *X, const float 
  *     so invalid input gives meaningless parents but no out-of-range access).
  *   parent_dev: device uint32 [n_instances][n_replicas] out: slot -> replica
  *     (within its instance) it copies; children contiguous, parents in order.
- *   lnQ_dev: device double [n_instances] out: ln Q_i of Eq. (13).
+ *   lnQ_dev: device double [n_instances] out: per population, the log of the
+ *     mean Boltzmann reweighting factor exp(-dbeta E) of its replicas.
  * Limits (GBMC_ERR_ARG beyond them): n_instances * n_replicas <= 131072,
  * n_instances <= 1024, dim*n_sites/2 + 1 <= 65537, n_instances *
  * (dim*n_sites/2 + 1) <= 524288.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture. Every call
+ * The weight tables are computed on the host and copied from host memory on
+ * every call (the host buffer is free again when the call returns). The first
+ * call on a device (and the first after its context was reset) looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture. Every call
  * shares the one array and it keeps the last call's contents (each call
  * clears what must start at zero), so calls whose work overlaps on the GPU
  * -- on different streams, or from different host threads -- race and give

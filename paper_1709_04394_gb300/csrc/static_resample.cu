@@ -1,15 +1,19 @@
 // static_resample.cu -- pa_resample_static: the population-annealing
 // resampling step for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph
-// capture region, host code whose device memory is owned by another
-// allocator (a memory pool that must not be fragmented or bypassed), or
-// embedded drivers that reserve all memory up front. This entry point gives
-// them the same resampling as pa_step (same kernels, same results) using a
-// fixed scratch area that is part of the library image: a file-scope
-// __device__ array of kStaticScratchBytes, which every GPU that loads the
-// library holds until the process exits. The caller passes the energies in
-// and receives the parent map and ln Q.
+// Some callers must not call cudaMalloc: processes whose device memory belongs
+// to another allocator (a framework's memory pool that has reserved the
+// device and must not be bypassed or fragmented), embedded or real-time
+// drivers that reserve all memory at start-up and forbid allocation later,
+// and code on a latency-critical path where the implicit device-wide
+// synchronisation of cudaMalloc / cudaFree would stall other streams. This
+// entry point gives them the same resampling as pa_step (same kernels, same
+// results) using a fixed scratch area that is part of the library image: a
+// file-scope __device__ array of kStaticScratchBytes, which every GPU that
+// loads the library holds until the process exits. The caller passes the
+// energies in and receives the parent map and ln Q.
+#include <cuda.h>
+
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -86,11 +90,47 @@ gbmc_status static_fail(gbmc_status st, const char* msg, cudaError_t e = cudaSuc
     return st;
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (in host code the array's name is only a host-side handle).
+// Device address of the scratch array and the SM count, looked up with the
+// device current (in host code the array's name is only a host-side handle,
+// not a device address). The address belongs to the device's current context:
+// it is cached together with that context's id (unique for the life of the
+// process) and looked up again when the id changes, e.g. after the primary
+// context was reset and the library's module was loaded anew.
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {};
+struct DevScratch {
+    unsigned long long ctx_id;
+    void* addr;
+    int sms;
+};
+DevScratch g_dev[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context, through the driver entry points
+// the runtime hands out (no link-time dependence on the driver library).
+cudaError_t current_ctx_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static cudaError_t status = cudaErrorUnknown;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        status = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (status == cudaSuccess)
+            status = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (status == cudaSuccess && (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess))
+            status = cudaErrorSymbolNotFound;
+        get_current = (CtxGetCurrentFn)f1;
+        get_id = (CtxGetIdFn)f2;
+    });
+    if (status != cudaSuccess) return status;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr || get_id(c, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 // Host staging of the weight tables (copied to the device before returning).
 double g_host_wexp[kStaticMaxBins];
@@ -122,15 +162,25 @@ extern "C" gbmc_status pa_resample_static(void* cuda_stream, int32_t device, int
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "cudaSetDevice", e);
     unsigned char* base = nullptr;
+    int sms = 0;
     {
         std::lock_guard<std::mutex> g(g_addr_mu);
-        if (!g_addr[device]) {
+        unsigned long long id = 0;
+        if ((e = current_ctx_id(&id)) != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "current context", e);
+        DevScratch& d = g_dev[device];
+        if (!d.addr || d.ctx_id != id) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_static_scratch);
             if (e != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "cudaGetSymbolAddress", e);
-            g_addr[device] = p;
+            int n = 0;
+            e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+            if (e != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "SM count", e);
+            d.addr = p;
+            d.sms = n > 0 ? n : 1;
+            d.ctx_id = id;
         }
-        base = (unsigned char*)g_addr[device];
+        base = (unsigned char*)d.addr;
+        sms = d.sms;
     }
 
     PaLattice P;
@@ -173,7 +223,7 @@ extern "C" gbmc_status pa_resample_static(void* cuda_stream, int32_t device, int
             g_host_wexp[b] = w;
             g_host_wint[b] = (unsigned long long)std::floor(std::ldexp(w, s_bits));
         }
-        // pageable source: returns once the host arrays have been staged
+        // pageable source: the copy has taken the host arrays when the call returns
         e = cudaMemcpyAsync(base + kOffWexp, g_host_wexp, 8 * nbins, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(base + kOffWint, g_host_wint, 8 * nbins, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "table upload", e);
@@ -185,7 +235,7 @@ extern "C" gbmc_status pa_resample_static(void* cuda_stream, int32_t device, int
     if ((e = launch_pa_reset(P, s)) != cudaSuccess) return static_fail(GBMC_ERR_CUDA, "reset", e);
     {
         uint64_t blocks = (total + 255) / 256;
-        if (blocks > 152ull * 16) blocks = 152ull * 16;
+        if (blocks > 16ull * (uint64_t)sms) blocks = 16ull * (uint64_t)sms;
         k_static_stats<<<(uint32_t)blocks, 256, 0, s>>>(E_dev, (int32_t*)(base + kOffE), total, n_replicas, P.e_lo,
                                                         P.nbins, P.hist, P.emin, P.emax);
         count_launch();

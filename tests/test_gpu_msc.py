@@ -86,7 +86,8 @@ def test_pa_msc_with_nearest_integer_resampling(ctx):
 def test_full_size_pa_msc_l64_r100000_sampled(ctx):
     # the benchmark population, multi-spin-coded sweeps: exact resampling of the
     # whole population and theta sweeps on sampled slots
-    _sampled_full_size_check(ctx, 2, 64, gbmc.GBMC_ISING_FM, 1, 100000, 10, 100, 1.0, 2, 24, 5, sweep_rng=MSC)
+    _sampled_full_size_check(ctx, 2, 64, gbmc.GBMC_ISING_FM, 1, 100000, 10, 100, 1.0, (1, 2, 99, 100), 24, 5,
+                             sweep_rng=MSC)
 
 
 def test_msc_rejects_unsupported_lattices(ctx):

@@ -116,24 +116,32 @@ def test_pa_step_by_step_equals_run(ctx):
     gbmc.lattice_free(l2)
 
 
-def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps, n_samples, seed,
+def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, check_steps, n_samples, seed,
                              sweep_rng=gbmc.GBMC_RNG_PHILOX):
     """Full-size population: exact check of the resampling (oracle on the whole
-    energy array) and of theta sweeps on sampled slots, for the first steps."""
+    energy array: every parent, ln Q) and of theta sweeps on sampled slots, at
+    the annealing steps in `check_steps` (the steps in between run unchecked,
+    their ln Z taken from the library's record)."""
     lat = gbmc.lattice_init(ctx, dim, L, model=model, n_instances=I, n_replicas=R, seed=seed)
     pa = gbmc.pa_create(ctx, [lat], theta, S, beta_f=beta_f, sweep_rng=sweep_rng)
     sweeps = oracle.msc_sweeps if sweep_rng == gbmc.GBMC_RNG_MSC else oracle.sweeps
     N = L ** dim
     betas = oracle.linear_betas(beta_f, S)
     E = np.empty(I * R, dtype=np.int32)
-    gbmc.pa_energies_out(ctx, pa, 0, E)
     lnZ = np.full(I, N * math.log(2.0))
     rng = np.random.default_rng(0)
     Js = [oracle.couplings(L, seed, i) if model == gbmc.GBMC_EA_PMJ else None for i in range(I)]
-    for step in range(1, n_steps + 1):
+    done = 0
+    for step in sorted(check_steps):
+        while done < step - 1:
+            row = gbmc.pa_step(ctx, pa)
+            done += 1
+            lnZ = np.array([row[i]["lnZ"] for i in range(I)])
+        gbmc.pa_energies_out(ctx, pa, 0, E)
         prev = spins_out(ctx, lat).reshape(I, R, N)
         Eprev = E.reshape(I, R).astype(np.int64)
         row = gbmc.pa_step(ctx, pa)
+        done += 1
         par = np.empty(I * R, dtype=np.uint32)
         gbmc.pa_parents_out(ctx, pa, 0, par)
         par = par.reshape(I, R)
@@ -142,6 +150,7 @@ def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps
         for i in range(I):
             counts, lnQ = oracle.resample(Eprev[i], betas[step] - betas[step - 1], seed, i, step)
             np.testing.assert_array_equal(par[i], oracle.children_order(counts))
+            assert row[i]["lnQ"] == pytest.approx(lnQ, rel=RTOL, abs=1e-13)
             lnZ[i] += lnQ
             assert row[i]["lnZ"] == pytest.approx(lnZ[i], rel=RTOL)
             assert row[i]["sumE"] == int(E.reshape(I, R)[i].astype(np.int64).sum())
@@ -156,13 +165,16 @@ def _sampled_full_size_check(ctx, dim, L, model, I, R, theta, S, beta_f, n_steps
 
 
 def test_full_size_pa_2d_l64_r100000_sampled(ctx):
-    # population annealing 2D Ising L = 64, R = 10^5, beta 0 -> 1 in 101 temperatures, theta = 10
-    _sampled_full_size_check(ctx, 2, 64, gbmc.GBMC_ISING_FM, 1, 100000, 10, 100, 1.0, 2, 24, 1)
+    # population annealing 2D Ising L = 64, R = 10^5, beta 0 -> 1 in 101 temperatures, theta = 10:
+    # the first two steps and the last two (beta = 0.99, 1.0: energies near the ground state, the
+    # weights spanning most of their range)
+    _sampled_full_size_check(ctx, 2, 64, gbmc.GBMC_ISING_FM, 1, 100000, 10, 100, 1.0, (1, 2, 99, 100), 24, 1)
 
 
 def test_full_size_pa_3d_ea_32x20000_sampled(ctx):
-    # 3D +-J spin glass L = 8, 32 instances x 2 10^4 replicas, beta 0 -> 3 in 201 temperatures, theta = 10
-    _sampled_full_size_check(ctx, 3, 8, gbmc.GBMC_EA_PMJ, 32, 20000, 10, 200, 3.0, 2, 24, 5)
+    # 3D +-J spin glass L = 8, 32 instances x 2 10^4 replicas, beta 0 -> 3 in 201 temperatures, theta = 10;
+    # steps 1, 2 and 199, 200 (beta = 2.985, 3.0)
+    _sampled_full_size_check(ctx, 3, 8, gbmc.GBMC_EA_PMJ, 32, 20000, 10, 200, 3.0, (1, 2, 199, 200), 24, 5)
 
 
 def test_full_size_pa_mixed_2d_sampled(ctx):
