@@ -107,6 +107,18 @@ gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
  * launch per half-sweep). Unknown mode: GBMC_ERR_ARG. */
 enum { GBMC_LAUNCH_AUTO = 0, GBMC_LAUNCH_GRID = 1, GBMC_LAUNCH_PERSISTENT = 2 };
 gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
+/* Kernel of the resident sweeps (checkerboard sweeps of copies held on chip,
+ * Sec. 3.1). BYTES: one byte per spin in colour planes (any lattice whose copy
+ * fits in a thread block's shared memory). BITS: one bit per spin, 32 sites of
+ * a colour per word (the multi-spin coding of sites of Sec. 3.1 applied to the
+ * copy on chip; the population stays in the int8 layout in device memory and
+ * is converted on load and store), for 2D ferromagnets with L in {64, 128,
+ * 256} and 3D lattices (ferromagnet or +-J) with L = 8; other lattices of the
+ * same call take the BYTES kernel. AUTO (default): BITS for a supported lattice
+ * class unless gbmc_autotune timed BYTES faster for it. All give bit-identical
+ * results (same Philox words per site). Unknown kernel: GBMC_ERR_ARG. */
+enum { GBMC_KERNEL_AUTO = 0, GBMC_KERNEL_BYTES = 1, GBMC_KERNEL_BITS = 2 };
+gbmc_status gbmc_set_sweep_kernel(gbmc_ctx *ctx, int32_t kernel);
 /* Test aid for the bounded waits: each grid barrier of the fused resampling
  * waits for `phantom_arrivals` CTAs more than the launch has, and each
  * neighbour wait of the strip-resident sweeps for that many half-sweeps more
@@ -259,7 +271,8 @@ gbmc_status observables(gbmc_ctx *ctx, const gbmc_lattice *lat, int32_t *E_dev, 
  * (up to 32768) copies of the lattice, swept as one instance (n_sweeps sweeps
  * at beta, the lattice itself is left unchanged), then the fastest of them
  * once more as a persistent launch, and the fastest is recorded for the
- * lattice class (dim, model, L) for the rest of the process. Untuned classes
+ * lattice class (dim, model, L) for the rest of the process; for the classes
+ * the bit-sliced kernel supports it is timed too (kernel). Untuned classes
  * use threads per copy = the power of two covering a quarter of a colour's
  * words (8..256; about four words per thread and half-sweep) in 256-thread
  * blocks. Every shape gives bit-identical results: the random words depend
@@ -273,12 +286,16 @@ typedef struct {
     double ms_per_sweep;      /* best time of one sweep of the timed replicas */
     uint32_t n_candidates;
     int32_t persistent;       /* 1: persistent launch (gbmc_set_sweep_launch) */
+    int32_t kernel;           /* GBMC_KERNEL_BITS: the bit-sliced kernel was fastest (gbmc_set_sweep_kernel);
+                                 GBMC_KERNEL_BYTES: the byte-plane shape above */
 } gbmc_tuning;
 gbmc_status gbmc_autotune(gbmc_ctx *ctx, const gbmc_lattice *lat, double beta, uint32_t n_sweeps,
                           gbmc_tuning *out);
 /* Force (shape != NULL) or clear (NULL) the shape of a lattice class; used by
  * tests to check that every shape gives the same spins. threads_per_copy: a
- * power of two <= 256; copies_per_cta in 1..64 with product <= 256. */
+ * power of two <= 256; copies_per_cta in 1..64 with product <= 256; kernel
+ * GBMC_KERNEL_BITS selects the bit-sliced kernel in AUTO mode, anything else
+ * the byte-plane shape. */
 gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tuning *shape);
 
 /* ------------------------------------------------------------------------ */
@@ -433,6 +450,26 @@ gbmc_status pa_parents_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, u
  * (device or host int32 [n_copies]). */
 gbmc_status pa_energies_out(gbmc_ctx *ctx, const gbmc_pa *pa, uint32_t lattice, int32_t *E_dst,
                             int32_t *M_dst, size_t count);
+
+/* Checkpoint and resume of an annealing run between steps. The random numbers
+ * are a function of (seed, step, sweep, replica, site) only (Sec. 4,
+ * counter-based generators), so a run continued from a saved state is
+ * bit-identical to the uninterrupted run. The state holds the step index,
+ * every lattice's seed, sweep counters, temperatures reached and schedule log,
+ * ln Z, the energies, magnetisations, energy histogram and range of the
+ * current population, the population sizes (variable-population laws) and the
+ * step records; the spins are not part of it (lattice_copy_out before saving,
+ * lattice_copy_in after loading).
+ * pa_state_bytes: size of the state as it is now (adaptive schedules grow it
+ * step by step). pa_state_save: writes it into host memory of exactly that
+ * size; synchronises. pa_state_load: restores it into a run created by
+ * pa_create with the same configuration on lattices of the same shapes
+ * (GBMC_ERR_ARG otherwise, leaving the run unchanged); then copy the saved
+ * configuration in with lattice_copy_in and continue with pa_step / pa_run.
+ * Synchronises. The format is this library's own (host byte order). */
+gbmc_status pa_state_bytes(const gbmc_pa *pa, size_t *bytes);
+gbmc_status pa_state_save(gbmc_ctx *ctx, const gbmc_pa *pa, void *host, size_t bytes);
+gbmc_status pa_state_load(gbmc_ctx *ctx, gbmc_pa *pa, const void *host, size_t bytes);
 
 /* ------------------------------------------------------------------------ */
 /* Parallel tempering (Sec. 5.1, Eq. (10)), on the same sweep kernel: each    */

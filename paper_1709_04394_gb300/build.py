@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbmc.so")
-SOURCES = ["api.cu", "sweep.cu", "tiles.cu", "msc.cu", "sw.cu", "pa.cu", "lattice.cu", "static_resample.cu", "schedule.cu", "mlp.cu", "bitpack.cu", "pt.cu"]
+SOURCES = ["api.cu", "sweep.cu", "bitsweep.cu", "tiles.cu", "msc.cu", "sw.cu", "pa.cu", "lattice.cu", "static_resample.cu", "schedule.cu", "mlp.cu", "bitpack.cu", "pt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"] if os.environ.get("GBMC_PTXAS_VERBOSE") else \

@@ -50,13 +50,14 @@ std::atomic<uint64_t> g_launches{0};
 enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
-    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_COUNT
+    PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_SWEEP_BITS,
+    PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
                                           "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
-                                          "bitpack_strips", "sweep_strips", "pt_exchange"};
+                                          "bitpack_strips", "sweep_strips", "pt_exchange", "sweep_bits"};
 
 // Device words of a context: 8 flags and counters, then the progress
 // counters of strip-resident sweeps (one per CTA, one CTA per SM).
@@ -81,6 +82,7 @@ struct gbmc_ctx {
     bool fused = true;              // one cooperative resampling launch per lattice and step
     bool coop = false;              // the device supports cooperative launches
     int32_t launch_mode = GBMC_LAUNCH_AUTO;  // grid or persistent resident sweeps
+    int32_t sweep_kernel = GBMC_KERNEL_AUTO; // bit-sliced or byte-plane resident sweeps
     uint32_t phantom = 0;           // test hook: extra barrier arrivals to wait for
     long long budget = 2000000000;  // cycles a barrier wait may last (about 1 s)
     bool prof = false;
@@ -140,6 +142,7 @@ struct gbmc_lattice {
     int8_t* cur;       // buffer holding the current configuration
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
     uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
+    uint32_t* jb3;     // the same bonds as bit words of the bit-sliced 3D L = 8 sweep [inst][2][6][8]
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
     uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags and union-find forest
     uint32_t* sw_parent;
@@ -241,6 +244,7 @@ struct Tuning {
     size_t smem;
     bool rowwise;     // allow the division-free row walk (needs tpr % (L/8) == 0)
     bool persistent;  // resident CTAs claim work units instead of one CTA per unit
+    bool bits;        // the bit-sliced kernel (where it supports the lattice)
 };
 
 // Launch shapes chosen by gbmc_autotune (or set with gbmc_set_tuning), per
@@ -256,6 +260,7 @@ struct Shape {
     uint32_t tpr, copies_per_cta;
     bool rowwise;
     bool persistent;
+    bool bits;
 };
 std::mutex g_shape_mu;
 std::map<ShapeKey, Shape> g_shapes;
@@ -300,14 +305,19 @@ Tuning tune(const gbmc_lattice* l, bool use_table = true) {
     if (use_table) {
         std::lock_guard<std::mutex> g(g_shape_mu);
         auto it = g_shapes.find(ShapeKey{l->d.dim, l->d.model, l->d.L});
-        if (it != g_shapes.end())
-            return make_tuning(l, it->second.tpr, it->second.copies_per_cta, it->second.rowwise,
-                               it->second.persistent);
+        if (it != g_shapes.end()) {
+            Tuning t = make_tuning(l, it->second.tpr, it->second.copies_per_cta, it->second.rowwise,
+                                   it->second.persistent);
+            t.bits = it->second.bits;
+            return t;
+        }
     }
     const uint64_t units = units_per_copy(l);
     uint32_t tpr = 8;
     while (4 * tpr < units && tpr < 256) tpr <<= 1;
-    return make_tuning(l, tpr, 256 / tpr, true);
+    Tuning t = make_tuning(l, tpr, 256 / tpr, true);
+    t.bits = true;  // untuned classes take the bit-sliced kernel where it applies
+    return t;
 }
 
 // Shapes for lattices launched together: they must share the CTA size, so
@@ -331,6 +341,7 @@ SweepJob base_job(const gbmc_lattice* l, const Tuning& tu) {
     J.dst = l->cur;
     J.jbits = l->jbits;
     J.jsplit = l->jsplit;
+    J.jb3 = l->jb3;
     J.seed = l->d.seed;
     J.L = (uint32_t)l->d.L;
     J.N = (uint32_t)l->N;
@@ -378,8 +389,8 @@ gbmc_status launch_msc_jobs(gbmc_ctx* ctx, SweepLaunch& P, uint32_t G) {
 // Enqueues one resident sweep launch of P's jobs. force_persistent: -1 takes
 // the context's launch mode (AUTO: the tuned shapes' choice, persistent for
 // batches of several lattices), 0 / 1 force a grid / persistent launch.
-gbmc_status launch_jobs(gbmc_ctx* ctx, const SweepLaunch& P0, const std::vector<Tuning>& tu,
-                        int force_persistent = -1) {
+gbmc_status launch_bytes(gbmc_ctx* ctx, const SweepLaunch& P0, const std::vector<Tuning>& tu,
+                         int force_persistent) {
     bool persistent = P0.njobs > 1;
     for (int j = 0; j < P0.njobs; ++j) persistent = persistent || tu[j].persistent;
     if (ctx->launch_mode == GBMC_LAUNCH_GRID) persistent = false;
@@ -420,6 +431,38 @@ gbmc_status launch_jobs(gbmc_ctx* ctx, const SweepLaunch& P0, const std::vector<
     ProfScope ps_(ctx, PK_SWEEP_RES);
     CUDA_TRY(launch_sweep_resident(P, total, threads, smem, ctx->stream));
     return GBMC_OK;
+}
+
+// Whether the bit-sliced kernel takes job J of launch P under kernel mode k.
+bool job_takes_bits(const SweepLaunch& P, const SweepJob& J, const Tuning& tu, int kernel) {
+    if (kernel == GBMC_KERNEL_BYTES || !bits_supported(P.dim, (int)J.L)) return false;
+    if (P.ea && !J.jb3) return false;
+    return kernel == GBMC_KERNEL_BITS || tu.bits;
+}
+
+// Enqueues the sweep launches of P's jobs: the jobs the bit-sliced kernel
+// takes in one launch of it, the others in one byte-plane resident launch.
+// force_kernel: -1 takes the context's kernel mode.
+gbmc_status launch_jobs(gbmc_ctx* ctx, const SweepLaunch& P0, const std::vector<Tuning>& tu,
+                        int force_persistent = -1, int force_kernel = -1) {
+    const int kernel = force_kernel >= 0 ? force_kernel : ctx->sweep_kernel;
+    SweepLaunch B = P0, Y = P0;
+    B.njobs = Y.njobs = 0;
+    std::vector<Tuning> ty;
+    for (int j = 0; j < P0.njobs; ++j) {
+        if (job_takes_bits(P0, P0.jobs[j], tu[j], kernel)) {
+            B.jobs[B.njobs++] = P0.jobs[j];
+        } else {
+            Y.jobs[Y.njobs++] = P0.jobs[j];
+            ty.push_back(tu[j]);
+        }
+    }
+    if (B.njobs) {
+        ProfScope ps_(ctx, PK_SWEEP_BITS);
+        CUDA_TRY(launch_sweep_bits(B, ctx->stream));
+    }
+    if (Y.njobs == 0) return GBMC_OK;
+    return launch_bytes(ctx, Y, ty, force_persistent);
 }
 
 gbmc_status dalloc(gbmc_pa* pa, void** p, size_t bytes) {
@@ -507,6 +550,14 @@ gbmc_status gbmc_set_sweep_launch(gbmc_ctx* ctx, int32_t mode) {
     if (mode != GBMC_LAUNCH_AUTO && mode != GBMC_LAUNCH_GRID && mode != GBMC_LAUNCH_PERSISTENT)
         return fail(GBMC_ERR_ARG, "unknown sweep launch mode %d", mode);
     ctx->launch_mode = mode;
+    return GBMC_OK;
+}
+
+gbmc_status gbmc_set_sweep_kernel(gbmc_ctx* ctx, int32_t kernel) {
+    if (!ctx) return fail(GBMC_ERR_ARG, "ctx is NULL");
+    if (kernel != GBMC_KERNEL_AUTO && kernel != GBMC_KERNEL_BYTES && kernel != GBMC_KERNEL_BITS)
+        return fail(GBMC_ERR_ARG, "unknown sweep kernel %d", kernel);
+    ctx->sweep_kernel = kernel;
     return GBMC_OK;
 }
 
@@ -649,6 +700,17 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
             }
             CUDA_TRY(launch_split_bonds(l->jbits, l->jsplit, (uint32_t)d->L, d->n_instances, ctx->stream));
         }
+        if (bits_supported(d->dim, d->L)) {
+            e = cudaMalloc(&l->jb3, 96ull * 4 * d->n_instances);
+            if (e != cudaSuccess) {
+                if (l->jsplit) cudaFree(l->jsplit);
+                cudaFree(l->jbits);
+                if (l->owns_spins) cudaFree(l->spins);
+                delete l;
+                return fail(GBMC_ERR_OOM, "cudaMalloc(bond words): %s", cudaGetErrorString(e));
+            }
+            CUDA_TRY(launch_bits3_bonds(l->jbits, l->jb3, d->n_instances, ctx->stream));
+        }
     }
     {
         ProfScope ps_(ctx, PK_INIT);
@@ -669,6 +731,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->owns_spins) cudaFree(l->spins);
     if (l->jbits) cudaFree(l->jbits);
     if (l->jsplit) cudaFree(l->jsplit);
+    if (l->jb3) cudaFree(l->jb3);
     if (l->alt) cudaFree(l->alt);
     if (l->sw_bonds) cudaFree(l->sw_bonds);
     if (l->sw_parent) cudaFree(l->sw_parent);
@@ -1801,6 +1864,236 @@ gbmc_status pa_energies_out(gbmc_ctx* ctx, const gbmc_pa* pa, uint32_t lattice, 
     return GBMC_OK;
 }
 
+// ---- checkpoint / resume of an annealing run ----
+}  // extern "C"
+
+namespace {
+
+constexpr uint32_t kStateMagic = 0x41504247u;  // "GBPA"
+constexpr uint32_t kStateVersion = 1u;
+
+// Plain byte serialisation of the run state (host byte order; the state is
+// meant to be restored by this library on a machine of the same byte order).
+struct StateOut {
+    uint8_t* p;
+    size_t left;
+    bool ok = true;
+    void put(const void* v, size_t n) {
+        if (!ok || n > left) {
+            ok = false;
+            return;
+        }
+        if (n) std::memcpy(p, v, n);
+        p += n;
+        left -= n;
+    }
+    template <typename T>
+    void put(const T& v) { put(&v, sizeof(T)); }
+};
+struct StateIn {
+    const uint8_t* p;
+    size_t left;
+    bool ok = true;
+    void get(void* v, size_t n) {
+        if (!ok || n > left) {
+            ok = false;
+            return;
+        }
+        if (n) std::memcpy(v, p, n);
+        p += n;
+        left -= n;
+    }
+    template <typename T>
+    T get() {
+        T v{};
+        get(&v, sizeof(T));
+        return v;
+    }
+};
+
+size_t pa_state_size(const gbmc_pa* pa) {
+    size_t b = 10 * 4 + (size_t)(pa->S + 1) * pa->P * sizeof(gbmc_pa_stats);
+    for (const auto& pl : pa->lats) {
+        const gbmc_lattice* l = pl.lat;
+        const uint64_t I = l->d.n_instances, C = l->ncopies;
+        b += 5 * 4 + 8 + 5 * 4 + 8;                          // shape, seed, counters, overlap
+        b += 4 + pl.betas.size() * 8 + 4 + pl.log.size() * sizeof(gbmc_schedule_record);
+        b += C * 8 + I * pl.nbins * 4 + I * 8 + I * 32 + I * 16;  // E, M, hist, range, sums, ln Z
+        if (pa->nearest) b += 2 * I * 4;
+    }
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+gbmc_status pa_state_bytes(const gbmc_pa* pa, size_t* bytes) {
+    if (!pa || !bytes) return fail(GBMC_ERR_ARG, "NULL argument");
+    *bytes = pa_state_size(pa);
+    return GBMC_OK;
+}
+
+gbmc_status pa_state_save(gbmc_ctx* ctx, const gbmc_pa* pa, void* host, size_t bytes) {
+    if (!ctx || !pa || !host) return fail(GBMC_ERR_ARG, "NULL argument");
+    if (bytes != pa_state_size(pa)) return fail(GBMC_ERR_ARG, "bytes must be %zu", pa_state_size(pa));
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    StateOut o{(uint8_t*)host, bytes};
+    o.put(kStateMagic);
+    o.put(kStateVersion);
+    o.put((uint32_t)pa->lats.size());
+    o.put(pa->P);
+    o.put(pa->S);
+    o.put((uint32_t)pa->cfg.schedule);
+    o.put((uint32_t)pa->cfg.resample);
+    o.put((uint32_t)pa->cfg.sweep_rng);
+    o.put(pa->cfg.theta);
+    o.put(pa->step);
+    const size_t sb = (size_t)(pa->S + 1) * pa->P * sizeof(gbmc_pa_stats);
+    if (o.ok && sb <= o.left) CUDA_TRY(cudaMemcpy(o.p, pa->stats, sb, cudaMemcpyDeviceToHost));
+    o.p += sb <= o.left ? sb : 0;
+    o.left -= sb <= o.left ? sb : 0;
+    for (const auto& pl : pa->lats) {
+        const gbmc_lattice* l = pl.lat;
+        const uint64_t I = l->d.n_instances, C = l->ncopies;
+        o.put((uint32_t)l->d.dim);
+        o.put((uint32_t)l->d.L);
+        o.put((uint32_t)l->d.model);
+        o.put(l->d.n_instances);
+        o.put(l->d.n_replicas);
+        o.put(l->d.seed);
+        o.put(l->t);
+        o.put(pl.t_start);
+        o.put(pl.steps);
+        o.put((uint32_t)pl.done);
+        o.put((uint32_t)pl.kind);
+        o.put(pl.overlap);
+        o.put((uint32_t)pl.betas.size());
+        o.put(pl.betas.data(), pl.betas.size() * 8);
+        o.put((uint32_t)pl.log.size());
+        o.put(pl.log.data(), pl.log.size() * sizeof(gbmc_schedule_record));
+        struct {
+            const void* d;
+            size_t n;
+        } arrays[] = {{pl.E, C * 4}, {pl.M, C * 4}, {pl.hist, I * pl.nbins * 4}, {pl.emin, I * 4},
+                      {pl.emax, I * 4}, {pl.sums, I * 32}, {pl.lnZ, I * 16}, {pa->nearest ? pl.nrep : nullptr, 2 * I * 4}};
+        for (const auto& a : arrays) {
+            if (!a.d) continue;
+            if (!o.ok || a.n > o.left) {
+                o.ok = false;
+                break;
+            }
+            CUDA_TRY(cudaMemcpy(o.p, a.d, a.n, cudaMemcpyDeviceToHost));
+            o.p += a.n;
+            o.left -= a.n;
+        }
+    }
+    if (!o.ok || o.left != 0) return fail(GBMC_ERR_STATE, "annealing state does not fit its size");
+    return GBMC_OK;
+}
+
+gbmc_status pa_state_load(gbmc_ctx* ctx, gbmc_pa* pa, const void* host, size_t bytes) {
+    if (!ctx || !pa || !host) return fail(GBMC_ERR_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    StateIn in{(const uint8_t*)host, bytes};
+    if (in.get<uint32_t>() != kStateMagic || in.get<uint32_t>() != kStateVersion)
+        return fail(GBMC_ERR_ARG, "not an annealing state of this library version");
+    const uint32_t nl = in.get<uint32_t>(), P = in.get<uint32_t>(), S = in.get<uint32_t>();
+    const uint32_t sched = in.get<uint32_t>(), law = in.get<uint32_t>(), rng = in.get<uint32_t>();
+    const uint32_t theta = in.get<uint32_t>(), step = in.get<uint32_t>();
+    if (!in.ok || nl != pa->lats.size() || P != pa->P || S != pa->S || sched != (uint32_t)pa->cfg.schedule ||
+        law != (uint32_t)pa->cfg.resample || rng != (uint32_t)pa->cfg.sweep_rng || theta != pa->cfg.theta ||
+        step > S)
+        return fail(GBMC_ERR_ARG, "annealing state belongs to a run of another configuration");
+    const size_t sb = (size_t)(S + 1) * P * sizeof(gbmc_pa_stats);
+    if (sb > in.left) return fail(GBMC_ERR_ARG, "annealing state truncated");
+    const uint8_t* stats_h = in.p;
+    in.p += sb;
+    in.left -= sb;
+    // validate every lattice record before changing anything
+    struct LatState {
+        uint64_t seed;
+        uint32_t t, t_start, steps, done, kind;
+        double overlap;
+        std::vector<double> betas;
+        std::vector<gbmc_schedule_record> log;
+        const uint8_t* arrays;
+    };
+    std::vector<LatState> ls(nl);
+    for (uint32_t i = 0; i < nl; ++i) {
+        const PaLat& pl = pa->lats[i];
+        const gbmc_lattice* l = pl.lat;
+        const uint32_t dim = in.get<uint32_t>(), L = in.get<uint32_t>(), model = in.get<uint32_t>();
+        const uint32_t I = in.get<uint32_t>(), R = in.get<uint32_t>();
+        if (!in.ok || dim != (uint32_t)l->d.dim || L != (uint32_t)l->d.L || model != (uint32_t)l->d.model ||
+            I != l->d.n_instances || R != l->d.n_replicas)
+            return fail(GBMC_ERR_ARG, "annealing state: lattice %u has another shape", i);
+        LatState& st = ls[i];
+        st.seed = in.get<uint64_t>();
+        st.t = in.get<uint32_t>();
+        st.t_start = in.get<uint32_t>();
+        st.steps = in.get<uint32_t>();
+        st.done = in.get<uint32_t>();
+        st.kind = in.get<uint32_t>();
+        st.overlap = in.get<double>();
+        const uint32_t nb = in.get<uint32_t>();
+        if (!in.ok || nb > in.left / 8 || nb == 0 || st.steps + 1 > nb || st.steps > S)
+            return fail(GBMC_ERR_ARG, "annealing state: lattice %u has a bad temperature list", i);
+        st.betas.resize(nb);
+        in.get(st.betas.data(), nb * 8);
+        if (!pa->adaptive && st.betas != pl.betas)
+            return fail(GBMC_ERR_ARG, "annealing state: lattice %u follows another schedule", i);
+        const uint32_t nlog = in.get<uint32_t>();
+        if (!in.ok || nlog > in.left / sizeof(gbmc_schedule_record))
+            return fail(GBMC_ERR_ARG, "annealing state truncated");
+        st.log.resize(nlog);
+        in.get(st.log.data(), nlog * sizeof(gbmc_schedule_record));
+        const uint64_t C = l->ncopies;
+        const size_t ab = C * 8 + (size_t)I * pl.nbins * 4 + (size_t)I * 56 + (pa->nearest ? 2ull * I * 4 : 0);
+        if (!in.ok || ab > in.left) return fail(GBMC_ERR_ARG, "annealing state truncated");
+        st.arrays = in.p;
+        in.p += ab;
+        in.left -= ab;
+    }
+    if (in.left != 0) return fail(GBMC_ERR_ARG, "annealing state has %zu trailing bytes", in.left);
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    pa->ctx = ctx;
+    CUDA_TRY(cudaMemcpy(pa->stats, stats_h, sb, cudaMemcpyHostToDevice));
+    for (uint32_t i = 0; i < nl; ++i) {
+        PaLat& pl = pa->lats[i];
+        gbmc_lattice* l = pl.lat;
+        const LatState& st = ls[i];
+        const uint64_t I = l->d.n_instances, C = l->ncopies;
+        l->d.seed = st.seed;
+        l->t = st.t;
+        l->cur = l->spins;  // lattice_copy_in writes the saved configuration here
+        pl.t_start = st.t_start;
+        pl.steps = st.steps;
+        pl.done = st.done != 0;
+        pl.kind = (int32_t)st.kind;
+        pl.overlap = st.overlap;
+        pl.betas = st.betas;
+        pl.log = st.log;
+        pl.stepping = !pl.done;
+        const uint8_t* a = st.arrays;
+        struct {
+            void* d;
+            size_t n;
+        } arrays[] = {{pl.E, C * 4}, {pl.M, C * 4}, {pl.hist, I * pl.nbins * 4}, {pl.emin, I * 4},
+                      {pl.emax, I * 4}, {pl.sums, I * 32}, {pl.lnZ, I * 16}, {pa->nearest ? pl.nrep : nullptr, 2 * I * 4}};
+        for (const auto& x : arrays) {
+            if (!x.d) continue;
+            CUDA_TRY(cudaMemcpy(x.d, a, x.n, cudaMemcpyHostToDevice));
+            a += x.n;
+        }
+    }
+    pa->step = step;
+    // a captured whole-run graph no longer describes the run
+    pa->graph_key.clear();
+    return GBMC_OK;
+}
+
 gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tuning* shape) {
     std::lock_guard<std::mutex> g(g_shape_mu);
     const ShapeKey k{dim, model, L};
@@ -1811,18 +2104,19 @@ gbmc_status gbmc_set_tuning(int32_t dim, int32_t model, int32_t L, const gbmc_tu
     const uint32_t tpr = shape->threads_per_copy, rpc = shape->copies_per_cta;
     if (tpr == 0 || (tpr & (tpr - 1)) || tpr > 256 || rpc == 0 || rpc > 64 || tpr * rpc > 256)
         return fail(GBMC_ERR_ARG, "threads_per_copy must be a power of two <= 256, copies_per_cta in 1..64, product <= 256");
-    g_shapes[k] = Shape{tpr, rpc, shape->row_walk != 0, shape->persistent != 0};
+    g_shapes[k] = Shape{tpr, rpc, shape->row_walk != 0, shape->persistent != 0, shape->kernel == GBMC_KERNEL_BITS};
     return GBMC_OK;
 }
 
 // One untimed launch, then two launches timed with CUDA events (synchronises).
 static gbmc_status time_launches(gbmc_ctx* ctx, const SweepLaunch& P, const std::vector<Tuning>& tv,
-                                 int persistent, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+                                 int persistent, cudaEvent_t e0, cudaEvent_t e1, float* ms,
+                                 int kernel = GBMC_KERNEL_BYTES) {
     gbmc_status st;
-    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
+    if ((st = launch_jobs(ctx, P, tv, persistent, kernel)) != GBMC_OK) return st;
     cudaEventRecord(e0, ctx->stream);
-    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
-    if ((st = launch_jobs(ctx, P, tv, persistent)) != GBMC_OK) return st;
+    if ((st = launch_jobs(ctx, P, tv, persistent, kernel)) != GBMC_OK) return st;
+    if ((st = launch_jobs(ctx, P, tv, persistent, kernel)) != GBMC_OK) return st;
     cudaEventRecord(e1, ctx->stream);
     cudaError_t ce = cudaEventSynchronize(e1);
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
@@ -1850,7 +2144,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     const uint32_t W = (uint32_t)l->d.L / 8;
     const uint64_t units = units_per_copy(l);
     double best = 1e30;
-    Shape best_shape{def.tpr, def.rpc, true, false};
+    Shape best_shape{def.tpr, def.rpc, true, false, false};
     uint32_t n_cand = 0;
     gbmc_status st = GBMC_OK;
     for (uint32_t tpr = 8; tpr <= 256 && st == GBMC_OK; tpr <<= 1) {
@@ -1882,7 +2176,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
                 ++n_cand;
                 if (ms < best) {
                     best = ms;
-                    best_shape = Shape{tu.tpr, tu.rpc, rw != 0, false};
+                    best_shape = Shape{tu.tpr, tu.rpc, rw != 0, false, false};
                 }
             }
         }
@@ -1915,6 +2209,17 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
                 best_shape.persistent = true;
             }
         }
+        // the bit-sliced kernel, where it supports the lattice
+        if (st == GBMC_OK && bits_supported(l->d.dim, l->d.L) && (l->d.model != GBMC_EA_PMJ || l->jb3)) {
+            st = time_launches(ctx, P, tv, 0, e0, e1, &ms, GBMC_KERNEL_BITS);
+            if (st == GBMC_OK) {
+                ++n_cand;
+                if (ms < best) {
+                    best = ms;
+                    best_shape.bits = true;
+                }
+            }
+        }
     }
     ctx->pool.push_back(e0);
     ctx->pool.push_back(e1);
@@ -1929,6 +2234,7 @@ gbmc_status gbmc_autotune(gbmc_ctx* ctx, const gbmc_lattice* l, double beta, uin
     out->copies_per_cta = best_shape.copies_per_cta;
     out->row_walk = best_shape.rowwise ? 1 : 0;
     out->persistent = best_shape.persistent ? 1 : 0;
+    out->kernel = best_shape.bits ? GBMC_KERNEL_BITS : GBMC_KERNEL_BYTES;
     out->ms_per_sweep = best / (2.0 * n_sweeps);
     out->n_candidates = n_cand;
     return GBMC_OK;

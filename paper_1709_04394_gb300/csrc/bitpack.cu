@@ -146,31 +146,6 @@ __device__ __forceinline__ void bp_neighbours(const uint32_t* oth, uint32_t L, u
     }
 }
 
-// The new value of the word s (32 sites of one colour) given its neighbour
-// words; q0 = the Philox counter q of its first site (colour rank k = y L/2 +
-// 32 w + b of bit b, q = k / 4).
-__device__ __forceinline__ uint32_t bp_word_update(uint32_t s, uint32_t up, uint32_t dn, uint32_t same, uint32_t side,
-                                                   const PhiloxFixed& pf, uint32_t q0, uint32_t T4, uint32_t T8) {
-    const uint32_t d1 = s ^ up, d2 = s ^ dn, d3 = s ^ same, d4 = s ^ side;  // 1 = unsatisfied bond
-    // bit-sliced a = d1 + d2 + d3 + d4 = a0 + 2 a1 + 4 a2
-    const uint32_t s1 = d1 ^ d2, c1 = d1 & d2, s2 = d3 ^ d4, c2 = d3 & d4;
-    const uint32_t a0 = s1 ^ s2, c3 = s1 & s2;
-    const uint32_t a1 = c1 ^ c2 ^ c3, a2 = (c1 & c2) | (c3 & (c1 ^ c2));
-    const uint32_t ge2 = a1 | a2;            // dE <= 0: always flips
-    const uint32_t eq1 = a0 & ~ge2;          // dE = 4
-    const uint32_t eq0 = ~(a0 | ge2);        // dE = 8
-    uint32_t r4 = 0, r8 = 0;                 // bit b of the word at bit 31 - b
-#pragma unroll
-    for (uint32_t i = 0; i < 8; ++i) {
-        const uint4 v = philox_q(pf, q0 + i);
-        accept_bits(r4, r8, T4, T8, v.x);
-        accept_bits(r4, r8, T4, T8, v.y);
-        accept_bits(r4, r8, T4, T8, v.z);
-        accept_bits(r4, r8, T4, T8, v.w);
-    }
-    return s ^ (ge2 | (eq1 & __brev(r4)) | (eq0 & __brev(r8)));
-}
-
 // One half-sweep of colour c over every copy: one thread per word of plane c.
 __global__ void __launch_bounds__(256) k_bp_halfsweep(uint32_t* P, uint32_t L, uint64_t copies, uint32_t R,
                                                       uint32_t inst_base, uint32_t colour, uint32_t t, uint32_t k0,

@@ -1,6 +1,11 @@
-// bits.cuh -- acceptance bits of bit-parallel (multi-spin-coded) updates.
+// bits.cuh -- bit-sliced updates of 32 same-colour sites held in one word
+// (one bit per spin, 1 = down): acceptance bits and the word updates shared by
+// the bit-packed layout (bitpack.cu) and the bit-sliced resident sweeps
+// (bitsweep.cu).
 #pragma once
 #include <cstdint>
+
+#include "device.cuh"
 
 namespace gbmc {
 
@@ -16,6 +21,73 @@ __device__ __forceinline__ void accept_bits(uint32_t& r4, uint32_t& r8, uint32_t
         "addc.u32 %1, %1, %1;\n\t}"
         : "+r"(r4), "+r"(r8)
         : "r"(T4), "r"(T8), "r"(u));
+}
+
+// r4, r8, r12 shifted by one bit each: three comparisons of u (3D, dE = 4,
+// 8, 12).
+__device__ __forceinline__ void accept_bits3(uint32_t& r4, uint32_t& r8, uint32_t& r12, uint32_t T4, uint32_t T8,
+                                             uint32_t T12, uint32_t u) {
+    accept_bits(r4, r8, T4, T8, u);
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %2;\n\t"
+        "addc.u32 %0, %0, %0;\n\t}"
+        : "+r"(r12)
+        : "r"(T12), "r"(u));
+}
+
+// The new value of the word s (32 sites of one colour) given its neighbour
+// words; q0 = the Philox counter q of its first site (colour rank k = y L/2 +
+// 32 w + b of bit b, q = k / 4).
+__device__ __forceinline__ uint32_t bp_word_update(uint32_t s, uint32_t up, uint32_t dn, uint32_t same, uint32_t side,
+                                                   const PhiloxFixed& pf, uint32_t q0, uint32_t T4, uint32_t T8) {
+    const uint32_t d1 = s ^ up, d2 = s ^ dn, d3 = s ^ same, d4 = s ^ side;  // 1 = unsatisfied bond
+    // bit-sliced a = d1 + d2 + d3 + d4 = a0 + 2 a1 + 4 a2
+    const uint32_t s1 = d1 ^ d2, c1 = d1 & d2, s2 = d3 ^ d4, c2 = d3 & d4;
+    const uint32_t a0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t a1 = c1 ^ c2 ^ c3, a2 = (c1 & c2) | (c3 & (c1 ^ c2));
+    const uint32_t ge2 = a1 | a2;            // dE <= 0: always flips
+    const uint32_t eq1 = a0 & ~ge2;          // dE = 4
+    const uint32_t eq0 = ~(a0 | ge2);        // dE = 8
+    uint32_t r4 = 0, r8 = 0;                 // bit b of the word at bit 31 - b
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint4 v = philox_q(pf, q0 + i);
+        accept_bits(r4, r8, T4, T8, v.x);
+        accept_bits(r4, r8, T4, T8, v.y);
+        accept_bits(r4, r8, T4, T8, v.z);
+        accept_bits(r4, r8, T4, T8, v.w);
+    }
+    return s ^ (ge2 | (eq1 & __brev(r4)) | (eq0 & __brev(r8)));
+}
+
+// Majority of three words, bit by bit (the carry of a full adder).
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
+
+// 3D: the new value of the word s given its six unsatisfied-bond masks d0..d5
+// (bit = 1 where s_i J_ij s_j = -1). a = d0 + .. + d5 bit-sliced; a site flips
+// iff a >= 3 (dE <= 0), or a = 2 and u <= T(4), a = 1 and u <= T(8), a = 0 and
+// u <= T(12). q0: Philox counter q of the word's first site.
+__device__ __forceinline__ uint32_t bp3_word_update(uint32_t s, uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3,
+                                                    uint32_t d4, uint32_t d5, const PhiloxFixed& pf, uint32_t q0,
+                                                    uint32_t T4, uint32_t T8, uint32_t T12) {
+    const uint32_t s1 = d0 ^ d1 ^ d2, c1 = maj3(d0, d1, d2);
+    const uint32_t s2 = d3 ^ d4 ^ d5, c2 = maj3(d3, d4, d5);
+    const uint32_t a0 = s1 ^ s2, t = s1 & s2;
+    const uint32_t a1 = c1 ^ c2 ^ t, a2 = maj3(c1, c2, t);
+    const uint32_t ge3 = a2 | (a1 & a0);     // dE <= 0
+    const uint32_t eq2 = a1 & ~(a0 | a2);    // dE = 4
+    const uint32_t eq1 = a0 & ~(a1 | a2);    // dE = 8
+    const uint32_t eq0 = ~(a0 | a1 | a2);    // dE = 12
+    uint32_t r4 = 0, r8 = 0, r12 = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint4 v = philox_q(pf, q0 + i);
+        accept_bits3(r4, r8, r12, T4, T8, T12, v.x);
+        accept_bits3(r4, r8, r12, T4, T8, T12, v.y);
+        accept_bits3(r4, r8, r12, T4, T8, T12, v.z);
+        accept_bits3(r4, r8, r12, T4, T8, T12, v.w);
+    }
+    return s ^ (ge3 | (eq2 & __brev(r4)) | (eq1 & __brev(r8)) | (eq0 & __brev(r12)));
 }
 
 }  // namespace gbmc

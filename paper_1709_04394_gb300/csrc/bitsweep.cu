@@ -1,0 +1,441 @@
+// bitsweep.cu -- checkerboard Metropolis sweeps (Sec. 3.1, Eq. (8)) of copies
+// held bit-sliced on chip: one bit per spin in per-colour planes (the separate
+// sub-lattice storage of Sec. 3.1 with multi-spin coding of the sites), so that
+// the neighbour count of 32 sites costs a handful of word operations and the
+// per-site work is the Philox word and its threshold comparisons.
+//
+// The population stays in the int8 layout of the ABI in global memory; each
+// warp converts its copy to bit planes on load (through the resampling gather
+// of Sec. 5.4 when a parent map is given) and back on store. The sites use the
+// same Philox words as every other sweep kernel (colour rank k of a site, q =
+// k >> 2, word k & 3), so the spins are bit-identical to theirs.
+//
+//  * k_sweep_bits2: 2D ferromagnet, L in {64, 128, 256}. One warp per copy,
+//    the copy in shared memory: plane c, row y, word w = the sites
+//    j = 32 w .. 32 w + 31 of colour c in row y (x = 2 j + ((y + c) & 1)),
+//    bit j - 32 w. No block-wide barrier: the warps of a block are independent.
+//  * k_sweep_bits3: 3D lattices with L = 8 (ferromagnet or +-J spin glass,
+//    Sec. 6). Eight lanes per copy, four copies per warp, the copy in
+//    registers: lane z holds word z of both planes = the 32 sites of colour c
+//    in the slab z (bit 4 y + j, x = 2 j + ((y + z + c) & 1)), i.e. colour
+//    ranks 32 z .. 32 z + 31. Neighbours along x and y are rotations of the
+//    other plane's word, along z the words of the neighbouring lanes.
+#include "bits.cuh"
+#include "device.cuh"
+#include "internal.h"
+
+namespace gbmc {
+
+namespace {
+
+constexpr uint32_t kBitsWarps = 4;  // warps per block: 4 copies (2D) or 16 copies (3D)
+
+// Down bits of the four bytes (+1 = 0x01, -1 = 0xFF) of a word: bit i = byte i
+// is negative (the four sign bits gathered by one multiply).
+__device__ __forceinline__ uint32_t nib_down(uint32_t four_bytes) {
+    return ((four_bytes & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// Four down bits -> four bytes +1 / -1 (bit i to byte i, then 0 -> 0x01, 1 -> 0xFF).
+__device__ __forceinline__ uint32_t spread4(uint32_t n) {
+    return ((n * 0x00204081u) & 0x01010101u) * 0xFEu + 0x01010101u;
+}
+
+// Eight consecutive sites (bytes b0..b7 in lo, hi) -> the down bits of the four
+// even-x sites (b0, b2, b4, b6) and of the four odd-x sites.
+__device__ __forceinline__ void pack8(uint32_t lo, uint32_t hi, uint32_t& ev, uint32_t& od) {
+    ev = nib_down(__byte_perm(lo, hi, 0x6420));
+    od = nib_down(__byte_perm(lo, hi, 0x7531));
+}
+
+// The inverse: four even-x and four odd-x down bits -> eight bytes.
+__device__ __forceinline__ uint2 unpack8(uint32_t ev, uint32_t od) {
+    const uint32_t e = spread4(ev), o = spread4(od);
+    return make_uint2(__byte_perm(e, o, 0x5140), __byte_perm(e, o, 0x7362));
+}
+
+// Which job a block belongs to (jobs own consecutive blocks).
+__device__ __forceinline__ int job_of(const SweepLaunch& P, uint32_t block) {
+    int j = 0;
+    while (j + 1 < P.njobs && block >= P.cta_begin[j + 1]) ++j;
+    return j;
+}
+
+// Thresholds of one copy: the job's, or its temperature's (parallel tempering).
+__device__ __forceinline__ void copy_thresholds(const SweepJob& J, uint64_t slot, uint32_t& T4, uint32_t& T8,
+                                                uint32_t& T12) {
+    if (J.temp_of) {
+        const uint32_t* th = J.thr_temp + 3ull * J.temp_of[slot];
+        T4 = th[0];
+        T8 = th[1];
+        T12 = th[2];
+    } else {
+        T4 = J.thr[0];
+        T8 = J.thr[1];
+        T12 = J.thr[2];
+    }
+}
+
+// Energy and magnetisation of one copy after the last sweep (or of every
+// sweep when a series is asked for): lane 0 writes them and, for annealing
+// runs, adds them to the population's histogram, range and exact sums.
+__device__ __forceinline__ void record_copy(const SweepJob& J, uint64_t slot, uint32_t inst, uint32_t s, bool sweep,
+                                            bool last, int E, int M) {
+    const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
+    if (J.Eser && sweep) J.Eser[(uint64_t)s * ncopies + slot] = E;
+    if (J.Mser && sweep) J.Mser[(uint64_t)s * ncopies + slot] = M;
+    if (!last) return;
+    if (J.E) J.E[slot] = E;
+    if (J.M) J.M[slot] = M;
+    if (J.hist) {
+        atomicAdd(&J.hist[(uint64_t)inst * J.nbins + (uint32_t)((E - J.e_lo) >> 2)], 1u);
+        atomicMin(&J.emin[inst], E);
+        atomicMax(&J.emax[inst], E);
+        unsigned long long* su = J.sums + (uint64_t)inst * 4;
+        const long long el = E, ml = M;
+        atomicAdd(&su[0], (unsigned long long)el);
+        atomicAdd(&su[1], (unsigned long long)(el * el));
+        atomicAdd(&su[2], (unsigned long long)(ml < 0 ? -ml : ml));
+        atomicAdd(&su[3], (unsigned long long)(ml * ml));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D
+// ---------------------------------------------------------------------------
+
+// Neighbour words of the colour-c word idx = (y, w): the other plane's words
+// in rows y - 1 and y + 1 and in row y, and the row-y word shifted by one site
+// towards j + 1 (odd x) or j - 1 (even x), wrapping around the row.
+__device__ __forceinline__ void nb2(const uint32_t* oth, uint32_t idx, uint32_t lgW, uint32_t L, uint32_t colour,
+                                    uint32_t& up, uint32_t& dn, uint32_t& same, uint32_t& side, uint32_t& q0) {
+    const uint32_t Wm = (1u << lgW) - 1u;
+    const uint32_t y = idx >> lgW, w = idx & Wm;
+    up = oth[(((y - 1u) & (L - 1u)) << lgW) + w];
+    dn = oth[(((y + 1u) & (L - 1u)) << lgW) + w];
+    same = oth[idx];
+    const bool odd = ((y + colour) & 1u) != 0u;
+    const uint32_t nbw = oth[(y << lgW) + ((odd ? w + 1u : w - 1u) & Wm)];
+    side = odd ? __funnelshift_r(same, nbw, 1) : __funnelshift_l(nbw, same, 1);
+    q0 = y * (L >> 3) + 8u * w;
+}
+
+__global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ SweepLaunch P, uint32_t wpb,
+                                                     uint32_t words_per_warp) {
+    extern __shared__ __align__(16) uint32_t smw[];
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const int jid = job_of(P, blockIdx.x);
+    const SweepJob& J = P.jobs[jid];
+    const uint64_t slot = (uint64_t)(blockIdx.x - P.cta_begin[jid]) * wpb + wib;
+    if (slot >= (uint64_t)J.n_inst * J.R) return;  // whole warp; no block barriers follow
+    uint32_t inst, r;
+    split_copy(slot, J.R, inst, r);
+    if (J.nlive && r >= J.nlive[inst]) return;     // variable populations: only live slots
+    const uint32_t L = J.L, N = J.N;
+    const uint32_t lgL = 31u - __clz(L), lgW = lgL - 6u;
+    const uint32_t PW = L << lgW;                  // words per colour plane
+    uint32_t* sm = smw + (uint64_t)wib * words_per_warp;
+    uint8_t* smb = reinterpret_cast<uint8_t*>(sm);
+
+    // ---- load: int8 rows -> bit planes (16 bytes = 8 even-x + 8 odd-x sites per lane and step) ----
+    const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
+    const uint4* g = reinterpret_cast<const uint4*>(J.src + srcslot * N);
+    for (uint32_t c16 = lane; c16 < (N >> 4); c16 += 32u) {
+        const uint4 v = g[c16];
+        uint32_t e0, o0, e1, o1;
+        pack8(v.x, v.y, e0, o0);
+        pack8(v.z, v.w, e1, o1);
+        const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
+        const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);  // byte of the plane
+        const uint32_t ce = y & 1u;                                             // colour of the even-x sites
+        smb[(ce * PW << 2) + b] = (uint8_t)(e0 | (e1 << 4));
+        smb[((ce ^ 1u) * PW << 2) + b] = (uint8_t)(o0 | (o1 << 4));
+    }
+    __syncwarp();
+
+    uint32_t T4, T8, T12;
+    copy_thresholds(J, slot, T4, T8, T12);
+    const uint32_t instance = J.inst_base + inst;
+    const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
+    const bool want_final = J.E || J.M || J.hist;
+    const uint32_t nsw = J.nsweeps;
+    for (uint32_t s = 0; s <= nsw; ++s) {
+        if (s == nsw && nsw != 0) break;  // s == nsw: measurement-only pass when nothing is swept
+        const bool sweep = s < nsw;
+        if (sweep) {
+            const uint32_t t = J.t0 + s;
+            for (uint32_t colour = 0; colour < 2; ++colour) {
+                const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
+                uint32_t* own = sm + colour * PW;
+                const uint32_t* oth = sm + (colour ^ 1u) * PW;
+                // two words per lane and step (PW is a multiple of 64): both are
+                // loaded and updated before either is stored (they only read the
+                // other plane)
+                for (uint32_t ia = lane; ia < PW; ia += 64u) {
+                    const uint32_t ib = ia + 32u;
+                    uint32_t ua, da, sa, xa, qa, ub, db, sb, xb, qb;
+                    nb2(oth, ia, lgW, L, colour, ua, da, sa, xa, qa);
+                    nb2(oth, ib, lgW, L, colour, ub, db, sb, xb, qb);
+                    const uint32_t wa = own[ia], wb = own[ib];
+                    const uint32_t na = bp_word_update(wa, ua, da, sa, xa, pf, qa, T4, T8);
+                    const uint32_t nb = bp_word_update(wb, ub, db, sb, xb, pf, qb, T4, T8);
+                    own[ia] = na;
+                    own[ib] = nb;
+                }
+                __syncwarp();
+            }
+        }
+        const bool last = sweep ? s + 1 == nsw : true;
+        if ((J.Eser && sweep) || (J.Mser && sweep) || (last && want_final)) {
+            // E = -sum over bonds s_i s_j: every bond has one colour-0 end, so
+            // E = 2 (unsatisfied bonds of the colour-0 sites) - 2 N
+            int U = 0, D = 0;
+            for (uint32_t idx = lane; idx < PW; idx += 32u) {
+                uint32_t up, dn, same, side, q0;
+                nb2(sm + PW, idx, lgW, L, 0u, up, dn, same, side, q0);
+                const uint32_t w0 = sm[idx];
+                U += __popc(w0 ^ up) + __popc(w0 ^ dn) + __popc(w0 ^ same) + __popc(w0 ^ side);
+                D += __popc(w0) + __popc(sm[PW + idx]);
+            }
+            U = warp_sum(U);
+            D = warp_sum(D);
+            if (lane == 0) record_copy(J, slot, inst, s, sweep, last, 2 * U - 2 * (int)N, (int)N - 2 * D);
+        }
+    }
+
+    // ---- store: bit planes -> int8 rows ----
+    if (nsw > 0 || J.dst != J.src || J.parent) {
+        uint4* d = reinterpret_cast<uint4*>(J.dst + slot * N);
+        for (uint32_t c16 = lane; c16 < (N >> 4); c16 += 32u) {
+            const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
+            const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);
+            const uint32_t ce = y & 1u;
+            const uint32_t ev = smb[(ce * PW << 2) + b], od = smb[((ce ^ 1u) * PW << 2) + b];
+            const uint2 lo = unpack8(ev & 15u, od & 15u), hi = unpack8(ev >> 4, od >> 4);
+            d[c16] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3D, L = 8
+// ---------------------------------------------------------------------------
+
+// Rotation of each 4-bit row (nibble) of a slab word by one site: bit j takes
+// bit j - 1 (lft) or bit j + 1 (rgt), wrapping within the row.
+__device__ __forceinline__ uint32_t rot_nib_lft(uint32_t w) {
+    return ((w << 1) & 0xEEEEEEEEu) | ((w >> 3) & 0x11111111u);
+}
+__device__ __forceinline__ uint32_t rot_nib_rgt(uint32_t w) {
+    return ((w >> 1) & 0x77777777u) | ((w << 3) & 0x88888888u);
+}
+
+// The six neighbour words of the colour-c word of slab z, in the bond order
+// (same-j x neighbour, other x neighbour, y - 1, y + 1, z - 1, z + 1), from the
+// other plane's word of this lane and of the lanes of slabs z -/+ 1.
+__device__ __forceinline__ void nb3(uint32_t oth, uint32_t z, uint32_t colour, uint32_t gbase, uint32_t nb[6]) {
+    // rows whose sites of colour c have odd x: (y + z + c) odd
+    const uint32_t odd_rows = ((z + colour) & 1u) ? 0x0F0F0F0Fu : 0xF0F0F0F0u;
+    nb[0] = oth;
+    nb[1] = (rot_nib_lft(oth) & ~odd_rows) | (rot_nib_rgt(oth) & odd_rows);
+    nb[2] = __funnelshift_l(oth, oth, 4);  // row y takes row y - 1
+    nb[3] = __funnelshift_r(oth, oth, 4);  // row y takes row y + 1
+    nb[4] = __shfl_sync(0xffffffffu, oth, gbase | ((z - 1u) & 7u));
+    nb[5] = __shfl_sync(0xffffffffu, oth, gbase | ((z + 1u) & 7u));
+}
+
+template <bool EA>
+__global__ void __launch_bounds__(128) k_sweep_bits3(const __grid_constant__ SweepLaunch P, uint32_t wpb) {
+    __shared__ __align__(16) uint32_t stage[kBitsWarps][4][16];  // [warp][copy][plane * 8 + z]
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const int jid = job_of(P, blockIdx.x);
+    const SweepJob& J = P.jobs[jid];
+    const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
+    const uint64_t warp_slot0 = ((uint64_t)(blockIdx.x - P.cta_begin[jid]) * wpb + wib) * 4u;
+    if (warp_slot0 >= ncopies) return;  // whole warp
+    const uint32_t g = lane >> 3, z = lane & 7u, gbase = lane & ~7u;
+    const uint64_t slot = warp_slot0 + g;
+    uint32_t inst = 0, r = 0;
+    bool active = slot < ncopies;
+    if (active) {
+        split_copy(slot, J.R, inst, r);
+        if (J.nlive && r >= J.nlive[inst]) active = false;
+    }
+    // every lane takes part in the shuffles; inactive copies compute on zeros
+    constexpr uint32_t N = 512u;
+    uint8_t* stb = reinterpret_cast<uint8_t*>(stage[wib][g]);
+
+    // ---- load: chunk m of 16 bytes = rows y, y + 1 (y = 2 (m & 3)) of slab m >> 2 ----
+    const uint64_t srcslot = active ? (J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot) : 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+        const uint32_t m = z + 8u * k, zz = m >> 2, y = (m & 3u) << 1;
+        uint4 v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+        if (active) v = reinterpret_cast<const uint4*>(J.src + srcslot * N)[m];
+        uint32_t ey, oy, ey1, oy1;
+        pack8(v.x, v.y, ey, oy);    // row y
+        pack8(v.z, v.w, ey1, oy1);  // row y + 1
+        // plane A = (y + z) & 1 holds the even-x sites of row y and the odd-x sites of row y + 1
+        const uint32_t A = (y + zz) & 1u;
+        stb[((A * 8u + zz) << 2) + (y >> 1)] = (uint8_t)(ey | (oy1 << 4));
+        stb[(((A ^ 1u) * 8u + zz) << 2) + (y >> 1)] = (uint8_t)(oy | (ey1 << 4));
+    }
+    __syncwarp();
+    uint32_t pl[2] = {stage[wib][g][z], stage[wib][g][8 + z]};
+    __syncwarp();
+
+    uint32_t jb[2][6];
+#pragma unroll
+    for (uint32_t c = 0; c < 2; ++c)
+#pragma unroll
+        for (uint32_t k = 0; k < 6; ++k)
+            jb[c][k] = (EA && active) ? J.jb3[(((uint64_t)inst * 2u + c) * 6u + k) * 8u + z] : 0u;
+
+    uint32_t T4, T8, T12;
+    copy_thresholds(J, active ? slot : 0, T4, T8, T12);
+    const uint32_t instance = J.inst_base + inst;
+    const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
+    const bool want_final = J.E || J.M || J.hist;
+    const uint32_t nsw = J.nsweeps;
+    for (uint32_t s = 0; s <= nsw; ++s) {
+        if (s == nsw && nsw != 0) break;
+        const bool sweep = s < nsw;
+        if (sweep) {
+            const uint32_t t = J.t0 + s;
+#pragma unroll 1
+            for (uint32_t colour = 0; colour < 2; ++colour) {
+                const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
+                uint32_t nb[6];
+                nb3(colour ? pl[0] : pl[1], z, colour, gbase, nb);
+                const uint32_t w = colour ? pl[1] : pl[0];
+                uint32_t d[6];
+#pragma unroll
+                for (uint32_t k = 0; k < 6; ++k) d[k] = w ^ nb[k] ^ (colour ? jb[1][k] : jb[0][k]);
+                const uint32_t nw = bp3_word_update(w, d[0], d[1], d[2], d[3], d[4], d[5], pf, 8u * z, T4, T8, T12);
+                if (colour) pl[1] = nw;
+                else pl[0] = nw;
+            }
+        }
+        const bool last = sweep ? s + 1 == nsw : true;
+        if ((J.Eser && sweep) || (J.Mser && sweep) || (last && want_final)) {
+            uint32_t nb[6];
+            nb3(pl[1], z, 0u, gbase, nb);
+            int U = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < 6; ++k) U += __popc(pl[0] ^ nb[k] ^ jb[0][k]);
+            int D = __popc(pl[0]) + __popc(pl[1]);
+#pragma unroll
+            for (uint32_t o = 4; o > 0; o >>= 1) {
+                U += __shfl_xor_sync(0xffffffffu, U, o);
+                D += __shfl_xor_sync(0xffffffffu, D, o);
+            }
+            // E = 2 (unsatisfied bonds of the colour-0 sites) - 3 N
+            if (active && z == 0) record_copy(J, slot, inst, s, sweep, last, 2 * U - 3 * (int)N, (int)N - 2 * D);
+        }
+    }
+
+    // ---- store ----
+    if (nsw > 0 || J.dst != J.src || J.parent) {
+        stage[wib][g][z] = pl[0];
+        stage[wib][g][8 + z] = pl[1];
+        __syncwarp();
+        if (active) {
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t m = z + 8u * k, zz = m >> 2, y = (m & 3u) << 1;
+                const uint32_t A = (y + zz) & 1u;
+                const uint32_t ba = stb[((A * 8u + zz) << 2) + (y >> 1)];
+                const uint32_t bb = stb[(((A ^ 1u) * 8u + zz) << 2) + (y >> 1)];
+                const uint2 row0 = unpack8(ba & 15u, bb & 15u);  // row y: even from A, odd from B
+                const uint2 row1 = unpack8(bb >> 4, ba >> 4);     // row y + 1: even from B, odd from A
+                reinterpret_cast<uint4*>(J.dst + slot * N)[m] = make_uint4(row0.x, row0.y, row1.x, row1.y);
+            }
+        }
+    }
+}
+
+// Bond words of the 3D L = 8 bit-sliced sweep: for instance i, colour c, bond
+// kind k and slab z, bit 4 y + j = 1 iff the bond between the colour-c site
+// (x = 2 j + ((y + z + c) & 1), y, z) and its k-th neighbour (order of nb3)
+// has J = -1. jbits: [inst][mu][site] bytes, 1 where the forward bond of the
+// site along mu has J = -1.
+__global__ void k_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_inst * 96u) return;
+    const uint32_t inst = g / 96u, rem = g - inst * 96u;
+    const uint32_t c = rem / 48u, k = (rem / 8u) % 6u, z = rem & 7u;
+    constexpr uint32_t L = 8u, N = 512u;
+    const uint8_t* jb = jbits + (uint64_t)inst * 3u * N;
+    uint32_t word = 0;
+    for (uint32_t y = 0; y < L; ++y)
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t o = (y + z + c) & 1u, x = 2u * j + o;
+            const uint32_t i = (z * L + y) * L + x;
+            const uint32_t xm = (z * L + y) * L + ((x + L - 1u) & (L - 1u));  // site x - 1
+            uint32_t bond;
+            switch (k) {
+                case 0: bond = o ? jb[xm] : jb[i]; break;                                     // same-j x neighbour
+                case 1: bond = o ? jb[i] : jb[xm]; break;                                     // the other x neighbour
+                case 2: bond = jb[N + (z * L + ((y + L - 1u) & (L - 1u))) * L + x]; break;    // y - 1
+                case 3: bond = jb[N + i]; break;                                              // y + 1
+                case 4: bond = jb[2u * N + ((((z + L - 1u) & (L - 1u)) * L + y) * L + x)]; break;  // z - 1
+                default: bond = jb[2u * N + i]; break;                                        // z + 1
+            }
+            word |= (bond ? 1u : 0u) << (4u * y + j);
+        }
+    jb3[g] = word;
+}
+
+}  // namespace
+
+bool bits_supported(int dim, int L) { return (dim == 2 && (L == 64 || L == 128 || L == 256)) || (dim == 3 && L == 8); }
+
+cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s) {
+    const uint32_t n = n_inst * 96u;
+    k_bits3_bonds<<<(n + 255u) / 256u, 256, 0, s>>>(jbits, jb3, n_inst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
+    constexpr uint32_t kWarps = kBitsWarps;
+    SweepLaunch P = P0;
+    // largest copies first: their blocks are dispatched first, shortening the tail
+    for (int a = 1; a < P.njobs; ++a)
+        for (int b = a; b > 0 && P.jobs[b].N > P.jobs[b - 1].N; --b) {
+            const SweepJob t = P.jobs[b];
+            P.jobs[b] = P.jobs[b - 1];
+            P.jobs[b - 1] = t;
+        }
+    const uint32_t copies_per_block = P.dim == 2 ? kWarps : 4u * kWarps;
+    uint32_t total = 0, words = 0;
+    for (int j = 0; j < P.njobs; ++j) {
+        const SweepJob& J = P.jobs[j];
+        if (!bits_supported(P.dim, (int)J.L)) return cudaErrorInvalidValue;
+        P.cta_begin[j] = total;
+        const uint64_t nb = ((uint64_t)J.n_inst * J.R + copies_per_block - 1) / copies_per_block;
+        if (total + nb > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+        total += (uint32_t)nb;
+        const uint32_t w = J.N / 32u;  // two planes of N / 2 bits
+        if (w > words) words = w;
+    }
+    P.cta_begin[P.njobs] = total;
+    P.total = total;
+    if (total == 0) return cudaSuccess;
+    if (P.dim == 2) {
+        const size_t smem = (size_t)kWarps * words * 4u;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_bits2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_sweep_bits2<<<total, 32u * kWarps, smem, s>>>(P, kWarps, words);
+    } else if (P.ea) {
+        k_sweep_bits3<true><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
+    } else {
+        k_sweep_bits3<false><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

@@ -42,6 +42,8 @@ struct SweepJob {
     const uint32_t* thr_temp; // parallel tempering: [T][3] thresholds per temperature, or null
     const uint32_t* temp_of;  // parallel tempering: [n_inst*R] temperature of each copy, or null
     const uint32_t* nlive;    // variable populations: [n_inst] live copies (the first ones); null: R
+    const uint32_t* jb3;      // +-J bonds of the bit-sliced 3D L = 8 sweep: [n_inst][2][6][8] words, bit 1
+                              // where J = -1; null for J = 1
 };
 
 struct SweepLaunch {
@@ -137,6 +139,15 @@ cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t 
 // Global-memory half-sweep over one job (large lattices); colour 0 or 1.
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);
+
+// Bit-sliced resident sweeps (bitsweep.cu): every copy converted to one bit
+// per spin on chip, same results as launch_sweep_resident. Supported lattices:
+// 2D ferromagnets with L in {64, 128, 256}, 3D lattices with L = 8 (all jobs of
+// a launch of one dimension and model). Uses its own block layout (P.cta_begin
+// and P.total are recomputed).
+bool bits_supported(int dim, int L);
+cudaError_t launch_sweep_bits(const SweepLaunch& P, cudaStream_t s);
+cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s);
 
 // Multi-spin-coded sweeps (2D ferromagnet, L % 16 == 0): jobs with rpc = 32 G
 // replicas per CTA; G in 1..4 groups of 32.

@@ -25,6 +25,7 @@ GBMC_INT8, GBMC_BITPACK = 0, 1
 GBMC_START_ALL_UP, GBMC_START_RANDOM = 0, 1
 GBMC_SCHED_LINEAR, GBMC_SCHED_LIST, GBMC_SCHED_BISECTION, GBMC_SCHED_MLP = 0, 1, 2, 3
 GBMC_LAUNCH_AUTO, GBMC_LAUNCH_GRID, GBMC_LAUNCH_PERSISTENT = 0, 1, 2
+GBMC_KERNEL_AUTO, GBMC_KERNEL_BYTES, GBMC_KERNEL_BITS = 0, 1, 2
 GBMC_RESAMPLE_MULTINOMIAL, GBMC_RESAMPLE_NEAREST, GBMC_RESAMPLE_POISSON = 0, 1, 2
 GBMC_RNG_PHILOX, GBMC_RNG_MSC = 0, 1
 
@@ -42,7 +43,7 @@ class KernelTime(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("resident", C.c_int32), ("threads_per_copy", C.c_uint32), ("copies_per_cta", C.c_uint32),
                 ("row_walk", C.c_int32), ("ms_per_sweep", C.c_double), ("n_candidates", C.c_uint32),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32), ("kernel", C.c_int32)]
 
 
 class ScheduleRecord(C.Structure):
@@ -107,6 +108,10 @@ def load():
             "gbmc_profile": ([p, C.c_int32], st),
             "gbmc_set_resample_mode": ([p, C.c_int32], st),
             "gbmc_set_sweep_launch": ([p, C.c_int32], st),
+            "gbmc_set_sweep_kernel": ([p, C.c_int32], st),
+            "pa_state_bytes": ([p, C.POINTER(C.c_size_t)], st),
+            "pa_state_save": ([p, p, p, C.c_size_t], st),
+            "pa_state_load": ([p, p, p, C.c_size_t], st),
             "gbmc_test_barrier_wait": ([p, C.c_uint32, C.c_uint64], st),
             "gbmc_profile_read": ([p, p, C.c_uint32, C.POINTER(C.c_uint32)], st),
             "gbmc_kernel_launches": ([], C.c_uint64),
@@ -211,6 +216,10 @@ def gbmc_set_sweep_launch(ctx, mode=GBMC_LAUNCH_AUTO):
     _check(load().gbmc_set_sweep_launch(ctx, int(mode)))
 
 
+def gbmc_set_sweep_kernel(ctx, kernel=GBMC_KERNEL_AUTO):
+    _check(load().gbmc_set_sweep_kernel(ctx, int(kernel)))
+
+
 def gbmc_test_barrier_wait(ctx, phantom_arrivals=0, budget_cycles=2000000000):
     _check(load().gbmc_test_barrier_wait(ctx, phantom_arrivals, budget_cycles))
 
@@ -295,12 +304,13 @@ def gbmc_autotune(ctx, lat, beta, n_sweeps=10) -> Tuning:
     return t
 
 
-def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_walk=True, persistent=False):
+def gbmc_set_tuning(dim, model, L, threads_per_copy=None, copies_per_cta=1, row_walk=True, persistent=False,
+                    kernel=GBMC_KERNEL_BYTES):
     """Force a launch shape for a lattice class; threads_per_copy=None clears it."""
     if threads_per_copy is None:
         _check(load().gbmc_set_tuning(dim, model, L, None))
         return
-    t = Tuning(1, threads_per_copy, copies_per_cta, int(bool(row_walk)), 0.0, 0, int(bool(persistent)))
+    t = Tuning(1, threads_per_copy, copies_per_cta, int(bool(row_walk)), 0.0, 0, int(bool(persistent)), int(kernel))
     _check(load().gbmc_set_tuning(dim, model, L, C.byref(t)))
 
 
@@ -409,6 +419,20 @@ def pa_schedule_log(pa, lattice=0) -> list:
         out.append({k: (list(getattr(r, k)) if k == "features" else getattr(r, k))
                     for k, _ in ScheduleRecord._fields_ if k != "pad"})
     return out
+
+
+def pa_state_save(ctx, pa) -> np.ndarray:
+    """The run's state between steps as a byte array (spins not included)."""
+    n = C.c_size_t()
+    _check(load().pa_state_bytes(pa, C.byref(n)))
+    buf = np.zeros(n.value, dtype=np.uint8)
+    _check(load().pa_state_save(ctx, pa, _ptr(buf), buf.nbytes))
+    return buf
+
+
+def pa_state_load(ctx, pa, state):
+    buf = np.ascontiguousarray(state, dtype=np.uint8)
+    _check(load().pa_state_load(ctx, pa, _ptr(buf), buf.nbytes))
 
 
 def pa_betas(pa, lattice=0) -> np.ndarray:
