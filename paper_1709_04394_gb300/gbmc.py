@@ -421,11 +421,15 @@ def pa_schedule_log(pa, lattice=0) -> list:
     return out
 
 
-def pa_state_save(ctx, pa) -> np.ndarray:
-    """The run's state between steps as a byte array (spins not included)."""
+def pa_state_bytes(pa) -> int:
     n = C.c_size_t()
     _check(load().pa_state_bytes(pa, C.byref(n)))
-    buf = np.zeros(n.value, dtype=np.uint8)
+    return n.value
+
+
+def pa_state_save(ctx, pa) -> np.ndarray:
+    """The run's state between steps as a byte array (spins not included)."""
+    buf = np.zeros(pa_state_bytes(pa), dtype=np.uint8)
     _check(load().pa_state_save(ctx, pa, _ptr(buf), buf.nbytes))
     return buf
 
