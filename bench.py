@@ -756,12 +756,31 @@ def kernel_name(w, prof):
     return "sweep_strips" if "sweep_strips" in prof else "sweep_tiles"
 
 
+def bits_lattice(dim, L):
+    """Lattice classes the bit-sliced resident kernel sweeps (its default)."""
+    return (dim == 2 and L in (64, 128, 256)) or (dim == 3 and L == 8)
+
+
+def dominant_share(w, kname):
+    """Share of the workload's site updates that the dominant kernel makes (a
+    mixed batch splits its lattices between the bit-sliced and byte-plane
+    kernels)."""
+    if w["kind"] != "pa" or kname not in ("sweep_bits", "sweep_resident"):
+        return 1.0
+    tot = sum(copies(l) * l[1] ** l[0] for l in w["lattices"])
+    mine = sum(copies(l) * l[1] ** l[0] for l in w["lattices"]
+               if bits_lattice(l[0], l[1]) == (kname == "sweep_bits"))
+    return mine / tot
+
+
 def alg_bytes_per_update(w, kname):
     """Algorithmic HBM bytes per site update of the dominant kernel."""
     if w["kind"] == "pa":
         # per launch each copy is read (through the parent map) and written once, plus E, M, parent
-        tot_upd = sum(copies(l) * l[1] ** l[0] for l in w["lattices"])
-        tot_bytes = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in w["lattices"])
+        lat = [l for l in w["lattices"] if kname not in ("sweep_bits", "sweep_resident")
+               or bits_lattice(l[0], l[1]) == (kname == "sweep_bits")] or w["lattices"]
+        tot_upd = sum(copies(l) * l[1] ** l[0] for l in lat)
+        tot_bytes = sum(copies(l) * (2 * l[1] ** l[0] + 12) for l in lat)
         return tot_bytes / (tot_upd * w["theta"])
     if w["kind"] == "pt":
         return 2.0 / w["theta"]
@@ -791,7 +810,7 @@ def gpu_record(w, workload, res, ws):
         n_l //= 3  # one update = bond, union and flip launches
     # launches that updated sites: every PA run has one measurement-only launch (step 0)
     n_sweeping = n_l * w["S"] // (w["S"] + 1) if w["kind"] == "pa" else n_l
-    upd = res["upd_prof"]  # site updates of the profiled pass, all made by the dominant kernel
+    upd = res["upd_prof"] * dominant_share(w, kname)  # site updates of the profiled pass made by that kernel
     secs = t_l * 1e-3
     alg_ops = ALG_INT_OPS_PER_MSC_UPDATE if w.get("msc") else ALG_INT_OPS_PER_SITE_UPDATE
     achieved = alg_ops * upd / secs / 1e9 if secs else float("nan")  # Gop/s

@@ -63,6 +63,14 @@ typedef struct gbmc_pt gbmc_pt;
 
 /* Library version (major*10000 + minor*100 + patch). */
 int gbmc_version(void);
+/* 1 for the bounds-checked build (libgbmc_check.so, compiled with GBMC_CHECK):
+ * its kernels verify their array indices, replace a bad one by 0 (so the access
+ * stays in bounds) and record the first failure; gbmc_sync and every other
+ * call that checks the device's error flags then return GBMC_ERR_STATE with
+ * "bounds check failed in <file>:<line>". 0 for the normal build, which has no
+ * checks. The checked build is for testing small and uneven lattices, not for
+ * timing. */
+int32_t gbmc_checked_build(void);
 
 /* Message of the calling thread's last failed call ("" if none). The pointer
  * stays valid until the thread's next gbmc call. */

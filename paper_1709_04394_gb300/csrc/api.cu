@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/gbmc.h"
+#include "check.cuh"
 #include "internal.h"
 
 using namespace gbmc;
@@ -71,6 +72,19 @@ constexpr uint32_t kTile = 128;
 namespace gbmc {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_last_error(const char* msg) { g_err = msg; }
+#ifdef GBMC_CHECK
+namespace {
+struct CheckEntry {
+    CheckReader read;
+    const char* file;
+};
+std::vector<CheckEntry>& check_entries() {
+    static std::vector<CheckEntry> v;
+    return v;
+}
+}  // namespace
+void check_register(CheckReader reader, const char* file) { check_entries().push_back({reader, file}); }
+#endif
 }  // namespace gbmc
 
 struct gbmc_ctx {
@@ -479,6 +493,14 @@ extern "C" {
 
 int gbmc_version(void) { return 100; }
 
+int32_t gbmc_checked_build(void) {
+#ifdef GBMC_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char* gbmc_last_error(void) { return g_err.c_str(); }
 
 gbmc_status gbmc_create(gbmc_ctx** out, int device, void* cuda_stream) {
@@ -523,6 +545,15 @@ gbmc_status gbmc_set_stream(gbmc_ctx* ctx, void* cuda_stream) {
 // (word 1) and a population that outgrew its capacity (word 4); the stream
 // must have been synchronised.
 static gbmc_status check_device_error(gbmc_ctx* ctx) {
+#ifdef GBMC_CHECK
+    for (const auto& c : check_entries()) {
+        unsigned line = 0;
+        if (c.read(&line)) {
+            const char* f = std::strrchr(c.file, '/');
+            return fail(GBMC_ERR_STATE, "bounds check failed in %s:%u", f ? f + 1 : c.file, line);
+        }
+    }
+#endif
     unsigned int w[8] = {};
     CUDA_TRY(cudaMemcpy(w, ctx->words, sizeof(w), cudaMemcpyDeviceToHost));
     if (w[1]) {

@@ -21,6 +21,7 @@
 //    ranks 32 z .. 32 z + 31. Neighbours along x and y are rotations of the
 //    other plane's word, along z the words of the neighbouring lanes.
 #include "bits.cuh"
+#include "check.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -111,11 +112,12 @@ __device__ __forceinline__ void nb2(const uint32_t* oth, uint32_t idx, uint32_t 
                                     uint32_t& up, uint32_t& dn, uint32_t& same, uint32_t& side, uint32_t& q0) {
     const uint32_t Wm = (1u << lgW) - 1u;
     const uint32_t y = idx >> lgW, w = idx & Wm;
-    up = oth[(((y - 1u) & (L - 1u)) << lgW) + w];
-    dn = oth[(((y + 1u) & (L - 1u)) << lgW) + w];
-    same = oth[idx];
+    const uint32_t PW = L << lgW;
+    up = oth[GBMC_IDX((((y - 1u) & (L - 1u)) << lgW) + w, PW)];
+    dn = oth[GBMC_IDX((((y + 1u) & (L - 1u)) << lgW) + w, PW)];
+    same = oth[GBMC_IDX(idx, PW)];
     const bool odd = ((y + colour) & 1u) != 0u;
-    const uint32_t nbw = oth[(y << lgW) + ((odd ? w + 1u : w - 1u) & Wm)];
+    const uint32_t nbw = oth[GBMC_IDX((y << lgW) + ((odd ? w + 1u : w - 1u) & Wm), PW)];
     side = odd ? __funnelshift_r(same, nbw, 1) : __funnelshift_l(nbw, same, 1);
     q0 = y * (L >> 3) + 8u * w;
 }
@@ -138,8 +140,9 @@ __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ Swe
     uint8_t* smb = reinterpret_cast<uint8_t*>(sm);
 
     // ---- load: int8 rows -> bit planes (16 bytes = 8 even-x + 8 odd-x sites per lane and step) ----
+    const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
     const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
-    const uint4* g = reinterpret_cast<const uint4*>(J.src + srcslot * N);
+    const uint4* g = reinterpret_cast<const uint4*>(J.src + GBMC_IDX(srcslot, ncopies) * N);
     for (uint32_t c16 = lane; c16 < (N >> 4); c16 += 32u) {
         const uint4 v = g[c16];
         uint32_t e0, o0, e1, o1;
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ Swe
         const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
         const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);  // byte of the plane
         const uint32_t ce = y & 1u;                                             // colour of the even-x sites
-        smb[(ce * PW << 2) + b] = (uint8_t)(e0 | (e1 << 4));
-        smb[((ce ^ 1u) * PW << 2) + b] = (uint8_t)(o0 | (o1 << 4));
+        smb[GBMC_IDX((ce * PW << 2) + b, words_per_warp * 4u)] = (uint8_t)(e0 | (e1 << 4));
+        smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + b, words_per_warp * 4u)] = (uint8_t)(o0 | (o1 << 4));
     }
     __syncwarp();
 
@@ -210,7 +213,8 @@ __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ Swe
             const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
             const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);
             const uint32_t ce = y & 1u;
-            const uint32_t ev = smb[(ce * PW << 2) + b], od = smb[((ce ^ 1u) * PW << 2) + b];
+            const uint32_t ev = smb[GBMC_IDX((ce * PW << 2) + b, words_per_warp * 4u)];
+            const uint32_t od = smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + b, words_per_warp * 4u)];
             const uint2 lo = unpack8(ev & 15u, od & 15u), hi = unpack8(ev >> 4, od >> 4);
             d[c16] = make_uint4(lo.x, lo.y, hi.x, hi.y);
         }
@@ -289,7 +293,8 @@ __global__ void __launch_bounds__(128) k_sweep_bits3(const __grid_constant__ Swe
     for (uint32_t c = 0; c < 2; ++c)
 #pragma unroll
         for (uint32_t k = 0; k < 6; ++k)
-            jb[c][k] = (EA && active) ? J.jb3[(((uint64_t)inst * 2u + c) * 6u + k) * 8u + z] : 0u;
+            jb[c][k] = (EA && active) ? J.jb3[GBMC_IDX((((uint64_t)inst * 2u + c) * 6u + k) * 8u + z, J.n_inst * 96ull)]
+                                      : 0u;
 
     uint32_t T4, T8, T12;
     copy_thresholds(J, active ? slot : 0, T4, T8, T12);

@@ -26,6 +26,7 @@
 #include <climits>
 
 #include "../../include/gbmc.h"
+#include "check.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -64,7 +65,7 @@ __device__ __forceinline__ void phase_weights(const PaLattice& P, uint32_t inst,
     for (int i = 0; i < kPerThread; ++i) {
         const uint32_t j = j0 + i;
         unsigned long long v = 0;
-        if (j < live) v = P.wint[(uint32_t)(P.E[base + j] - emin) >> 2];
+        if (j < live) v = P.wint[GBMC_IDX((uint32_t)(P.E[base + j] - emin) >> 2, P.nbins)];
         run += v;
         w[i] = run;
     }
@@ -90,7 +91,7 @@ __device__ __forceinline__ void phase_reduce(const PaLattice& P, uint32_t inst, 
         const uint32_t bmin = (uint32_t)(emin - P.e_lo) >> 2, bmax = (uint32_t)(emax - P.e_lo) >> 2;
         for (uint32_t b = bmin + threadIdx.x; b <= bmax; b += blockDim.x) {
             const uint32_t hb = h[b];
-            if (hb) acc += (double)hb * P.wexp[b - bmin];
+            if (hb) acc += (double)hb * P.wexp[GBMC_IDX(b - bmin, P.nbins)];
             h[b] = 0u;
         }
     }
@@ -152,7 +153,7 @@ __device__ __forceinline__ void phase_draw(const PaLattice& P, uint64_t g) {
         if (__ldcg(P.cloc + base + mid) > xr) b = mid;
         else a = mid + 1;
     }
-    atomicAdd(&P.counts[base + a], 1u);
+    atomicAdd(&P.counts[base + GBMC_IDX(a, P.R)], 1u);
 }
 
 // Nearest-integer copies of replica g (global over the lattice's populations):
@@ -285,7 +286,7 @@ __device__ __forceinline__ void phase_place(const PaLattice& P, uint32_t inst, u
                     atomicExch(P.overflow, 1u);
                     break;
                 }
-                P.parent[base + S + m] = j;
+                P.parent[base + GBMC_IDX(S + m, P.R)] = j;
             }
             P.counts[base + j] = 0u;
         }

@@ -15,6 +15,7 @@
 //  * k_halfsweep_global: one colour of one sweep straight on global memory, for
 //    lattices too large for shared memory (one launch per half-sweep, the
 //    kernel-boundary synchronisation described in Sec. 3.1).
+#include "check.cuh"
 #include "device.cuh"
 #include "internal.h"
 #include "units.cuh"
@@ -166,13 +167,15 @@ __device__ __forceinline__ void resident_unit(const SweepLaunch& P, uint32_t uni
             const uint32_t c = idx / chunks, ch = idx - c * chunks;
             const uint32_t row = ch / W;
             const uint64_t slot = slot0 + c;
-            const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
-            const uint2 v = *reinterpret_cast<const uint2*>(J.src + srcslot * N + (uint64_t)ch * 8);
+            const uint64_t srcslot =
+                J.parent ? (uint64_t)inst * J.R + J.parent[GBMC_IDX(slot, (uint64_t)J.n_inst * J.R)] : slot;
+            const uint2 v = *reinterpret_cast<const uint2*>(
+                J.src + GBMC_IDX(srcslot * N + (uint64_t)ch * 8, (uint64_t)J.n_inst * J.R * N - 7));
             const uint32_t y = DIM == 3 ? row % L : row, z = DIM == 3 ? row / L : 0;
             const uint32_t pe = (y + z) & 1u;
             uint32_t* pl = reinterpret_cast<uint32_t*>(smem + c * stride_b);
-            pl[pe * (H >> 2) + ch] = __byte_perm(v.x, v.y, 0x6420);
-            pl[(pe ^ 1u) * (H >> 2) + ch] = __byte_perm(v.x, v.y, 0x7531);
+            pl[GBMC_IDX(pe * (H >> 2) + ch, N >> 2)] = __byte_perm(v.x, v.y, 0x6420);
+            pl[GBMC_IDX((pe ^ 1u) * (H >> 2) + ch, N >> 2)] = __byte_perm(v.x, v.y, 0x7531);
         }
         if (EA) {
             const uint4* jsrc = reinterpret_cast<const uint4*>(J.jsplit + (uint64_t)inst * 6 * N);
@@ -300,7 +303,8 @@ __device__ __forceinline__ void resident_unit(const SweepLaunch& P, uint32_t uni
                 uint2 v;
                 v.x = __byte_perm(ev, od, 0x5140);
                 v.y = __byte_perm(ev, od, 0x7362);
-                *reinterpret_cast<uint2*>(J.dst + (slot0 + cc) * N + (uint64_t)ch * 8) = v;
+                *reinterpret_cast<uint2*>(
+                    J.dst + GBMC_IDX((slot0 + cc) * N + (uint64_t)ch * 8, (uint64_t)J.n_inst * J.R * N - 7)) = v;
             }
         } else {
             const uint32_t nw = N >> 2;

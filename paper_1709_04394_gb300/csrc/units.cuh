@@ -16,6 +16,7 @@
 // works on the row-major layout with 8-byte chunks; L % 8 != 0 uses a per-site
 // path with the same Philox words.
 #pragma once
+#include "check.cuh"
 #include "device.cuh"
 
 namespace gbmc {
@@ -47,11 +48,11 @@ __device__ __forceinline__ void unit_swar(uint8_t* sp, const uint8_t* jb, uint32
     const uint32_t gr = g + 1 == G ? 0 : g + 1;
     const uint32_t rowu = y == 0 ? row + L - 1 : row - 1;       // y - 1
     const uint32_t rowd = y + 1 == L ? row + 1 - L : row + 1;   // y + 1
-    const uint64_t cur = ld8(sp + base + 8 * g);
-    const uint64_t prv = ld8(sp + base + 8 * gl);
-    const uint64_t nxt = ld8(sp + base + 8 * gr);
-    const uint64_t up = ld8(sp + rowu * L + 8 * g);
-    const uint64_t dn = ld8(sp + rowd * L + 8 * g);
+    const uint64_t cur = ld8(sp + GBMC_IDX(base + 8 * g, N - 7));
+    const uint64_t prv = ld8(sp + GBMC_IDX(base + 8 * gl, N - 7));
+    const uint64_t nxt = ld8(sp + GBMC_IDX(base + 8 * gr, N - 7));
+    const uint64_t up = ld8(sp + GBMC_IDX(rowu * L + 8 * g, N - 7));
+    const uint64_t dn = ld8(sp + GBMC_IDX(rowd * L + 8 * g, N - 7));
     const uint64_t dc = down_bits(cur);
     uint64_t lft = down_bits((cur << 8) | (prv >> 56));
     uint64_t rgt = down_bits((cur >> 8) | (nxt << 56));
@@ -61,8 +62,8 @@ __device__ __forceinline__ void unit_swar(uint8_t* sp, const uint8_t* jb, uint32
     if (DIM == 3) {
         rowb = z == 0 ? row + (L - 1) * L : row - L;              // z - 1
         const uint32_t rowf = z + 1 == L ? row - (L - 1) * L : row + L;  // z + 1
-        bkb = down_bits(ld8(sp + rowb * L + 8 * g));
-        frb = down_bits(ld8(sp + rowf * L + 8 * g));
+        bkb = down_bits(ld8(sp + GBMC_IDX(rowb * L + 8 * g, N - 7)));
+        frb = down_bits(ld8(sp + GBMC_IDX(rowf * L + 8 * g, N - 7)));
     }
     if (EA) {
         // bond planes: byte 1 where J = -1; an unsatisfied bond has d_i ^ d_j ^ b = 1
@@ -128,14 +129,15 @@ __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint3
     uint32_t* own = reinterpret_cast<uint32_t*>(sp + colour * H);
     const uint32_t* oth = reinterpret_cast<const uint32_t*>(sp + (colour ^ 1u) * H);
     const uint32_t rw = row * W;
-    const uint32_t cur = own[rw + g];
-    const uint32_t same = oth[rw + g];
+    const uint32_t PW = H >> 2;  // words per colour plane
+    const uint32_t cur = own[GBMC_IDX(rw + g, PW)];
+    const uint32_t same = oth[GBMC_IDX(rw + g, PW)];
     // horizontal neighbour not sharing j: j+1 (odd x) or j-1 (even x)
-    const uint32_t side = o ? __funnelshift_r(same, oth[rw + (g + 1 == W ? 0 : g + 1)], 8)
-                            : __funnelshift_l(oth[rw + (g == 0 ? W - 1 : g - 1)], same, 8);
+    const uint32_t side = o ? __funnelshift_r(same, oth[GBMC_IDX(rw + (g + 1 == W ? 0 : g + 1), PW)], 8)
+                            : __funnelshift_l(oth[GBMC_IDX(rw + (g == 0 ? W - 1 : g - 1), PW)], same, 8);
     const uint32_t rowu = y == 0 ? row + L - 1 : row - 1;
     const uint32_t rowd = y + 1 == L ? row + 1 - L : row + 1;
-    const uint32_t up = oth[rowu * W + g], dn = oth[rowd * W + g];
+    const uint32_t up = oth[GBMC_IDX(rowu * W + g, PW)], dn = oth[GBMC_IDX(rowd * W + g, PW)];
     uint32_t a4;
     const uint32_t* b = EA ? reinterpret_cast<const uint32_t*>(jb) + rw + g : nullptr;
     const uint32_t P = H >> 2;  // words per plane
@@ -148,7 +150,7 @@ __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint3
     if (DIM == 3) {
         const uint32_t rowb = z == 0 ? row + (L - 1) * L : row - L;
         const uint32_t rowf = z + 1 == L ? row - (L - 1) * L : row + L;
-        const uint32_t bk = oth[rowb * W + g], fr = oth[rowf * W + g];
+        const uint32_t bk = oth[GBMC_IDX(rowb * W + g, PW)], fr = oth[GBMC_IDX(rowf * W + g, PW)];
         if (EA) a4 += (neq4(cur, bk) ^ b[4 * P]) + (neq4(cur, fr) ^ b[5 * P]);
         else a4 += neq4(cur, bk) + neq4(cur, fr);
     }
@@ -165,7 +167,7 @@ __device__ __forceinline__ void unit_split(uint8_t* sp, const uint8_t* jb, uint3
     }
     const uint32_t nw = cur ^ flip;
     if constexpr (STORE) {
-        if (doflip) own[rw + g] = nw;
+        if (doflip) own[GBMC_IDX(rw + g, PW)] = nw;
     } else {
         *st_idx = rw + g;
         *st_val = nw;
@@ -211,7 +213,8 @@ __device__ __forceinline__ void unit_scalar(int8_t* sp, const uint8_t* jb, uint3
             jd = jb[N + i] ? -1 : 1;
             ju = jb[N + i_u] ? -1 : 1;
         }
-        int h = jl * sp[i_l] + jr * sp[i_r] + ju * sp[i_u] + jd * sp[i_d];
+        int h = jl * sp[GBMC_IDX(i_l, N)] + jr * sp[GBMC_IDX(i_r, N)] + ju * sp[GBMC_IDX(i_u, N)] +
+                jd * sp[GBMC_IDX(i_d, N)];
         if (DIM == 3) {
             const uint32_t zbk = z == 0 ? L - 1 : z - 1, zf = z + 1 == L ? 0 : z + 1;
             const uint32_t i_b = (zbk * L + y) * L + x, i_f = (zf * L + y) * L + x;
@@ -219,9 +222,9 @@ __device__ __forceinline__ void unit_scalar(int8_t* sp, const uint8_t* jb, uint3
                 jf = jb[2 * N + i] ? -1 : 1;
                 jbk = jb[2 * N + i_b] ? -1 : 1;
             }
-            h += jbk * sp[i_b] + jf * sp[i_f];
+            h += jbk * sp[GBMC_IDX(i_b, N)] + jf * sp[GBMC_IDX(i_f, N)];
         }
-        const int si = sp[i];
+        const int si = sp[GBMC_IDX(i, N)];
         const int dE = 2 * si * h;
         const uint32_t u = m == 0 ? w.x : m == 1 ? w.y : m == 2 ? w.z : w.w;
         const uint32_t thr = dE == 4 ? T.t4 : (dE == 8 ? T.t8 : T.t12);

@@ -16,7 +16,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgbmc.so")
+# GBMC_LIBRARY=libgbmc_check.so selects the bounds-checked build (same directory)
+LIB_PATH = os.path.join(_HERE, os.path.basename(os.environ.get("GBMC_LIBRARY", "libgbmc.so")))
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "gbmc.h")
 
 GBMC_OK, GBMC_ERR_ARG, GBMC_ERR_OOM, GBMC_ERR_CUDA, GBMC_ERR_TIMEOUT, GBMC_ERR_STATE = 0, -1, -2, -3, -4, -5
@@ -100,6 +101,7 @@ def load():
         p, st = C.c_void_p, C.c_int
         sig = {
             "gbmc_version": ([], C.c_int),
+            "gbmc_checked_build": ([], C.c_int32),
             "gbmc_last_error": ([], C.c_char_p),
             "gbmc_create": ([C.POINTER(C.c_void_p), C.c_int, p], st),
             "gbmc_set_stream": ([p, p], st),
@@ -214,6 +216,10 @@ def gbmc_set_resample_mode(ctx, fused=True):
 
 def gbmc_set_sweep_launch(ctx, mode=GBMC_LAUNCH_AUTO):
     _check(load().gbmc_set_sweep_launch(ctx, int(mode)))
+
+
+def gbmc_checked_build() -> bool:
+    return bool(load().gbmc_checked_build())
 
 
 def gbmc_set_sweep_kernel(ctx, kernel=GBMC_KERNEL_AUTO):

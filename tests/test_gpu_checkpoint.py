@@ -50,7 +50,7 @@ def test_pa_run_is_reproducible_from_seed(ctx):
     gbmc.lattice_free(lat)
 
 
-def _pa_run_split(ctx, make_lats, k, cfg, steps_whole=None):
+def _pa_run_split(ctx, make_lats, k, cfg, insts=None):
     """A whole annealing run, and the same run stopped after k steps, saved
     (state + spins), restored into a new run on new lattices and finished."""
     lats = make_lats()
@@ -81,9 +81,20 @@ def _pa_run_split(ctx, make_lats, k, cfg, steps_whole=None):
     got, n_got = gbmc.pa_run(ctx, pa, capacity=cfg["n_steps"] + 1)
     assert n_got == ref["n"]
     np.testing.assert_array_equal(got, ref["stats"])
+    pop = 0
     for i, l in enumerate(lats):
-        np.testing.assert_array_equal(spins_out(ctx, l), ref["spins"][i])
-        np.testing.assert_array_equal(_parents(ctx, pa, i, l), ref["parents"][i])
+        info = gbmc.lattice_info(l)
+        # spins and parents of the live slots (with a variable population the
+        # slots beyond it hold stale values)
+        n_inst = insts[i] if insts else 1
+        R = info.n_copies // n_inst
+        sp, sp_ref = spins_out(ctx, l).reshape(n_inst, R, -1), ref["spins"][i].reshape(n_inst, R, -1)
+        par, par_ref = _parents(ctx, pa, i, l).reshape(n_inst, R), ref["parents"][i].reshape(n_inst, R)
+        for k in range(n_inst):
+            live = int(got[n_got, pop + k]["n_replicas"]) if "resample" in cfg else R
+            np.testing.assert_array_equal(sp[k, :live], sp_ref[k, :live])
+            np.testing.assert_array_equal(par[k, :live], par_ref[k, :live])
+        pop += n_inst
         np.testing.assert_array_equal(gbmc.pa_betas(pa, i), ref["betas"][i])
     gbmc.pa_free(pa)
     for l in lats:
@@ -114,7 +125,7 @@ def test_pa_split_at_step_k_equals_whole_run_adaptive_and_variable(ctx):
     def make_ea():
         return [gbmc.lattice_init(ctx, 3, 8, model=gbmc.GBMC_EA_PMJ, n_instances=3, n_replicas=500, seed=12)]
     _pa_run_split(ctx, make_ea, 4, dict(theta=2, n_steps=8, beta_f=2.0, resample=gbmc.GBMC_RESAMPLE_NEAREST,
-                                        initial_replicas=400))
+                                        initial_replicas=400), insts=[3])
 
 
 def test_pa_state_load_rejects_another_configuration(ctx):
