@@ -59,11 +59,11 @@ gbmc.gbmc_set_sweep_kernel(ctx, gbmc.GBMC_KERNEL_AUTO)
 
 # annealing: multinomial (mixed sizes), nearest-integer and Poisson laws, 3D +-J instances
 lats = [gbmc.lattice_init(ctx, 2, 4, n_replicas=37, seed=5, instance_base=0),
-        gbmc.lattice_init(ctx, 2, 8, n_replicas=29, seed=5, instance_base=1),
+        gbmc.lattice_init(ctx, 2, 8, n_replicas=45, seed=5, instance_base=1),
         gbmc.lattice_init(ctx, 2, 64, n_replicas=9, seed=5, instance_base=2)]
 pa = gbmc.pa_create(ctx, lats, 2, 4)
 stats, _ = gbmc.pa_run(ctx, pa, capacity=5)
-ref = oracle.pa_run(2, 8, 5, 1, 29, oracle.linear_betas(1.0, 4), 2)
+ref = oracle.pa_run(2, 8, 5, 1, 45, oracle.linear_betas(1.0, 4), 2)
 assert np.array_equal(stats[:, 1]["sumE"], ref["sumE"])
 gbmc.pa_free(pa)
 for l in lats:
