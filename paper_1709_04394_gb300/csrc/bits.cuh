@@ -23,6 +23,46 @@ __device__ __forceinline__ void accept_bits(uint32_t& r4, uint32_t& r8, uint32_t
         : "r"(T4), "r"(T8), "r"(u));
 }
 
+// Philox4x32-10 of philox_q (device.cuh) with each 32 x 32 -> 64-bit product
+// as one wide multiply (both halves from one instruction): the same words,
+// fewer multiply-pipe instructions in the bit-sliced updates, where the
+// products dominate that pipe.
+__device__ __forceinline__ void mulhilo_wide(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    uint64_t p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
+__device__ __forceinline__ uint4 philox_q_wide(const PhiloxFixed& f, uint32_t q) {
+    uint32_t x, y;
+    mulhilo_wide(kPhiloxM0, q, x, y);
+    x ^= f.x0;
+    uint32_t h1, l1;
+    mulhilo_wide(kPhiloxM1, x, h1, l1);
+    uint4 c = make_uint4(h1 ^ f.b1, l1, f.u1 ^ y, f.v1);
+    uint32_t k0 = f.k0, k1 = f.k1;
+#pragma unroll
+    for (int round = 2; round < 10; ++round) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo_wide(kPhiloxM0, c.x, hi0, lo0);
+        mulhilo_wide(kPhiloxM1, c.z, hi1, lo1);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+// r = 2 r + [u <= T]: one comparison.
+__device__ __forceinline__ void accept_bit(uint32_t& r, uint32_t T, uint32_t u) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %2;\n\t"
+        "addc.u32 %0, %0, %0;\n\t}"
+        : "+r"(r)
+        : "r"(T), "r"(u));
+}
+
 // r4, r8, r12 shifted by one bit each: three comparisons of u (3D, dE = 4,
 // 8, 12).
 __device__ __forceinline__ void accept_bits3(uint32_t& r4, uint32_t& r8, uint32_t& r12, uint32_t T4, uint32_t T8,
@@ -51,7 +91,7 @@ __device__ __forceinline__ uint32_t bp_word_update(uint32_t s, uint32_t up, uint
     uint32_t r4 = 0, r8 = 0;                 // bit b of the word at bit 31 - b
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) {
-        const uint4 v = philox_q(pf, q0 + i);
+        const uint4 v = philox_q_wide(pf, q0 + i);
         accept_bits(r4, r8, T4, T8, v.x);
         accept_bits(r4, r8, T4, T8, v.y);
         accept_bits(r4, r8, T4, T8, v.z);
@@ -81,7 +121,7 @@ __device__ __forceinline__ uint32_t bp3_word_update(uint32_t s, uint32_t d0, uin
     uint32_t r4 = 0, r8 = 0, r12 = 0;
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) {
-        const uint4 v = philox_q(pf, q0 + i);
+        const uint4 v = philox_q_wide(pf, q0 + i);
         accept_bits3(r4, r8, r12, T4, T8, T12, v.x);
         accept_bits3(r4, r8, r12, T4, T8, T12, v.y);
         accept_bits3(r4, r8, r12, T4, T8, T12, v.z);
