@@ -730,7 +730,10 @@ def main():
     print(json.dumps(line))
 
 
-# Secondary records of the default run: the other configurations of the path,
+# Secondary records of the default run: the other configurations of the path
+# (single L = 4096 lattice, int8 and bit-packed; 3D +-J and mixed-size
+# annealing) and of its variants (multi-spin coding, nearest-integer
+# resampling, parallel tempering, double checkerboard, Swendsen-Wang), with
 # (timed steps, warm-up steps) each, so that the whole default run stays within
 # a few minutes.
 SECONDARY = {
@@ -738,6 +741,11 @@ SECONDARY = {
     "ising2d-L4096-bitpack": (10, 3),
     "pa-ea3d-L8": (3, 3),
     "pa-mixed-2d": (3, 3),
+    "pa-ising2d-L64-msc": (3, 3),
+    "pa-ising2d-L64-nearest": (3, 3),
+    "pt-ea3d-L8": (3, 3),
+    "ising2d-L4096-dcb": (5, 3),
+    "ising2d-L4096-sw": (3, 3),
 }
 
 

@@ -1018,9 +1018,7 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
     CUDA_TRY(cudaSetDevice(ctx->device));
     if (!l->sw_parent) {
         const bool tiled = sw_tiled((uint32_t)l->d.dim, (uint32_t)l->d.L);
-        // forest (4 bytes per site) and, for 2D tiles, one run mask per tile row (1/8 byte per site)
-        const uint64_t extra = tiled && l->d.dim == 2 ? l->N / 8 : 0;
-        cudaError_t e = cudaMalloc(&l->sw_parent, (4 * l->N + extra) * l->ncopies);
+        cudaError_t e = cudaMalloc(&l->sw_parent, 4 * l->N * l->ncopies);
         if (e == cudaSuccess && !tiled) e = cudaMalloc(&l->sw_bonds, l->N * l->ncopies);
         if (e != cudaSuccess) {
             cudaFree(l->sw_parent);
@@ -1034,7 +1032,6 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
     P.spins = l->cur;
     P.bonds = l->sw_bonds;
     P.parent = l->sw_parent;
-    if (sw_tiled((uint32_t)l->d.dim, (uint32_t)l->d.L) && l->d.dim == 2) P.runs = l->sw_parent + l->N * l->ncopies;
     P.err = ctx->words + 1;
     P.seed = l->d.seed;
     // T_bond = ceil(p 2^32) - 1, p = 1 - exp(-2 beta): "r < p" as an integer comparison

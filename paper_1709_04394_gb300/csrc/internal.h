@@ -175,7 +175,6 @@ struct SwLaunch {
     uint8_t* bonds;           // [copies][N] bit mu: forward bond along mu active
     uint32_t* parent;         // [copies][N] union-find forest
     int32_t* labels;          // [copies][N] cluster name (smallest site) of every site, or null
-    uint32_t* runs;           // 2D tiled: [copies][N / 32] run-start mask of every tile row
     unsigned int* err;        // raised if a hook loop ran out of its cap
     uint64_t seed;
     uint64_t copy0;

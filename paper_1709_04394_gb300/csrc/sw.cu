@@ -34,24 +34,6 @@
 // Each component again ends rooted at its smallest site (a hook always puts
 // the larger root under the smaller), so the labels and coins do not depend
 // on the order of the unions.
-//
-// 2D tiles by rows (L % 32 == 0; the 2D tiled path): one warp per 32 x 32
-// tile, lane y holding tile row y as 32-bit masks:
-//  k_sw_local_rows : spins -> a down mask; the row's 16 Philox calls give the
-//                    x and y bond words of its 32 sites (bond b = 2 i + mu,
-//                    call b >> 2, word b & 3); activation by bit-sliced
-//                    comparisons. Runs along x are the intervals between
-//                    inactive x bonds, each represented by its first site; the
-//                    y bonds unite runs of neighbouring rows (one union per
-//                    pair of overlapping runs) in a shared-memory union-find
-//                    over run starts; every site's parent becomes its tile
-//                    component's smallest site, and the row's run-start mask
-//                    is kept for the flip;
-//  k_sw_cross      : as above (bonds leaving the tile, global forest);
-//  k_sw_flip_rows  : per run, the root of its first site (global forest; the
-//                    roots of the tile's local components are cached in shared
-//                    memory) and the root's coin; the flips of a row are one
-//                    mask applied to its 32 spins.
 #include "bits.cuh"
 #include "device.cuh"
 #include "internal.h"
@@ -130,10 +112,11 @@ __device__ __forceinline__ void sw_bond_flags_row(const SwLaunch& P, const int8_
         dif[2] = own ^ *reinterpret_cast<const uint32_t*>(s + (z + 1 == L ? i0 - (L - 1) * LL : i0 + LL));
     }
     flags[0] = flags[1] = flags[2] = flags[3] = 0u;
+    // the same words as philox4x32_10((q, t, r, c3)): t, r and c3 hoisted, wide products
+    const PhiloxFixed pf = philox_fix(P.t, r, c3, (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
 #pragma unroll
     for (uint32_t c = 0; c < DIM; ++c) {
-        const uint4 w = philox4x32_10(make_uint4((DIM * i0) / 4 + c, P.t, r, c3), (uint32_t)P.seed,
-                                      (uint32_t)(P.seed >> 32));
+        const uint4 w = philox_q_wide(pf, (DIM * i0) / 4 + c);
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             const uint32_t n = (4 * c + k) / DIM, mu = (4 * c + k) % DIM;
@@ -321,8 +304,8 @@ __global__ void __launch_bounds__(256) k_sw_flip(const __grid_constant__ SwLaunc
     if (P.labels) P.labels[copy * P.N + i] = (int32_t)root;
 }
 
-__device__ __forceinline__ uint32_t sw_coin(const SwLaunch& P, uint32_t root, uint32_t r, uint32_t c3) {
-    const uint4 w = philox4x32_10(make_uint4(root >> 2, P.t, r, c3), (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+__device__ __forceinline__ uint32_t sw_coin(const PhiloxFixed& pf, uint32_t root) {
+    const uint4 w = philox_q_wide(pf, root >> 2);
     const uint32_t word = (root & 3u) == 0 ? w.x : (root & 3u) == 1 ? w.y : (root & 3u) == 2 ? w.z : w.w;
     return word >> 31;
 }
@@ -375,14 +358,15 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
         end[k] = cl;
     }
     // end nodes: the root in the global forest and its coin
-    const uint32_t c3 = c3_word(kPurposeSwFlip, 0u, P.inst_base + inst);
+    const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwFlip, 0u, P.inst_base + inst), (uint32_t)P.seed,
+                                      (uint32_t)(P.seed >> 32));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (end[k] != l0 + k) continue;
         const uint32_t p = tpar[l0 + k];
         const uint32_t root = p == i0 + k ? p : sw_find<true>(par, p);
         troot[l0 + k] = root;
-        tcoin[l0 + k] = (uint8_t)sw_coin(P, root, r, c3);
+        tcoin[l0 + k] = (uint8_t)sw_coin(pf, root);
     }
     __syncthreads();
     // i0 % 4 == 0 and the spin buffer is 16-byte aligned: one word per thread
@@ -401,198 +385,6 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
     }
 }
 
-// ---- 2D tiles by rows ----
-constexpr uint32_t kSwRowWarps = 4;  // tiles per block
-
-// Down mask of 16 bytes of +-1 spins: bit i = byte i is -1.
-__device__ __forceinline__ uint32_t sw_down16(uint4 v) {
-    auto nib = [](uint32_t w) { return ((w & 0x80808080u) * 0x00204081u) >> 28; };
-    return nib(v.x) | (nib(v.y) << 4) | (nib(v.z) << 8) | (nib(v.w) << 12);
-}
-
-// First site of the run holding site x (bit x of the run-start mask R; bit 0 is always set).
-__device__ __forceinline__ uint32_t sw_run_start(uint32_t R, uint32_t x) {
-    return 31u - __clz(R & (0xFFFFFFFFu >> (31u - x)));
-}
-
-// Shared-memory slot of tile-local site id = 32 y + x: one word of padding per
-// row, so that the 32 lanes (one row each) hit 32 different banks.
-__device__ __forceinline__ uint32_t sw_slot(uint32_t id) { return id + (id >> 5); }
-
-// find / unite of the row kernels' union-find over local site ids (parents
-// only ever move to smaller ids, as in sw_find / sw_unite).
-__device__ __forceinline__ uint32_t sw_rfind(uint32_t* lp, uint32_t x) {
-    volatile uint32_t* v = lp;
-    uint32_t cur = v[sw_slot(x)];
-    if (cur == x) return x;
-    uint32_t prev = x, next;
-    while (cur > (next = v[sw_slot(cur)])) {
-        v[sw_slot(prev)] = next;  // path halving
-        prev = cur;
-        cur = next;
-    }
-    return cur;
-}
-
-__device__ __forceinline__ void sw_runite(uint32_t* lp, uint32_t a, uint32_t b, unsigned int* err) {
-    uint32_t ra = sw_rfind(lp, a), rb = sw_rfind(lp, b);
-    uint32_t n = 0;
-    while (ra != rb) {
-        if (ra > rb) {
-            const uint32_t t = ra;
-            ra = rb;
-            rb = t;
-        }
-        const uint32_t old = atomicMin(lp + sw_slot(rb), ra);  // hook the larger root under the smaller
-        if (old == rb) break;
-        rb = sw_rfind(lp, old);
-        ra = sw_rfind(lp, ra);
-        if (++n == kSwHookCap) {
-            atomicExch(err, 1u);
-            break;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(32 * kSwRowWarps) k_sw_local_rows(const __grid_constant__ SwLaunch P) {
-    __shared__ uint32_t lp_all[kSwRowWarps][1056];  // union-find over run starts (slot sw_slot(id))
-    __shared__ uint16_t rt_all[kSwRowWarps][1056];  // root id of each run, at its start's slot
-    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    const uint32_t L = P.L, ntx = L >> 5;
-    const uint32_t tile = blockIdx.x * kSwRowWarps + wib;
-    if (tile >= ntx * ntx) return;  // whole warp; the kernel has no block barrier
-    const uint64_t copy = P.copy0 + blockIdx.y;
-    uint32_t* lp = lp_all[wib];
-    uint16_t* rt = rt_all[wib];
-    uint32_t inst, r;
-    split_copy(copy, P.R, inst, r);
-    const uint32_t bx = tile % ntx, by = tile / ntx, y = lane, row = y * 32u;
-    const uint32_t rb = (by * 32u + y) * L + bx * 32u;  // global index of the row's first site (even)
-    const int8_t* s = P.spins + copy * P.N;
-    const uint32_t S = sw_down16(*reinterpret_cast<const uint4*>(s + rb)) |
-                       (sw_down16(*reinterpret_cast<const uint4*>(s + rb + 16)) << 16);
-    const uint32_t Sn = __shfl_down_sync(0xffffffffu, S, 1);  // row y + 1
-    // bonds to the right (x < 31) and down (y < 31) that stay inside the tile, between equal spins
-    const uint32_t ex = ~(S ^ (S >> 1)) & 0x7FFFFFFFu;
-    const uint32_t ey = y < 31u ? ~(S ^ Sn) : 0u;
-    uint32_t X = 0u, Y = 0u;
-    if (P.T_bond >= 0) {
-        const uint32_t T = (uint32_t)P.T_bond;
-        const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst), (uint32_t)P.seed,
-                                          (uint32_t)(P.seed >> 32));
-        uint32_t ax = 0u, ay = 0u;  // site x's bit at 31 - x
-#pragma unroll 4
-        for (uint32_t k = 0; k < 16; ++k) {
-            // call k covers sites 2k, 2k + 1: (x bond, y bond) of each
-            const uint4 w = philox_q_wide(pf, (rb >> 1) + k);
-            accept_bit(ax, T, w.x);
-            accept_bit(ay, T, w.y);
-            accept_bit(ax, T, w.z);
-            accept_bit(ay, T, w.w);
-        }
-        X = __brev(ax) & ex;
-        Y = __brev(ay) & ey;
-    }
-    // runs along x: a run starts where the bond from the left is inactive
-    const uint32_t R = ~(X << 1);
-    for (uint32_t m = R; m; m &= m - 1u) {
-        const uint32_t id = row + __ffs(m) - 1u;
-        lp[sw_slot(id)] = id;
-    }
-    __syncwarp();
-    // y bonds: one union per pair of overlapping runs of rows y and y + 1 (a bond
-    // joins the same pair as the bond left of it unless a run starts there in
-    // either row)
-    const uint32_t Rn = __shfl_down_sync(0xffffffffu, R, 1);
-    for (uint32_t U = Y & ~((Y << 1) & ~R & ~Rn); U; U &= U - 1u) {
-        const uint32_t x = __ffs(U) - 1u;
-        sw_runite(lp, row + sw_run_start(R, x), row + 32u + sw_run_start(Rn, x), P.err);
-    }
-    __syncwarp();
-    for (uint32_t m = R; m; m &= m - 1u) {
-        const uint32_t id = row + __ffs(m) - 1u;
-        rt[sw_slot(id)] = (uint16_t)sw_rfind(lp, id);
-    }
-    __syncwarp();
-    // parent of every site = its tile component's smallest site (global index)
-    uint32_t* par = P.parent + copy * P.N + rb;
-    const uint32_t gx0 = bx * 32u, gy0 = by * 32u;
-#pragma unroll
-    for (uint32_t c = 0; c < 8; ++c) {
-        uint32_t g[4];
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t root = rt[sw_slot(row + sw_run_start(R, 4u * c + k))];
-            g[k] = (gy0 + (root >> 5)) * L + gx0 + (root & 31u);
-        }
-        // rb % 4 == 0 and the forest is a cudaMalloc block: 16-byte aligned
-        reinterpret_cast<uint4*>(par)[c] = make_uint4(g[0], g[1], g[2], g[3]);
-    }
-    P.runs[copy * (P.N >> 5) + (rb >> 5)] = R;
-}
-
-__global__ void __launch_bounds__(32 * kSwRowWarps) k_sw_flip_rows(const __grid_constant__ SwLaunch P) {
-    __shared__ uint32_t croot_all[kSwRowWarps][1056];  // global root of a tile-local root, at its slot
-    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    const uint32_t L = P.L, ntx = L >> 5;
-    const uint32_t tile = blockIdx.x * kSwRowWarps + wib;
-    if (tile >= ntx * ntx) return;
-    const uint64_t copy = P.copy0 + blockIdx.y;
-    uint32_t* croot = croot_all[wib];
-    for (uint32_t i = lane; i < 1056u; i += 32u) croot[i] = 0xFFFFFFFFu;
-    __syncwarp();
-    uint32_t inst, r;
-    split_copy(copy, P.R, inst, r);
-    const uint32_t bx = tile % ntx, by = tile / ntx, y = lane;
-    const uint32_t rb = (by * 32u + y) * L + bx * 32u;
-    uint32_t* par = P.parent + copy * P.N;
-    const uint32_t R = P.runs[copy * (P.N >> 5) + (rb >> 5)];
-    const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwFlip, 0u, P.inst_base + inst), (uint32_t)P.seed,
-                                      (uint32_t)(P.seed >> 32));
-    const uint32_t gx0 = bx * 32u, gy0 = by * 32u;
-    uint32_t flip = 0u;
-    for (uint32_t m = R; m; m &= m - 1u) {
-        const uint32_t xs = __ffs(m) - 1u;
-        const uint32_t rest = m & (m - 1u);
-        const uint32_t xe = rest ? __ffs(rest) - 1u : 32u;  // the run is sites xs .. xe - 1
-        const uint32_t p = __ldcg(par + rb + xs);            // its first site's parent
-        const uint32_t px = P.lshift ? (p & (L - 1u)) : p % L, py = P.lshift ? (p >> P.lshift) : p / L;
-        uint32_t root;
-        if (px - gx0 < 32u && py - gy0 < 32u) {
-            // a site of this tile: its component's root is found once per tile
-            const uint32_t slot = sw_slot((py - gy0) * 32u + (px - gx0));
-            root = croot[slot];
-            if (root == 0xFFFFFFFFu) {
-                root = sw_find<true>(par, p);
-                croot[slot] = root;  // lanes racing here store the same root
-            }
-        } else {
-            root = sw_find<true>(par, p);
-        }
-        const uint4 w = philox_q_wide(pf, root >> 2);
-        const uint32_t coin = ((root & 3u) == 0 ? w.x : (root & 3u) == 1 ? w.y : (root & 3u) == 2 ? w.z : w.w) >> 31;
-        const uint32_t run = (xe == 32u ? 0xFFFFFFFFu : (1u << xe) - 1u) & ~((1u << xs) - 1u);
-        if (coin) flip |= run;
-        if (P.labels) {
-            int32_t* lab = P.labels + copy * P.N + rb;
-            for (uint32_t x = xs; x < xe; ++x) lab[x] = (int32_t)root;
-        }
-    }
-    // flip the row's spins: the bytes of flipped sites change sign (0x01 <-> 0xFF)
-    uint4* sp = reinterpret_cast<uint4*>(P.spins + copy * P.N + rb);
-    auto sgn = [](uint32_t nib) { return ((nib * 0x00204081u) & 0x01010101u) * 0xFEu; };
-#pragma unroll
-    for (uint32_t c = 0; c < 2; ++c) {
-        uint4 v = sp[c];
-        const uint32_t f = flip >> (16u * c);
-        v.x ^= sgn(f & 15u);
-        v.y ^= sgn((f >> 4) & 15u);
-        v.z ^= sgn((f >> 8) & 15u);
-        v.w ^= sgn((f >> 12) & 15u);
-        sp[c] = v;
-    }
-}
-
 cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s) {
     if (P0.N % 4 != 0) return cudaErrorInvalidValue;
     for (uint64_t c0 = 0; c0 < copies; c0 += 65535) {
@@ -602,21 +394,9 @@ cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s
         const uint32_t quads = P.N / 4;
         const bool tiled = sw_tiled(P.dim, P.L);
         cudaError_t e;
-        if (tiled && P.dim == 2) {
-            const uint32_t blocks = (P.N / 1024 + kSwRowWarps - 1) / kSwRowWarps;
-            k_sw_local_rows<<<dim3(blocks, nc), 32 * kSwRowWarps, 0, s>>>(P);
-            count_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            k_sw_cross<<<dim3((sw_cross_count(P.N, P.dim) + 255) / 256, nc), 256, 0, s>>>(P);
-            count_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            k_sw_flip_rows<<<dim3(blocks, nc), 32 * kSwRowWarps, 0, s>>>(P);
-            count_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            continue;
-        }
         if (tiled) {
-            k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            if (P.dim == 2) k_sw_local<2><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            else k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             k_sw_cross<<<dim3((sw_cross_count(P.N, P.dim) + 255) / 256, nc), 256, 0, s>>>(P);
