@@ -45,13 +45,14 @@ ALG_INT_OPS_PER_MSC_UPDATE = 3.0 + 80.0 / 128.0
 SW_BYTES_PER_SITE = 11
 
 
-def recorded_traffic(kernel_files, replicas):
-    """DRAM bytes per launch from the committed ncu record, or None if the
-    kernel sources changed since the counters were taken."""
+def recorded_traffic(kname, replicas):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu record
+    (profiles/<kernel>_traffic.json), or None if there is none or the kernel's
+    sources changed since the counters were taken."""
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "profiles", "sweep_resident_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "%s_traffic.json" % kname)) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for name in rec["source_files"]:
@@ -443,6 +444,10 @@ def run_learned(args, seeds=None, plain_steps=None):
     from paper_1709_04394_gb300 import exact, gbmc
 
     cfg = dict(LEARNED)
+    if getattr(args, "mlp_band", None):
+        cfg["lo"], cfg["hi"] = args.mlp_band
+    if getattr(args, "train_shrink", None):
+        cfg["train_shrink"] = args.train_shrink
     torch.cuda.set_device(0)
     gbuild.build()
     ctx = gbmc.gbmc_create(0, torch.cuda.current_stream().cuda_stream)
@@ -645,6 +650,10 @@ def main():
                     help="default workload only: skip the secondary records (configs 2, 4 and the single-seed "
                          "learned-schedule comparison)")
     ap.add_argument("--learned-seeds", type=int, default=3)
+    ap.add_argument("--mlp-band", type=float, nargs=2, default=None,
+                    help="pa-learned: overlap band [lo, hi] in which an MLP proposal is kept (default 0.85 0.90)")
+    ap.add_argument("--train-shrink", type=float, default=None,
+                    help="pa-learned: train the MLP towards this multiple of the bisection step (default 0.97)")
     ap.add_argument("--plain-steps", type=int, nargs="*", default=[250, 500, 1000, 2000, 4000])
     args = ap.parse_args()
     if args.workload == "pa-learned":
@@ -855,7 +864,7 @@ def gpu_record(w, workload, res, ws):
         "roofline": {**roof,
                      "traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                     "scaled by replicas from the committed ncu record)",
+                                     "scaled by replicas from profiles/<kernel>_traffic.json)",
                      "avg_launch_ms": t_l / n_sweeping if n_sweeping else None, "launches": n_l,
                      "sweeping_launches": n_sweeping,
                      "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
