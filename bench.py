@@ -775,7 +775,7 @@ def kernel_name(w, prof):
 
 def bits_lattice(dim, L):
     """Lattice classes the bit-sliced resident kernel sweeps (its default)."""
-    return (dim == 2 and L in (64, 128, 256)) or (dim == 3 and L == 8)
+    return (dim == 2 and L in (16, 32, 64, 128, 256)) or (dim == 3 and L == 8)
 
 
 def dominant_share(w, kname):

@@ -120,8 +120,8 @@ gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
  * fits in a thread block's shared memory). BITS: one bit per spin, 32 sites of
  * a colour per word (the multi-spin coding of sites of Sec. 3.1 applied to the
  * copy on chip; the population stays in the int8 layout in device memory and
- * is converted on load and store), for 2D ferromagnets with L in {64, 128,
- * 256} and 3D lattices (ferromagnet or +-J) with L = 8; other lattices of the
+ * is converted on load and store), for 2D ferromagnets with L in {16, 32, 64,
+ * 128, 256} and 3D lattices (ferromagnet or +-J) with L = 8; other lattices of the
  * same call take the BYTES kernel. AUTO (default): BITS for a supported lattice
  * class unless gbmc_autotune timed BYTES faster for it. All give bit-identical
  * results (same Philox words per site). Unknown kernel: GBMC_ERR_ARG. */

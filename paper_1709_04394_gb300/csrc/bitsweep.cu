@@ -10,10 +10,13 @@
 // same Philox words as every other sweep kernel (colour rank k of a site, q =
 // k >> 2, word k & 3), so the spins are bit-identical to theirs.
 //
-//  * k_sweep_bits2: 2D ferromagnet, L in {64, 128, 256}. One warp per copy,
-//    the copy in shared memory: plane c, row y, word w = the sites
-//    j = 32 w .. 32 w + 31 of colour c in row y (x = 2 j + ((y + c) & 1)),
-//    bit j - 32 w. No block-wide barrier: the warps of a block are independent.
+//  * k_sweep_bits2: 2D ferromagnet, L in {16, 32, 64, 128, 256}. The copy in
+//    shared memory, each colour plane as N / 64 words of 32 consecutive colour
+//    ranks: for L >= 64 plane c, row y, word w = the sites j = 32 w .. 32 w +
+//    31 of colour c in row y (x = 2 j + ((y + c) & 1)), bit j - 32 w; for
+//    L = 32 (16) a word holds 2 (4) rows of L / 2 sites. One warp per copy for
+//    L >= 64, one lane per word and 2 (8) copies per warp for L = 32 (16). No
+//    block-wide barrier: the warps of a block are independent.
 //  * k_sweep_bits3: 3D lattices with L = 8 (ferromagnet or +-J spin glass,
 //    Sec. 6). Eight lanes per copy, four copies per warp, the copy in
 //    registers: lane z holds word z of both planes = the 32 sites of colour c
@@ -105,9 +108,10 @@ __device__ __forceinline__ void record_copy(const SweepJob& J, uint64_t slot, ui
 // 2D
 // ---------------------------------------------------------------------------
 
-// Neighbour words of the colour-c word idx = (y, w): the other plane's words
-// in rows y - 1 and y + 1 and in row y, and the row-y word shifted by one site
-// towards j + 1 (odd x) or j - 1 (even x), wrapping around the row.
+// Neighbour words of the colour-c word idx = (y, w) when a row spans
+// L / 64 >= 1 words: the other plane's words in rows y - 1 and y + 1 and in
+// row y, and the row-y word shifted by one site towards j + 1 (odd x) or
+// j - 1 (even x), wrapping around the row.
 __device__ __forceinline__ void nb2(const uint32_t* oth, uint32_t idx, uint32_t lgW, uint32_t L, uint32_t colour,
                                     uint32_t& up, uint32_t& dn, uint32_t& same, uint32_t& side, uint32_t& q0) {
     const uint32_t Wm = (1u << lgW) - 1u;
@@ -122,45 +126,86 @@ __device__ __forceinline__ void nb2(const uint32_t* oth, uint32_t idx, uint32_t 
     q0 = y * (L >> 3) + 8u * w;
 }
 
+// The same when a word holds 64 / L rows of S = L / 2 sites (L = 16: four
+// rows of 8, L = 32: two rows of 16): row s of word w is y = (64 / L) w + s,
+// bits S s .. S s + S - 1. Rows y -/+ 1 are the neighbouring S-bit segments
+// (across words at the ends); the x neighbour not sharing j is a rotation
+// by one site within each row, towards j + 1 in the rows of odd x
+// ((s + c) odd) and towards j - 1 in the others.
+__device__ __forceinline__ void nb2_rows(const uint32_t* oth, uint32_t w, uint32_t PW, uint32_t S, uint32_t colour,
+                                         uint32_t& up, uint32_t& dn, uint32_t& same, uint32_t& side, uint32_t& q0) {
+    const uint32_t wm = PW - 1u;
+    same = oth[GBMC_IDX(w, PW)];
+    const uint32_t prev = oth[GBMC_IDX((w - 1u) & wm, PW)], next = oth[GBMC_IDX((w + 1u) & wm, PW)];
+    up = __funnelshift_l(prev, same, S);  // (same << S) | (prev >> (32 - S))
+    dn = __funnelshift_r(same, next, S);  // (same >> S) | (next << (32 - S))
+    const uint32_t top = S == 16u ? 0x80008000u : 0x80808080u;  // last site of each row
+    const uint32_t bot = S == 16u ? 0x00010001u : 0x01010101u;  // first site of each row
+    const uint32_t to_next = ((same >> 1) & ~top) | ((same << (S - 1u)) & top);  // bit j <- bit j + 1
+    const uint32_t to_prev = ((same << 1) & ~bot) | ((same >> (S - 1u)) & bot);  // bit j <- bit j - 1
+    const uint32_t odd_s = S == 16u ? 0xFFFF0000u : 0xFF00FF00u;                 // rows s odd
+    const uint32_t odd_x = colour ? ~odd_s : odd_s;                               // rows with odd x
+    side = (to_next & odd_x) | (to_prev & ~odd_x);
+    q0 = 8u * w;
+}
+
+// ROWS: every job has L <= 32 (words of several rows), else every job has L >= 64.
+template <bool ROWS>
 __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ SweepLaunch P, uint32_t wpb,
                                                      uint32_t words_per_warp) {
     extern __shared__ __align__(16) uint32_t smw[];
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     const int jid = job_of(P, blockIdx.x);
     const SweepJob& J = P.jobs[jid];
-    const uint64_t slot = (uint64_t)(blockIdx.x - P.cta_begin[jid]) * wpb + wib;
-    if (slot >= (uint64_t)J.n_inst * J.R) return;  // whole warp; no block barriers follow
-    uint32_t inst, r;
-    split_copy(slot, J.R, inst, r);
-    if (J.nlive && r >= J.nlive[inst]) return;     // variable populations: only live slots
     const uint32_t L = J.L, N = J.N;
-    const uint32_t lgL = 31u - __clz(L), lgW = lgL - 6u;
-    const uint32_t PW = L << lgW;                  // words per colour plane
-    uint32_t* sm = smw + (uint64_t)wib * words_per_warp;
-    uint8_t* smb = reinterpret_cast<uint8_t*>(sm);
-
-    // ---- load: int8 rows -> bit planes (16 bytes = 8 even-x + 8 odd-x sites per lane and step) ----
+    const uint32_t lgL = 31u - __clz(L);
+    const uint32_t PW = N >> 6;                    // words per colour plane
+    // lanes per copy: 32 (L >= 64), or one per word (L <= 32: a plane has 4 or 16 words)
+    const uint32_t lpc = ROWS ? PW : 32u, lgl = ROWS ? 31u - __clz(lpc) : 5u;
+    const uint32_t li = ROWS ? lane & (lpc - 1u) : lane, grp = ROWS ? lane >> lgl : 0u;
+    const uint32_t per_warp = ROWS ? 32u >> lgl : 1u;
     const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
-    const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
-    const uint4* g = reinterpret_cast<const uint4*>(J.src + GBMC_IDX(srcslot, ncopies) * N);
-    for (uint32_t c16 = lane; c16 < (N >> 4); c16 += 32u) {
-        const uint4 v = g[c16];
-        uint32_t e0, o0, e1, o1;
-        pack8(v.x, v.y, e0, o0);
-        pack8(v.z, v.w, e1, o1);
-        const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
-        const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);  // byte of the plane
-        const uint32_t ce = y & 1u;                                             // colour of the even-x sites
-        smb[GBMC_IDX((ce * PW << 2) + b, words_per_warp * 4u)] = (uint8_t)(e0 | (e1 << 4));
-        smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + b, words_per_warp * 4u)] = (uint8_t)(o0 | (o1 << 4));
+    const uint64_t wslot = ((uint64_t)(blockIdx.x - P.cta_begin[jid]) * wpb + wib) * per_warp;
+    if (wslot >= ncopies) return;                  // whole warp; no block barriers follow
+    const uint64_t slot = wslot + grp;
+    uint32_t inst = 0, r = 0;
+    bool active = slot < ncopies;
+    if (active) {
+        split_copy(slot, J.R, inst, r);
+        if (J.nlive && r >= J.nlive[inst]) active = false;  // variable populations: only live slots
+    }
+    if (!ROWS && !active) return;                  // one copy per warp: the whole warp
+    // every lane of the warp takes part in its syncs and reductions
+    uint32_t* sm = smw + (uint64_t)wib * words_per_warp + (uint64_t)grp * 2u * PW;
+    uint8_t* smb = reinterpret_cast<uint8_t*>(sm);
+    const uint32_t bytes = words_per_warp * 4u;
+    const uint32_t cshift = lgL - 4u;              // 16-byte chunks per row = L / 16
+
+    // ---- load: int8 rows -> bit planes. A chunk of 16 sites holds 8 even-x sites
+    // (colour y & 1) and 8 odd-x sites, consecutive colour ranks in each plane:
+    // their down bits are byte c16 of the two planes ----
+    if (active) {
+        const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
+        const uint4* g = reinterpret_cast<const uint4*>(J.src + GBMC_IDX(srcslot, ncopies) * N);
+        for (uint32_t c16 = li; c16 < (N >> 4); c16 += lpc) {
+            const uint4 v = g[c16];
+            uint32_t e0, o0, e1, o1;
+            pack8(v.x, v.y, e0, o0);
+            pack8(v.z, v.w, e1, o1);
+            const uint32_t ce = (c16 >> cshift) & 1u;  // colour of the even-x sites of row y
+            smb[GBMC_IDX((ce * PW << 2) + c16, bytes)] = (uint8_t)(e0 | (e1 << 4));
+            smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + c16, bytes)] = (uint8_t)(o0 | (o1 << 4));
+        }
     }
     __syncwarp();
 
     uint32_t T4, T8, T12;
-    copy_thresholds(J, slot, T4, T8, T12);
+    copy_thresholds(J, active ? slot : 0, T4, T8, T12);
     const uint32_t instance = J.inst_base + inst;
     const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
     const bool want_final = J.E || J.M || J.hist;
+    constexpr bool rows = ROWS;
+    const uint32_t lgW = rows ? 0u : lgL - 6u, S = L >> 1;
     const uint32_t nsw = J.nsweeps;
     for (uint32_t s = 0; s <= nsw; ++s) {
         if (s == nsw && nsw != 0) break;  // s == nsw: measurement-only pass when nothing is swept
@@ -171,19 +216,26 @@ __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ Swe
                 const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
                 uint32_t* own = sm + colour * PW;
                 const uint32_t* oth = sm + (colour ^ 1u) * PW;
-                // two words per lane and step (PW is a multiple of 64): both are
-                // loaded and updated before either is stored (they only read the
-                // other plane)
-                for (uint32_t ia = lane; ia < PW; ia += 64u) {
-                    const uint32_t ib = ia + 32u;
-                    uint32_t ua, da, sa, xa, qa, ub, db, sb, xb, qb;
-                    nb2(oth, ia, lgW, L, colour, ua, da, sa, xa, qa);
-                    nb2(oth, ib, lgW, L, colour, ub, db, sb, xb, qb);
-                    const uint32_t wa = own[ia], wb = own[ib];
-                    const uint32_t na = bp_word_update(wa, ua, da, sa, xa, pf, qa, T4, T8);
-                    const uint32_t nb = bp_word_update(wb, ub, db, sb, xb, pf, qb, T4, T8);
-                    own[ia] = na;
-                    own[ib] = nb;
+                if (active && rows) {
+                    uint32_t u, d, sa, x, q;
+                    nb2_rows(oth, li, PW, S, colour, u, d, sa, x, q);
+                    const uint32_t nw = bp_word_update(own[li], u, d, sa, x, pf, q, T4, T8);
+                    own[li] = nw;
+                } else if (active) {
+                    // two words per lane and step (PW is a multiple of 64): both are
+                    // loaded and updated before either is stored (they only read the
+                    // other plane)
+                    for (uint32_t ia = li; ia < PW; ia += 64u) {
+                        const uint32_t ib = ia + 32u;
+                        uint32_t ua, da, sa, xa, qa, ub, db, sb, xb, qb;
+                        nb2(oth, ia, lgW, L, colour, ua, da, sa, xa, qa);
+                        nb2(oth, ib, lgW, L, colour, ub, db, sb, xb, qb);
+                        const uint32_t wa = own[ia], wb = own[ib];
+                        const uint32_t na = bp_word_update(wa, ua, da, sa, xa, pf, qa, T4, T8);
+                        const uint32_t nb = bp_word_update(wb, ub, db, sb, xb, pf, qb, T4, T8);
+                        own[ia] = na;
+                        own[ib] = nb;
+                    }
                 }
                 __syncwarp();
             }
@@ -193,28 +245,31 @@ __global__ void __launch_bounds__(128) k_sweep_bits2(const __grid_constant__ Swe
             // E = -sum over bonds s_i s_j: every bond has one colour-0 end, so
             // E = 2 (unsatisfied bonds of the colour-0 sites) - 2 N
             int U = 0, D = 0;
-            for (uint32_t idx = lane; idx < PW; idx += 32u) {
-                uint32_t up, dn, same, side, q0;
-                nb2(sm + PW, idx, lgW, L, 0u, up, dn, same, side, q0);
-                const uint32_t w0 = sm[idx];
-                U += __popc(w0 ^ up) + __popc(w0 ^ dn) + __popc(w0 ^ same) + __popc(w0 ^ side);
-                D += __popc(w0) + __popc(sm[PW + idx]);
+            if (active) {
+                for (uint32_t idx = li; idx < PW; idx += lpc) {
+                    uint32_t up, dn, same, side, q0;
+                    if (rows) nb2_rows(sm + PW, idx, PW, S, 0u, up, dn, same, side, q0);
+                    else nb2(sm + PW, idx, lgW, L, 0u, up, dn, same, side, q0);
+                    const uint32_t w0 = sm[idx];
+                    U += __popc(w0 ^ up) + __popc(w0 ^ dn) + __popc(w0 ^ same) + __popc(w0 ^ side);
+                    D += __popc(w0) + __popc(sm[PW + idx]);
+                }
             }
-            U = warp_sum(U);
-            D = warp_sum(D);
-            if (lane == 0) record_copy(J, slot, inst, s, sweep, last, 2 * U - 2 * (int)N, (int)N - 2 * D);
+            for (uint32_t o = lpc >> 1; o > 0; o >>= 1) {  // within the copy's lanes
+                U += __shfl_xor_sync(0xffffffffu, U, o);
+                D += __shfl_xor_sync(0xffffffffu, D, o);
+            }
+            if (active && li == 0) record_copy(J, slot, inst, s, sweep, last, 2 * U - 2 * (int)N, (int)N - 2 * D);
         }
     }
 
     // ---- store: bit planes -> int8 rows ----
-    if (nsw > 0 || J.dst != J.src || J.parent) {
+    if (active && (nsw > 0 || J.dst != J.src || J.parent)) {
         uint4* d = reinterpret_cast<uint4*>(J.dst + slot * N);
-        for (uint32_t c16 = lane; c16 < (N >> 4); c16 += 32u) {
-            const uint32_t o = c16 << 4, y = o >> lgL, x0 = o & (L - 1u);
-            const uint32_t b = (((y << lgW) + (x0 >> 6)) << 2) + ((x0 & 63u) >> 4);
-            const uint32_t ce = y & 1u;
-            const uint32_t ev = smb[GBMC_IDX((ce * PW << 2) + b, words_per_warp * 4u)];
-            const uint32_t od = smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + b, words_per_warp * 4u)];
+        for (uint32_t c16 = li; c16 < (N >> 4); c16 += lpc) {
+            const uint32_t ce = (c16 >> cshift) & 1u;
+            const uint32_t ev = smb[GBMC_IDX((ce * PW << 2) + c16, bytes)];
+            const uint32_t od = smb[GBMC_IDX(((ce ^ 1u) * PW << 2) + c16, bytes)];
             const uint2 lo = unpack8(ev & 15u, od & 15u), hi = unpack8(ev >> 4, od >> 4);
             d[c16] = make_uint4(lo.x, lo.y, hi.x, hi.y);
         }
@@ -393,7 +448,9 @@ __global__ void k_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_in
 
 }  // namespace
 
-bool bits_supported(int dim, int L) { return (dim == 2 && (L == 64 || L == 128 || L == 256)) || (dim == 3 && L == 8); }
+bool bits_supported(int dim, int L) {
+    return (dim == 2 && (L == 16 || L == 32 || L == 64 || L == 128 || L == 256)) || (dim == 3 && L == 8);
+}
 
 cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s) {
     const uint32_t n = n_inst * 96u;
@@ -402,7 +459,7 @@ cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_i
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
+static cudaError_t launch_bits_group(const SweepLaunch& P0, bool rows, cudaStream_t s) {
     constexpr uint32_t kWarps = kBitsWarps;
     SweepLaunch P = P0;
     // largest copies first: their blocks are dispatched first, shortening the tail
@@ -412,16 +469,19 @@ cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
             P.jobs[b] = P.jobs[b - 1];
             P.jobs[b - 1] = t;
         }
-    const uint32_t copies_per_block = P.dim == 2 ? kWarps : 4u * kWarps;
     uint32_t total = 0, words = 0;
     for (int j = 0; j < P.njobs; ++j) {
         const SweepJob& J = P.jobs[j];
         if (!bits_supported(P.dim, (int)J.L)) return cudaErrorInvalidValue;
         P.cta_begin[j] = total;
-        const uint64_t nb = ((uint64_t)J.n_inst * J.R + copies_per_block - 1) / copies_per_block;
+        // 2D: one copy per warp, or 32 / (N / 64) copies when a plane has fewer
+        // than 32 words (L = 16: 8, L = 32: 2); 3D L = 8: 4 copies per warp
+        const uint32_t pw = J.N / 64u;
+        const uint32_t per_warp = P.dim == 2 ? (pw < 32u ? 32u / pw : 1u) : 4u;
+        const uint64_t nb = ((uint64_t)J.n_inst * J.R + per_warp * kWarps - 1) / (per_warp * kWarps);
         if (total + nb > 0x7FFFFFFFull) return cudaErrorInvalidValue;
         total += (uint32_t)nb;
-        const uint32_t w = J.N / 32u;  // two planes of N / 2 bits
+        const uint32_t w = per_warp * 2u * pw;  // two planes of N / 2 bits per copy
         if (w > words) words = w;
     }
     P.cta_begin[P.njobs] = total;
@@ -429,11 +489,12 @@ cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     if (P.dim == 2) {
         const size_t smem = (size_t)kWarps * words * 4u;
+        auto kern = rows ? k_sweep_bits2<true> : k_sweep_bits2<false>;
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_bits2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_sweep_bits2<<<total, 32u * kWarps, smem, s>>>(P, kWarps, words);
+        kern<<<total, 32u * kWarps, smem, s>>>(P, kWarps, words);
     } else if (P.ea) {
         k_sweep_bits3<true><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
     } else {
@@ -441,6 +502,21 @@ cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
     }
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
+    if (P0.dim != 2) return launch_bits_group(P0, false, s);
+    // 2D: lattices whose words hold several rows (L <= 32) in their own launch
+    SweepLaunch A = P0, B = P0;
+    A.njobs = B.njobs = 0;
+    for (int j = 0; j < P0.njobs; ++j) {
+        if (P0.jobs[j].L <= 32) A.jobs[A.njobs++] = P0.jobs[j];
+        else B.jobs[B.njobs++] = P0.jobs[j];
+    }
+    cudaError_t e = cudaSuccess;
+    if (B.njobs) e = launch_bits_group(B, false, s);
+    if (e == cudaSuccess && A.njobs) e = launch_bits_group(A, true, s);
+    return e;
 }
 
 }  // namespace gbmc

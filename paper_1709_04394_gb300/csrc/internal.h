@@ -142,9 +142,10 @@ cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint
 
 // Bit-sliced resident sweeps (bitsweep.cu): every copy converted to one bit
 // per spin on chip, same results as launch_sweep_resident. Supported lattices:
-// 2D ferromagnets with L in {64, 128, 256}, 3D lattices with L = 8 (all jobs of
-// a launch of one dimension and model). Uses its own block layout (P.cta_begin
-// and P.total are recomputed).
+// 2D ferromagnets with L in {16, 32, 64, 128, 256}, 3D lattices with L = 8 (all jobs of
+// a launch of one dimension and model; 2D lattices with L <= 32 and L >= 64 go
+// to separate launches). Uses its own block layout (P.cta_begin and P.total
+// are recomputed).
 bool bits_supported(int dim, int L);
 cudaError_t launch_sweep_bits(const SweepLaunch& P, cudaStream_t s);
 cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s);

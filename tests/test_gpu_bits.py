@@ -1,5 +1,5 @@
 """GPU parity of the bit-sliced resident sweep kernel (one bit per spin on
-chip; 2D ferromagnets with L = 64, 128, 256 and 3D lattices with L = 8)
+chip; 2D ferromagnets with L = 16, 32, 64, 128, 256 and 3D lattices with L = 8)
 against the CPU oracle, element by element: spins, per-sweep energies and
 magnetisations, annealing runs (multinomial and nearest-integer resampling,
 mixed lattice sizes in one step), parallel tempering; and the bit-sliced and
@@ -37,6 +37,8 @@ def _kernel_ran(ctx, fn):
 
 @pytest.mark.parametrize("dim,L,model,I,R,beta,n", [
     (2, 64, gbmc.GBMC_ISING_FM, 1, 5, 0.4406868, 7),
+    (2, 16, gbmc.GBMC_ISING_FM, 2, 5, 0.4406868, 6),  # 8 copies per warp, 10 of 32 in a block
+    (2, 32, gbmc.GBMC_ISING_FM, 1, 3, 0.5, 5),        # 2 copies per warp, the second warp half empty
     (2, 128, gbmc.GBMC_ISING_FM, 2, 3, 0.3, 3),
     (2, 256, gbmc.GBMC_ISING_FM, 1, 2, 0.6, 2),
     (2, 64, gbmc.GBMC_ISING_FM, 1, 3, 0.0, 2),       # beta = 0: every site flips every half-sweep
@@ -75,6 +77,8 @@ def test_bits_sweeps_match_oracle(bits, dim, L, model, I, R, beta, n):
 
 
 @pytest.mark.parametrize("dim,L,model,I,R", [(2, 64, gbmc.GBMC_ISING_FM, 1, 1027),
+                                             (2, 16, gbmc.GBMC_ISING_FM, 3, 45),
+                                             (2, 32, gbmc.GBMC_ISING_FM, 1, 77),
                                              (2, 128, gbmc.GBMC_ISING_FM, 3, 101),
                                              (2, 256, gbmc.GBMC_ISING_FM, 1, 33),
                                              (3, 8, gbmc.GBMC_EA_PMJ, 5, 203),
@@ -96,10 +100,11 @@ def test_bits_equals_bytes_kernel(ctx, dim, L, model, I, R):
 
 
 def test_bits_pa_mixed_lattices_match_oracle(bits):
-    # one annealing step covers an L = 32 lattice (byte-plane kernel) and L = 64, 128
-    # lattices (bit-sliced kernel)
+    # one annealing step covers an L = 24 lattice (byte-plane kernel) and L = 16, 32,
+    # 64, 128 lattices (bit-sliced kernel: launches for words of several rows and of
+    # whole rows)
     S, theta, seed = 4, 2, 13
-    spec = [(32, 300), (64, 401), (128, 37)]
+    spec = [(24, 200), (16, 301), (32, 150), (64, 401), (128, 37)]
     lats = [gbmc.lattice_init(bits, 2, L, n_replicas=R, seed=seed, instance_base=k) for k, (L, R) in enumerate(spec)]
     pa = gbmc.pa_create(bits, lats, theta, S, beta_f=1.0)
     prof = _kernel_ran(bits, lambda: gbmc.pa_run(bits, pa, capacity=S + 1))
@@ -183,11 +188,11 @@ def test_sweep_kernel_mode_checks(ctx):
     # lattices the bit-sliced kernel does not support take the byte-plane kernel in BITS mode
     gbmc.gbmc_set_sweep_kernel(ctx, BITS)
     try:
-        lat = gbmc.lattice_init(ctx, 2, 32, n_replicas=3, seed=2)
+        lat = gbmc.lattice_init(ctx, 2, 24, n_replicas=3, seed=2)
         prof = _kernel_ran(ctx, lambda: gbmc.metropolis_sweeps(ctx, lat, 0.4, 2))
         assert "sweep_resident" in prof and "sweep_bits" not in prof
-        s = oracle.init_spins(2, 32, 2, 0, 1, True)
-        oracle.sweeps(2, 32, s, None, 0.4, 2, 0, 1, 0, 2)
+        s = oracle.init_spins(2, 24, 2, 0, 1, True)
+        oracle.sweeps(2, 24, s, None, 0.4, 2, 0, 1, 0, 2)
         np.testing.assert_array_equal(spins_out(ctx, lat)[1], s)
         gbmc.lattice_free(lat)
     finally:
