@@ -240,6 +240,77 @@ __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaun
     *reinterpret_cast<uint4*>(P.parent + copy * P.N + i0) = make_uint4(g[0], g[1], g[2], g[3]);
 }
 
+// First site of the run holding site x (run-start mask R of the row; bit 0 is always set).
+__device__ __forceinline__ uint32_t sw_run_start(uint32_t R, uint32_t x) {
+    return 31u - __clz(R & (0xFFFFFFFFu >> (31u - x)));
+}
+
+// 2D tiles, the labelling by runs: as k_sw_local<2> (thread t: sites 4t .. 4t+3,
+// eight lanes per tile row), with the union-find over run starts only. A row's
+// run starts and y bonds become 32-bit masks; a y bond unites the runs holding
+// its two ends, and one union per pair of overlapping runs suffices (the bond
+// at x joins the same pair as the one at x - 1 unless a run starts at x in
+// either row); the root of each run is found once, at its start, and every site
+// takes its run's root.
+__global__ void __launch_bounds__(256) k_sw_local_runs(const __grid_constant__ SwLaunch P) {
+    __shared__ uint32_t lp[1024];
+    __shared__ uint16_t rt[1024];    // root of each run, at its start
+    __shared__ uint32_t rmask[32];   // run starts of each tile row
+    const uint64_t copy = P.copy0 + blockIdx.y;
+    const int8_t* s = P.spins + copy * P.N;
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
+    const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
+    const uint32_t L = P.L, ntx = L / 32u;
+    const uint32_t bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
+    const uint32_t l0 = 4 * threadIdx.x, lx = l0 & 31u, ly = l0 >> 5, row = l0 - lx;
+    const uint32_t i0 = (by * 32u + ly) * L + bx * 32u + lx;
+    uint32_t flags[4];
+    sw_bond_flags_row<2>(P, s, i0, bx * 32u + lx, by * 32u + ly, 0u, r, c3, flags);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t left = __shfl_up_sync(0xffffffffu, flags[3] & 1u, 1);  // bond into this thread's first site
+    uint32_t R = (lx == 0 || !left) ? 1u : 0u, Y = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k > 0) R |= (flags[k - 1] & 1u) ? 0u : 1u << k;
+        Y |= (flags[k] & 2u) ? 1u << k : 0u;
+    }
+    R <<= 4 * (lane & 7u);
+    Y <<= 4 * (lane & 7u);
+#pragma unroll
+    for (uint32_t o = 1; o < 8u; o <<= 1) {
+        R |= __shfl_xor_sync(0xffffffffu, R, o);
+        Y |= __shfl_xor_sync(0xffffffffu, Y, o);
+    }
+    if ((lane & 7u) == 0) rmask[ly] = R;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+        if ((R >> (lx + k)) & 1u) lp[l0 + k] = l0 + k;  // run starts are their own parents
+    __syncthreads();
+    if (ly < 31u) {
+        const uint32_t Rn = rmask[ly + 1];
+        const uint32_t U = Y & ~((Y << 1) & ~R & ~Rn);
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t x = lx + k;
+            if ((U >> x) & 1u) sw_unite<false>(lp, row + sw_run_start(R, x), row + 32u + sw_run_start(Rn, x), P.err);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+        if ((R >> (lx + k)) & 1u) rt[l0 + k] = (uint16_t)sw_find<false>(lp, l0 + k);
+    __syncthreads();
+    uint32_t g[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+        const uint32_t root = rt[row + sw_run_start(R, lx + k)];
+        g[k] = (by * 32u + (root >> 5)) * L + bx * 32u + (root & 31u);
+    }
+    // i0 % 4 == 0, N % 4 == 0 and the forest is a cudaMalloc block: 16-byte aligned
+    *reinterpret_cast<uint4*>(P.parent + copy * P.N + i0) = make_uint4(g[0], g[1], g[2], g[3]);
+}
+
 // The bonds that leave their tile: e < N / tx are the sites with x % tx == tx - 1
 // (bond along x), then N / ty sites with y % ty == ty - 1 (along y), then in 3D
 // N / tz sites with z % tz == tz - 1 (along z).
@@ -395,7 +466,7 @@ cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s
         const bool tiled = sw_tiled(P.dim, P.L);
         cudaError_t e;
         if (tiled) {
-            if (P.dim == 2) k_sw_local<2><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            if (P.dim == 2) k_sw_local_runs<<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
             else k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
