@@ -252,10 +252,19 @@ __device__ __forceinline__ uint32_t sw_run_start(uint32_t R, uint32_t x) {
 // at x joins the same pair as the one at x - 1 unless a run starts at x in
 // either row); the root of each run is found once, at its start, and every site
 // takes its run's root.
+// Appends the items with has = true of the warp's lanes to the warp's queue q
+// (lane order), advancing n; all 32 lanes call it together.
+__device__ __forceinline__ void sw_warp_push(uint32_t* q, uint32_t& n, bool has, uint32_t item) {
+    const uint32_t b = __ballot_sync(0xffffffffu, has);
+    if (has) q[n + __popc(b & ((1u << (threadIdx.x & 31u)) - 1u))] = item;
+    n += __popc(b);
+}
+
 __global__ void __launch_bounds__(256) k_sw_local_runs(const __grid_constant__ SwLaunch P) {
     __shared__ uint32_t lp[1024];
     __shared__ uint16_t rt[1024];    // root of each run, at its start
     __shared__ uint32_t rmask[32];   // run starts of each tile row
+    __shared__ uint32_t queue[8][128];  // per warp: unions (a | b << 16), then run starts
     const uint64_t copy = P.copy0 + blockIdx.y;
     const int8_t* s = P.spins + copy * P.N;
     uint32_t inst, r;
@@ -287,19 +296,29 @@ __global__ void __launch_bounds__(256) k_sw_local_runs(const __grid_constant__ S
     for (uint32_t k = 0; k < 4; ++k)
         if ((R >> (lx + k)) & 1u) lp[l0 + k] = l0 + k;  // run starts are their own parents
     __syncthreads();
-    if (ly < 31u) {
-        const uint32_t Rn = rmask[ly + 1];
-        const uint32_t U = Y & ~((Y << 1) & ~R & ~Rn);
+    // the warp's unions, then its run starts, go through a queue so that every
+    // lane works on one at a time (instead of each lane on its own few sites)
+    uint32_t* q = queue[threadIdx.x >> 5];
+    uint32_t n = 0;
+    {
+        const uint32_t Rn = ly < 31u ? rmask[ly + 1] : 0u;
+        const uint32_t U = ly < 31u ? Y & ~((Y << 1) & ~R & ~Rn) : 0u;
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             const uint32_t x = lx + k;
-            if ((U >> x) & 1u) sw_unite<false>(lp, row + sw_run_start(R, x), row + 32u + sw_run_start(Rn, x), P.err);
+            const bool has = (U >> x) & 1u;
+            sw_warp_push(q, n, has,
+                         has ? (row + sw_run_start(R, x)) | ((row + 32u + sw_run_start(Rn, x)) << 16) : 0u);
         }
     }
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32u) sw_unite<false>(lp, q[i] & 0xFFFFu, q[i] >> 16, P.err);
     __syncthreads();
+    n = 0;
 #pragma unroll
-    for (uint32_t k = 0; k < 4; ++k)
-        if ((R >> (lx + k)) & 1u) rt[l0 + k] = (uint16_t)sw_find<false>(lp, l0 + k);
+    for (uint32_t k = 0; k < 4; ++k) sw_warp_push(q, n, (R >> (lx + k)) & 1u, l0 + k);
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32u) rt[q[i]] = (uint16_t)sw_find<false>(lp, q[i]);
     __syncthreads();
     uint32_t g[4];
 #pragma unroll
@@ -385,6 +404,7 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
     __shared__ uint32_t tpar[1024];   // the tile's parent pointers (global site indices)
     __shared__ uint32_t troot[1024];  // root of each end node
     __shared__ uint8_t tcoin[1024];   // its coin (1: the cluster flips)
+    __shared__ uint32_t tqueue[8][128];  // per warp: its end nodes (local indices)
     const uint64_t copy = P.copy0 + blockIdx.y;
     uint32_t inst, r;
     split_copy(copy, P.R, inst, r);
@@ -428,16 +448,23 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
         }
         end[k] = cl;
     }
-    // end nodes: the root in the global forest and its coin
+    // end nodes: the root in the global forest and its coin, through a per-warp
+    // queue so that every lane works on one end node at a time
     const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwFlip, 0u, P.inst_base + inst), (uint32_t)P.seed,
                                       (uint32_t)(P.seed >> 32));
+    uint32_t* q = tqueue[threadIdx.x >> 5];
+    uint32_t n = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (end[k] != l0 + k) continue;
-        const uint32_t p = tpar[l0 + k];
-        const uint32_t root = p == i0 + k ? p : sw_find<true>(par, p);
-        troot[l0 + k] = root;
-        tcoin[l0 + k] = (uint8_t)sw_coin(pf, root);
+    for (int k = 0; k < 4; ++k) sw_warp_push(q, n, end[k] == l0 + k, l0 + k);
+    __syncwarp();
+    for (uint32_t i = threadIdx.x & 31u; i < n; i += 32u) {
+        const uint32_t l = q[i];
+        const uint32_t ex = l % T.tx, ey = (l / T.tx) % T.ty, ez = l / (T.tx * T.ty);
+        const uint32_t gl = ((bz * T.tz + ez) * L + by * T.ty + ey) * L + bx * T.tx + ex;  // its global index
+        const uint32_t p = tpar[l];
+        const uint32_t root = p == gl ? p : sw_find<true>(par, p);
+        troot[l] = root;
+        tcoin[l] = (uint8_t)sw_coin(pf, root);
     }
     __syncthreads();
     // i0 % 4 == 0 and the spin buffer is 16-byte aligned: one word per thread
