@@ -765,7 +765,8 @@ def kernel_name(w, prof):
         if w.get("msc"):
             return "sweep_msc"
         return "sweep_bits" if "sweep_bits" in prof else "sweep_resident"
-    if w.get("layout", 0) == 1:
+    if w.get("layout", 0) == 1 or "bitpack_strips" in prof:
+        # int8 lattices too: their strip sweeps run packed to bits
         return "bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep"
     if "dcb" in w:
         return "sweep_dcb"

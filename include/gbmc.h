@@ -123,8 +123,14 @@ gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
  * is converted on load and store), for 2D ferromagnets with L in {16, 32, 64,
  * 128, 256} and 3D lattices (ferromagnet or +-J) with L = 8; other lattices of the
  * same call take the BYTES kernel. AUTO (default): BITS for a supported lattice
- * class unless gbmc_autotune timed BYTES faster for it. All give bit-identical
- * results (same Philox words per site). Unknown kernel: GBMC_ERR_ARG. */
+ * class unless gbmc_autotune timed BYTES faster for it. The mode also picks the
+ * strip-resident sweeps of large int8 2D ferromagnets (gbmc_set_sweep_launch):
+ * BYTES runs them on the int8 strips; AUTO and BITS, where the bit-packed strip
+ * kernel fits (L % 1024 == 0, at most SM count / 8 copies), pack the
+ * configuration to one bit per spin in a library buffer (N / 8 bytes per copy,
+ * kept with the lattice), run every sweep of the call there and unpack it (three
+ * launches per call). All give bit-identical results (same Philox words per
+ * site). Unknown kernel: GBMC_ERR_ARG. */
 enum { GBMC_KERNEL_AUTO = 0, GBMC_KERNEL_BYTES = 1, GBMC_KERNEL_BITS = 2 };
 gbmc_status gbmc_set_sweep_kernel(gbmc_ctx *ctx, int32_t kernel);
 /* Test aid for the bounded waits: each grid barrier of the fused resampling

@@ -52,13 +52,14 @@ enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
     PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_SWEEP_BITS,
-    PK_COUNT
+    PK_BP_PACK, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
                                           "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
-                                          "bitpack_strips", "sweep_strips", "pt_exchange", "sweep_bits"};
+                                          "bitpack_strips", "sweep_strips", "pt_exchange", "sweep_bits",
+                                          "bitpack_convert"};
 
 // Device words of a context: 8 flags and counters, then the progress
 // counters of strip-resident sweeps (one per CTA, one CTA per SM).
@@ -157,6 +158,7 @@ struct gbmc_lattice {
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
     uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
     uint32_t* jb3;     // the same bonds as bit words of the bit-sliced 3D L = 8 sweep [inst][2][6][8]
+    uint32_t* packed;  // bit-packed copy of the configuration for the strip-resident bit sweeps (int8 layout)
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
     uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags and union-find forest
     uint32_t* sw_parent;
@@ -763,6 +765,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->jbits) cudaFree(l->jbits);
     if (l->jsplit) cudaFree(l->jsplit);
     if (l->jb3) cudaFree(l->jb3);
+    if (l->packed) cudaFree(l->packed);
     if (l->alt) cudaFree(l->alt);
     if (l->sw_bonds) cudaFree(l->sw_bonds);
     if (l->sw_parent) cudaFree(l->sw_parent);
@@ -909,6 +912,54 @@ gbmc_status metropolis_sweeps(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint3
     const Tuning tu = tune(l);
     SweepJob J = base_job(l, tu);
     thresholds(beta, J.thr);
+    {
+        // large 2D ferromagnets in the int8 layout, every sweep of the call in one
+        // launch of the bit-packed strip kernel: the configuration is packed to one
+        // bit per spin first and unpacked after (same Philox words, same spins as
+        // the byte strip kernel, a fraction of its instructions per update)
+        uint32_t Gc = 0, rmax = 0, threads = 0;
+        size_t smem = 0;
+        if (!tu.resident && ctx->sweep_kernel != GBMC_KERNEL_BYTES && l->d.dim == 2 &&
+            l->d.model == GBMC_ISING_FM && !E_series && !M_series && ctx->launch_mode != GBMC_LAUNCH_GRID &&
+            ctx->coop && n_sweeps <= 0x40000000u && ctx->sm_count <= (int)(kCtxWords - 8) &&
+            bp_strips_shape((uint32_t)l->d.L, l->ncopies, ctx->sm_count, Gc, rmax, threads, smem)) {
+            if (!l->packed) {
+                cudaError_t e = cudaMalloc(&l->packed, l->ncopies * (l->N / 8));
+                if (e != cudaSuccess) return fail(GBMC_ERR_OOM, "cudaMalloc(packed copy): %s", cudaGetErrorString(e));
+            }
+            {
+                ProfScope ps_(ctx, PK_BP_PACK);
+                CUDA_TRY(launch_bp_pack(l->cur, l->packed, (uint32_t)l->d.L, l->ncopies, ctx->stream));
+            }
+            BpStrips S;
+            std::memset(&S, 0, sizeof(S));
+            S.P = l->packed;
+            S.progress = ctx->words + 8;
+            S.err = ctx->words + 1;
+            S.budget = ctx->budget;
+            S.seed = l->d.seed;
+            S.L = (uint32_t)l->d.L;
+            S.Gc = Gc;
+            S.rmax = rmax;
+            S.R = l->d.n_replicas;
+            S.inst_base = l->d.instance_base;
+            S.t0 = l->t;
+            S.n_half = 2 * n_sweeps;
+            S.T4 = J.thr[0];
+            S.T8 = J.thr[1];
+            S.phantom = ctx->phantom;
+            {
+                ProfScope ps_(ctx, PK_BP_STRIPS);
+                CUDA_TRY(launch_bp_strips(S, l->ncopies, threads, smem, ctx->sm_count, ctx->stream));
+            }
+            {
+                ProfScope ps_(ctx, PK_BP_PACK);
+                CUDA_TRY(launch_bp_unpack(l->packed, l->cur, (uint32_t)l->d.L, l->ncopies, ctx->stream));
+            }
+            l->t += n_sweeps;
+            return GBMC_OK;
+        }
+    }
     // strips of rows resident in shared memory for the whole call (large 2D ferromagnets, no E/M series)
     uint32_t sGc = 0, srmax = 0, sthreads = 0;
     size_t ssmem = 0;

@@ -61,6 +61,7 @@ def test_int8_strip_neighbour_wait_runs_out_and_is_reported(ctx):
     L = 1024
     lat = gbmc.lattice_init(ctx, 2, L, seed=8)
     gbmc.gbmc_test_barrier_wait(ctx, 1, 2_000_000)
+    gbmc.gbmc_set_sweep_kernel(ctx, gbmc.GBMC_KERNEL_BYTES)  # the int8 strip kernel itself
     try:
         gbmc.metropolis_sweeps(ctx, lat, 0.44, 2)
         with pytest.raises(gbmc.GbmcError) as e:
@@ -68,6 +69,7 @@ def test_int8_strip_neighbour_wait_runs_out_and_is_reported(ctx):
         assert e.value.status == gbmc.GBMC_ERR_TIMEOUT
     finally:
         gbmc.gbmc_test_barrier_wait(ctx, 0, 2_000_000_000)
+        gbmc.gbmc_set_sweep_kernel(ctx, gbmc.GBMC_KERNEL_AUTO)
     gbmc.gbmc_sync(ctx)
     gbmc.lattice_free(lat)
     lat = gbmc.lattice_init(ctx, 2, L, seed=8)

@@ -132,15 +132,22 @@ def test_large_lattice_paths_match_oracle(ctx, L, n, chunks, mode):
     gbmc.lattice_free(lat)
 
 
+@pytest.mark.parametrize("kernel", [gbmc.GBMC_KERNEL_BYTES, gbmc.GBMC_KERNEL_AUTO])
 @pytest.mark.parametrize("L,I,R,n,beta", [(1024, 1, 3, 4, 0.6), (2048, 2, 1, 3, 0.3), (4096, 1, 2, 2, 0.2)])
-def test_strip_resident_sweeps_several_copies(ctx, L, I, R, n, beta):
-    # one launch per call, strips of every copy side by side; counters continue
+def test_strip_resident_sweeps_several_copies(ctx, L, I, R, n, beta, kernel):
+    # every sweep of a call in one strip launch, strips of every copy side by side;
+    # counters continue. BYTES: the int8 strips (one launch per call); AUTO: the
+    # configuration packed to bits, the bit-packed strips, unpacked (three launches)
     lat = gbmc.lattice_init(ctx, 2, L, n_instances=I, n_replicas=R, seed=21, instance_base=5)
     gbmc.lattice_set_sweep_counter(lat, 3)
-    n0 = gbmc.gbmc_kernel_launches()
-    gbmc.metropolis_sweeps(ctx, lat, beta, n - 1)
-    gbmc.metropolis_sweeps(ctx, lat, beta, 1)
-    assert gbmc.gbmc_kernel_launches() - n0 == 2
+    gbmc.gbmc_set_sweep_kernel(ctx, kernel)
+    try:
+        n0 = gbmc.gbmc_kernel_launches()
+        gbmc.metropolis_sweeps(ctx, lat, beta, n - 1)
+        gbmc.metropolis_sweeps(ctx, lat, beta, 1)
+        assert gbmc.gbmc_kernel_launches() - n0 == (2 if kernel == gbmc.GBMC_KERNEL_BYTES else 6)
+    finally:
+        gbmc.gbmc_set_sweep_kernel(ctx, gbmc.GBMC_KERNEL_AUTO)
     got = spins_out(ctx, lat)
     for i in range(I):
         for r in range(R):
