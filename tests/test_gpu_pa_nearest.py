@@ -116,23 +116,38 @@ def test_pa_nearest_mixed_batch_and_graph_replay(ctx, law):
 @pytest.mark.parametrize("law", LAWS)
 def test_pa_nearest_full_size_resampling_step_l64(ctx, law):
     # R_0 = 10^5 replicas of L = 64 (capacity 1.05 10^5): the whole resampling
-    # of step 3 (counts, R_3, children order) from the library's own energies
-    L, R0, cap, seed = 64, 100000, 105000, 9
+    # (counts, R_i, children order, ln Q) of step 3 and of the last step 100
+    # (beta = 1) from the library's own energies, and the last step's theta
+    # sweeps on sampled slots
+    L, R0, cap, seed, theta = 64, 100000, 105000, 9, 10
     betas = oracle.linear_betas(1.0, 100)
     lat = gbmc.lattice_init(ctx, 2, L, n_replicas=cap, seed=seed)
-    pa = gbmc.pa_create(ctx, [lat], 10, 100, resample=law, initial_replicas=R0)
-    rows = [gbmc.pa_step(ctx, pa) for _ in range(2)]
-    n2 = int(rows[-1][0]["n_replicas"])
-    E = np.empty(cap, dtype=np.int32)
-    gbmc.pa_energies_out(ctx, pa, 0, E)
-    row3 = gbmc.pa_step(ctx, pa)
-    par = np.empty(cap, dtype=np.uint32)
-    gbmc.pa_parents_out(ctx, pa, 0, par)
+    pa = gbmc.pa_create(ctx, [lat], theta, 100, resample=law, initial_replicas=R0)
     resample = oracle.resample_poisson if law == POISSON else oracle.resample_nearest
-    counts, Rn, lnQ = resample(E[:n2].astype(np.int64), betas[3] - betas[2], R0, cap, seed, 0, 3)
-    assert int(row3[0]["n_replicas"]) == Rn and abs(Rn - R0) < 2000
-    np.testing.assert_array_equal(par[:Rn], oracle.children_order(counts))
-    assert abs(row3[0]["lnQ"] - lnQ) <= RTOL * abs(lnQ) + 1e-13
+    done, n_prev = 0, R0
+    for step in (3, 100):
+        while done < step - 1:
+            n_prev = int(gbmc.pa_step(ctx, pa)[0]["n_replicas"])
+            done += 1
+        E = np.empty(cap, dtype=np.int32)
+        gbmc.pa_energies_out(ctx, pa, 0, E)
+        prev = spins_out(ctx, lat) if step == 100 else None
+        row = gbmc.pa_step(ctx, pa)
+        done += 1
+        par = np.empty(cap, dtype=np.uint32)
+        gbmc.pa_parents_out(ctx, pa, 0, par)
+        counts, Rn, lnQ = resample(E[:n_prev].astype(np.int64), betas[step] - betas[step - 1], R0, cap, seed, 0,
+                                   step)
+        assert int(row[0]["n_replicas"]) == Rn and abs(Rn - R0) < 3000
+        np.testing.assert_array_equal(par[:Rn], oracle.children_order(counts))
+        assert abs(row[0]["lnQ"] - lnQ) <= RTOL * abs(lnQ) + 1e-13
+        if prev is not None:
+            cur = spins_out(ctx, lat)
+            for slot in np.random.default_rng(step).integers(Rn, size=8):
+                s = prev[par[slot]].copy()
+                oracle.sweeps(2, L, s, None, betas[step], seed, 0, int(slot), (step - 1) * theta, theta)
+                np.testing.assert_array_equal(cur[slot], s)
+        n_prev = Rn
     gbmc.pa_free(pa)
     gbmc.lattice_free(lat)
 
