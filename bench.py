@@ -462,6 +462,10 @@ def run_learned(args, seeds=None, plain_steps=None):
             kw.update(target_overlap=cfg["target"], dbeta_max=cfg["dbeta_max"], mlp_params=params,
                       overlap_lo=cfg["lo"], overlap_hi=cfg["hi"])
             S = cfg["cap"]
+        # every run from sweep counter 0: its random numbers depend only on (schedule, seed),
+        # not on the runs before it on the same lattices
+        for l in lats:
+            gbmc.lattice_set_sweep_counter(l, 0)
         pa = gbmc.pa_create(ctx, lats, cfg["theta"], S, schedule=schedule, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
