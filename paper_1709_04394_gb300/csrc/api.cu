@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gbmc.h"
 #include "check.cuh"
 #include "internal.h"
@@ -124,19 +126,23 @@ struct gbmc_ctx {
 };
 
 namespace {
-// Brackets one launcher call with CUDA events when profiling is on.
+// Brackets one launcher call with an NVTX range named after its kernel kind
+// (free unless a profiler is attached) and, when profiling is on, with CUDA
+// events.
 struct ProfScope {
     gbmc_ctx* c;
     int kind;
     uint64_t n0;
     cudaEvent_t a = nullptr;
     ProfScope(gbmc_ctx* ctx, int k) : c(ctx), kind(k), n0(g_launches.load()) {
+        nvtxRangePushA(kProfNames[k]);
         if (c->prof) {
             a = c->event();
             cudaEventRecord(a, c->stream);
         }
     }
     ~ProfScope() {
+        nvtxRangePop();
         const uint64_t n = g_launches.load() - n0;
         if (c->prof) {
             cudaEvent_t b = c->event();
