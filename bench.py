@@ -277,7 +277,8 @@ def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
             tuned = gbmc.gbmc_autotune(ctx, lats[0], 0.5 * w["beta_f"], w["theta"])
             result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
                                 "row_walk": tuned.row_walk, "persistent": tuned.persistent,
-                                "candidates": tuned.n_candidates}
+                                "candidates": tuned.n_candidates,
+                                "kernel": "bits" if tuned.kernel == gbmc.GBMC_KERNEL_BITS else "bytes"}
         law = gbmc.GBMC_RESAMPLE_POISSON if w.get("poisson") else gbmc.GBMC_RESAMPLE_NEAREST
         kw = dict(resample=law, initial_replicas=w["nearest"]) if "nearest" in w else {}
         if w.get("msc"):
@@ -303,7 +304,8 @@ def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
         tuned = gbmc.gbmc_autotune(ctx, lat, float(pt_betas(w)[w["T"] // 2]), w["theta"])
         result["tuning"] = {"threads_per_copy": tuned.threads_per_copy, "copies_per_cta": tuned.copies_per_cta,
                             "row_walk": tuned.row_walk, "persistent": tuned.persistent,
-                            "candidates": tuned.n_candidates}
+                            "candidates": tuned.n_candidates,
+                            "kernel": "bits" if tuned.kernel == gbmc.GBMC_KERNEL_BITS else "bytes"}
         pts = [gbmc.pt_create(ctx, lat, pt_betas(w), w["theta"])]
 
         def step(k, graph=False):
