@@ -34,3 +34,28 @@ def test_all_cores_oracle_timing_runs_one_sample_per_core():
     w = dict(kind="sweeps", dim=2, L=64, sweeps=2, beta=0.44, layout=0)
     v, cores, seconds = bench.cpu_oracle_all_cores(w)
     assert cores >= 1 and seconds > 0 and v > 0
+
+
+def test_roofline_attribution_helpers():
+    # which kernel a workload's roofline line is about, the share of the updates
+    # it makes and its algorithmic bytes per update
+    sys.path.insert(0, ROOT)
+    import bench
+
+    W = bench.WORKLOADS
+    assert bench.kernel_name(W["pa-ising2d-L64"], {"sweep_bits": (1, 1.0)}) == "sweep_bits"
+    assert bench.kernel_name(W["pa-ising2d-L64"], {"sweep_resident": (1, 1.0)}) == "sweep_resident"
+    assert bench.kernel_name(W["ising2d-L4096"], {"bitpack_strips": (1, 1.0), "bitpack_convert": (2, 0.1)}) == \
+        "bitpack_strips"
+    assert bench.kernel_name(W["ising2d-L4096"], {"sweep_strips": (1, 1.0)}) == "sweep_strips"
+    assert bench.kernel_name(W["ising2d-L4096-sw"], {"swendsen_wang": (3, 1.0)}) == "swendsen_wang"
+    # every lattice of the mixed batch is one the bit-sliced kernel sweeps
+    assert bench.dominant_share(W["pa-mixed-2d"], "sweep_bits") == 1.0
+    mixed = dict(W["pa-mixed-2d"], lattices=[(2, 24, 0, 1, 1000), (2, 64, 0, 1, 1000)])
+    share = bench.dominant_share(mixed, "sweep_bits")
+    assert abs(share - 64 ** 2 / (24 ** 2 + 64 ** 2)) < 1e-12
+    assert abs(bench.dominant_share(mixed, "sweep_resident") + share - 1.0) < 1e-12
+    # PA: a copy read and written once per theta sweeps, plus E, M and its parent
+    b = bench.alg_bytes_per_update(W["pa-ising2d-L64"], "sweep_bits")
+    assert abs(b - (2 * 4096 + 12) / (4096 * 10)) < 1e-12
+    assert bench.alg_bytes_per_update(W["ising2d-L4096-sw"], "swendsen_wang") == 11.0
