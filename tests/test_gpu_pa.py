@@ -178,33 +178,40 @@ def test_full_size_pa_3d_ea_32x20000_sampled(ctx):
 
 
 def test_full_size_pa_mixed_2d_sampled(ctx):
-    # the mixed batch in one launch per step: (L, R) = (32, 10^5), (64, 5 10^4),
-    # (128, 2 10^4), (256, 10^4), instance k for lattice k; resampling checked
-    # whole, theta sweeps on sampled slots of every lattice, first two steps
+    # the mixed batch in one step: (L, R) = (32, 10^5), (64, 5 10^4), (128, 2 10^4),
+    # (256, 10^4), instance k for lattice k; resampling checked whole, theta sweeps
+    # on sampled slots of every lattice, at steps 1, 2 and 99, 100 (beta = 0.99, 1.0)
     spec, theta, S, seed = [(32, 100000), (64, 50000), (128, 20000), (256, 10000)], 10, 100, 3
     lats = [gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=seed, instance_base=k) for k, (L, R) in enumerate(spec)]
     pa = gbmc.pa_create(ctx, lats, theta, S)
     betas = oracle.linear_betas(1.0, S)
     rng = np.random.default_rng(4)
     E = [np.empty(R, dtype=np.int32) for _, R in spec]
-    for k in range(len(spec)):
-        gbmc.pa_energies_out(ctx, pa, k, E[k])
     lnZ = [L * L * math.log(2.0) for L, _ in spec]
-    for step in (1, 2):
+    done = 0
+    for step in (1, 2, 99, 100):
+        while done < step - 1:
+            row = gbmc.pa_step(ctx, pa)
+            done += 1
+            lnZ = [row[k]["lnZ"] for k in range(len(spec))]
+        for k in range(len(spec)):
+            gbmc.pa_energies_out(ctx, pa, k, E[k])
         prev = [spins_out(ctx, lat) for lat in lats]
         Eprev = [e.astype(np.int64) for e in E]
         row = gbmc.pa_step(ctx, pa)
+        done += 1
         for k, (L, R) in enumerate(spec):
             par = np.empty(R, dtype=np.uint32)
             gbmc.pa_parents_out(ctx, pa, k, par)
             gbmc.pa_energies_out(ctx, pa, k, E[k])
             counts, lnQ = oracle.resample(Eprev[k], betas[step] - betas[step - 1], seed, k, step)
             np.testing.assert_array_equal(par, oracle.children_order(counts))
+            assert row[k]["lnQ"] == pytest.approx(lnQ, rel=RTOL, abs=1e-13)
             lnZ[k] += lnQ
             assert row[k]["lnZ"] == pytest.approx(lnZ[k], rel=RTOL)
             assert row[k]["sumE"] == int(E[k].astype(np.int64).sum())
             cur = spins_out(ctx, lats[k])
-            for slot in rng.integers(R, size=6):
+            for slot in rng.integers(R, size=4):
                 s = prev[k][par[slot]].copy()
                 oracle.sweeps(2, L, s, None, betas[step], seed, k, int(slot), (step - 1) * theta, theta)
                 np.testing.assert_array_equal(cur[slot], s)
