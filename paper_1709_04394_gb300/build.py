@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libgbmc.so")
 # the bounds-checked variant (kernels compiled with GBMC_CHECK)
 BUILD_CHECK = os.path.join(HERE, "_build_check")
 LIB_CHECK = os.path.join(HERE, "libgbmc_check.so")
-SOURCES = ["api.cu", "sweep.cu", "bitsweep.cu", "tiles.cu", "msc.cu", "sw.cu", "pa.cu", "lattice.cu", "static_resample.cu", "schedule.cu", "mlp.cu", "bitpack.cu", "pt.cu"]
+SOURCES = ["api.cu", "sweep.cu", "bitsweep.cu", "tiles.cu", "dcb_bits.cu", "msc.cu", "sw.cu", "pa.cu", "lattice.cu", "static_resample.cu", "schedule.cu", "mlp.cu", "bitpack.cu", "pt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-v"] if os.environ.get("GBMC_PTXAS_VERBOSE") else \

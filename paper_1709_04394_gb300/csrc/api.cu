@@ -54,14 +54,14 @@ enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
     PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_SWEEP_BITS,
-    PK_BP_PACK, PK_COUNT
+    PK_BP_PACK, PK_SWEEP_DCB_BITS, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
                                           "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
                                           "bitpack_strips", "sweep_strips", "pt_exchange", "sweep_bits",
-                                          "bitpack_convert"};
+                                          "bitpack_convert", "sweep_dcb_bits"};
 
 // Device words of a context: 8 flags and counters, then the progress
 // counters of strip-resident sweeps (one per CTA, one CTA per SM).
@@ -1168,12 +1168,15 @@ gbmc_status metropolis_sweeps_dcb(gbmc_ctx* ctx, gbmc_lattice* l, double beta, u
     TL.thr[0] = thr[0];
     TL.thr[1] = thr[1];
     TL.nsweeps = k;
+    // bit-sliced tiles (the same spins) unless the byte-plane kernels are forced
+    const bool bits = dcb_bits_supported(tile) && ctx->sweep_kernel != GBMC_KERNEL_BYTES;
     for (uint32_t m = 0; m < n_rounds; ++m) {
         TL.t0 = l->t + m * k;
         for (uint32_t coarse = 0; coarse < 2; ++coarse) {
             TL.coarse = coarse;
-            ProfScope ps_(ctx, PK_SWEEP_DCB);
-            CUDA_TRY(launch_sweep_dcb(TL, l->ncopies, ctx->stream));
+            ProfScope ps_(ctx, bits ? PK_SWEEP_DCB_BITS : PK_SWEEP_DCB);
+            if (bits) CUDA_TRY(launch_dcb_bits(TL, l->ncopies, ctx->stream));
+            else CUDA_TRY(launch_sweep_dcb(TL, l->ncopies, ctx->stream));
         }
         if (E_series || M_series) {
             ProfScope ps_(ctx, PK_OBS);

@@ -1,13 +1,38 @@
 // bits.cuh -- bit-sliced updates of 32 same-colour sites held in one word
-// (one bit per spin, 1 = down): acceptance bits and the word updates shared by
-// the bit-packed layout (bitpack.cu) and the bit-sliced resident sweeps
-// (bitsweep.cu).
+// (one bit per spin, 1 = down): int8 <-> bit conversion, acceptance bits and
+// the word updates shared by the bit-packed layout (bitpack.cu), the
+// bit-sliced resident sweeps (bitsweep.cu) and the bit-sliced double
+// checkerboard (dcb_bits.cu).
 #pragma once
 #include <cstdint>
 
 #include "device.cuh"
 
 namespace gbmc {
+
+// Down bits of the four bytes (+1 = 0x01, -1 = 0xFF) of a word: bit i = byte i
+// is negative (the four sign bits gathered by one multiply).
+__device__ __forceinline__ uint32_t nib_down(uint32_t four_bytes) {
+    return ((four_bytes & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// Four down bits -> four bytes +1 / -1 (bit i to byte i, then 0 -> 0x01, 1 -> 0xFF).
+__device__ __forceinline__ uint32_t spread4(uint32_t n) {
+    return ((n * 0x00204081u) & 0x01010101u) * 0xFEu + 0x01010101u;
+}
+
+// Eight consecutive sites (bytes b0..b7 in lo, hi) -> the down bits of the four
+// even-x sites (b0, b2, b4, b6) and of the four odd-x sites.
+__device__ __forceinline__ void pack8(uint32_t lo, uint32_t hi, uint32_t& ev, uint32_t& od) {
+    ev = nib_down(__byte_perm(lo, hi, 0x6420));
+    od = nib_down(__byte_perm(lo, hi, 0x7531));
+}
+
+// The inverse: four even-x and four odd-x down bits -> eight bytes.
+__device__ __forceinline__ uint2 unpack8(uint32_t ev, uint32_t od) {
+    const uint32_t e = spread4(ev), o = spread4(od);
+    return make_uint2(__byte_perm(e, o, 0x5140), __byte_perm(e, o, 0x7362));
+}
 
 // r4 = 2 r4 + [u <= T4], r8 = 2 r8 + [u <= T8]: the carry of T - u (set iff
 // no borrow, i.e. u <= T) shifted in by an add-with-carry, two instructions

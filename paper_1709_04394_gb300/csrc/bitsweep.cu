@@ -34,30 +34,6 @@ namespace {
 
 constexpr uint32_t kBitsWarps = 4;  // warps per block: 4 copies (2D) or 16 copies (3D)
 
-// Down bits of the four bytes (+1 = 0x01, -1 = 0xFF) of a word: bit i = byte i
-// is negative (the four sign bits gathered by one multiply).
-__device__ __forceinline__ uint32_t nib_down(uint32_t four_bytes) {
-    return ((four_bytes & 0x80808080u) * 0x00204081u) >> 28;
-}
-
-// Four down bits -> four bytes +1 / -1 (bit i to byte i, then 0 -> 0x01, 1 -> 0xFF).
-__device__ __forceinline__ uint32_t spread4(uint32_t n) {
-    return ((n * 0x00204081u) & 0x01010101u) * 0xFEu + 0x01010101u;
-}
-
-// Eight consecutive sites (bytes b0..b7 in lo, hi) -> the down bits of the four
-// even-x sites (b0, b2, b4, b6) and of the four odd-x sites.
-__device__ __forceinline__ void pack8(uint32_t lo, uint32_t hi, uint32_t& ev, uint32_t& od) {
-    ev = nib_down(__byte_perm(lo, hi, 0x6420));
-    od = nib_down(__byte_perm(lo, hi, 0x7531));
-}
-
-// The inverse: four even-x and four odd-x down bits -> eight bytes.
-__device__ __forceinline__ uint2 unpack8(uint32_t ev, uint32_t od) {
-    const uint32_t e = spread4(ev), o = spread4(od);
-    return make_uint2(__byte_perm(e, o, 0x5140), __byte_perm(e, o, 0x7362));
-}
-
 // Which job a block belongs to (jobs own consecutive blocks).
 __device__ __forceinline__ int job_of(const SweepLaunch& P, uint32_t block) {
     int j = 0;

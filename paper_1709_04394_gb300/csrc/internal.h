@@ -136,6 +136,10 @@ cudaError_t launch_sweep_strips(const StripLaunch& S, uint64_t copies, uint32_t 
 // Double checkerboard (Fig. 5 right): the tiles of coarse colour P.coarse, each
 // swept P.nsweeps times in place (src == dst); T in {32, 64, 128}, L % 2T == 0.
 cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t s);
+// The same double checkerboard with each tile bit-sliced in registers
+// (dcb_bits.cu): T in {64, 128}, the same spins.
+bool dcb_bits_supported(uint32_t T);
+cudaError_t launch_dcb_bits(const TileLaunch& P, uint64_t copies, cudaStream_t s);
 // Global-memory half-sweep over one job (large lattices); colour 0 or 1.
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);

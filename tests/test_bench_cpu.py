@@ -49,6 +49,8 @@ def test_roofline_attribution_helpers():
         "bitpack_strips"
     assert bench.kernel_name(W["ising2d-L4096"], {"sweep_strips": (1, 1.0)}) == "sweep_strips"
     assert bench.kernel_name(W["ising2d-L4096-sw"], {"swendsen_wang": (3, 1.0)}) == "swendsen_wang"
+    assert bench.kernel_name(W["ising2d-L4096-dcb"], {"sweep_dcb_bits": (2, 1.0)}) == "sweep_dcb_bits"
+    assert bench.kernel_name(W["ising2d-L4096-dcb"], {"sweep_dcb": (2, 1.0)}) == "sweep_dcb"
     # every lattice of the mixed batch is one the bit-sliced kernel sweeps
     assert bench.dominant_share(W["pa-mixed-2d"], "sweep_bits") == 1.0
     mixed = dict(W["pa-mixed-2d"], lattices=[(2, 24, 0, 1, 1000), (2, 64, 0, 1, 1000)])
@@ -59,3 +61,8 @@ def test_roofline_attribution_helpers():
     b = bench.alg_bytes_per_update(W["pa-ising2d-L64"], "sweep_bits")
     assert abs(b - (2 * 4096 + 12) / (4096 * 10)) < 1e-12
     assert bench.alg_bytes_per_update(W["ising2d-L4096-sw"], "swendsen_wang") == 11.0
+    # double checkerboard, 64 x 64 tiles, k = 10: the bit-sliced tile reads a
+    # one-site halo, the byte-plane window an 8-site one
+    assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb_bits") - (2 + 4 / 64) / 10) < 1e-12
+    assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb") - (80 ** 2 + 64 ** 2) / 64 ** 2 / 10) \
+        < 1e-12

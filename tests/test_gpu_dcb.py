@@ -13,15 +13,32 @@ pytestmark = pytest.mark.gpu
 BETA_C = 0.4406868
 
 
+AUTO, BYTES = gbmc.GBMC_KERNEL_AUTO, gbmc.GBMC_KERNEL_BYTES
+
+
+@pytest.fixture(params=[AUTO, BYTES], ids=["default", "bytes"])
+def kernel(request, ctx):
+    """Tiles of 64 and 128 sites run bit-sliced by default; BYTES forces the
+    byte-plane tiles (the only kernel for 32)."""
+    gbmc.gbmc_set_sweep_kernel(ctx, request.param)
+    yield request.param
+    gbmc.gbmc_set_sweep_kernel(ctx, AUTO)
+
+
 @pytest.mark.parametrize("L,tile,k,rounds,R,beta", [
     (64, 32, 3, 2, 3, BETA_C),
     (256, 64, 1, 3, 2, 0.3),
     (256, 128, 4, 1, 1, 0.6),
     (512, 64, 10, 1, 1, BETA_C),
     (128, 32, 2, 2, 5, 0.0),        # beta = 0: every visit flips
+    (128, 64, 3, 2, 2, 0.0),        # 2 x 2 tiles: both halo columns of a tile are the same tile
+    (256, 128, 2, 2, 3, 0.0),
+    (512, 128, 5, 2, 2, 1.2),       # cold: few flips
     (4096, 64, 10, 1, 1, BETA_C),   # the benchmark lattice, whole
 ])
-def test_dcb_matches_oracle(ctx, L, tile, k, rounds, R, beta):
+def test_dcb_matches_oracle(ctx, kernel, L, tile, k, rounds, R, beta):
+    if L >= 4096 and kernel == BYTES:
+        pytest.skip("the byte-plane tiles are checked at full size by the bits-equals-bytes test")
     seed = 11 + L
     lat = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=seed, instance_base=2)
     gbmc.lattice_set_sweep_counter(lat, 5)
@@ -80,3 +97,38 @@ def test_dcb_rejects_unsupported_lattices(ctx):
         with pytest.raises(gbmc.GbmcError):
             gbmc.metropolis_sweeps_dcb(ctx, lat, 0.4, 1, 1, 32)
         gbmc.lattice_free(lat)
+
+
+def _dcb_run(ctx, kernel, L, tile, k, rounds, R, seed, beta):
+    gbmc.gbmc_set_sweep_kernel(ctx, kernel)
+    try:
+        lat = gbmc.lattice_init(ctx, 2, L, n_replicas=R, seed=seed)
+        gbmc.lattice_set_sweep_counter(lat, 17)
+        E, M = device_i32(rounds * R), device_i32(rounds * R)
+        gbmc.gbmc_profile(ctx, True)
+        gbmc.metropolis_sweeps_dcb(ctx, lat, beta, rounds, k, tile, E, M)
+        prof = {name: n for name, (n, _) in gbmc.gbmc_profile_read(ctx).items()}
+        gbmc.gbmc_profile(ctx, False)
+        out = (spins_out(ctx, lat), E.cpu().numpy(), M.cpu().numpy())
+        gbmc.lattice_free(lat)
+    finally:
+        gbmc.gbmc_set_sweep_kernel(ctx, AUTO)
+    return out, prof
+
+
+@pytest.mark.parametrize("L,tile,k,rounds,R,beta", [
+    (1024, 64, 5, 3, 2, BETA_C),
+    (1024, 128, 7, 2, 3, 0.35),
+    (4096, 64, 10, 2, 1, BETA_C),   # the benchmark's launch configuration, two rounds
+    (4096, 128, 3, 1, 1, 0.6),
+])
+def test_dcb_bits_equals_bytes(ctx, L, tile, k, rounds, R, beta):
+    """The bit-sliced tiles (the default for 64 and 128) and the byte-plane
+    tiles give the same spins and observables, bit for bit, from a random
+    start; each call runs only its own kernel, two launches per round."""
+    a, pa = _dcb_run(ctx, AUTO, L, tile, k, rounds, R, 5 + L, beta)
+    b, pb = _dcb_run(ctx, BYTES, L, tile, k, rounds, R, 5 + L, beta)
+    assert pa.get("sweep_dcb_bits") == 2 * rounds and "sweep_dcb" not in pa
+    assert pb.get("sweep_dcb") == 2 * rounds and "sweep_dcb_bits" not in pb
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
