@@ -775,7 +775,10 @@ def kernel_name(w, prof):
         # int8 lattices too: their strip sweeps run packed to bits
         return "bitpack_strips" if "bitpack_strips" in prof else "bitpack_halfsweep"
     if "dcb" in w:
-        return "sweep_dcb_bits" if "sweep_dcb_bits" in prof else "sweep_dcb"
+        for k in ("sweep_dcb_resident", "sweep_dcb_bits"):
+            if k in prof:
+                return k
+        return "sweep_dcb"
     if w.get("sw"):
         return "swendsen_wang"
     return "sweep_strips" if "sweep_strips" in prof else "sweep_tiles"
@@ -813,6 +816,10 @@ def alg_bytes_per_update(w, kname):
         return float(SW_BYTES_PER_SITE)
     if "dcb" in w:
         k, tile = w["dcb"]
+        if kname == "sweep_dcb_resident":
+            # the lattice read and written once per call; per round each tile writes
+            # its edges (T / 2 bytes) and reads its neighbours' (T / 4 bytes)
+            return 2.0 / w["sweeps"] + 0.75 / (tile * k)
         if kname == "sweep_dcb_bits":
             return (2 * tile ** 2 + 4 * tile) / tile ** 2 / k   # tile and one-site halo in, tile out, per k sweeps
         return ((tile + 16) ** 2 + tile ** 2) / tile ** 2 / k   # window in, tile out, per k sweeps

@@ -112,7 +112,12 @@ gbmc_status gbmc_set_resample_mode(gbmc_ctx *ctx, int32_t fused);
  * trading its first and last rows with its neighbours through global memory
  * after every half-sweep (bounded waits; GBMC_ERR_TIMEOUT if one runs out);
  * GRID uses the per-launch kernels (halo tiles of up to 4 sweeps, resp. one
- * launch per half-sweep). Unknown mode: GBMC_ERR_ARG. */
+ * launch per half-sweep). Double-checkerboard sweeps with bit-sliced tiles
+ * (metropolis_sweeps_dcb): PERSISTENT runs every round of a call in one
+ * launch whenever all tile pairs fit on the device at once, GRID one launch
+ * per coarse colour and round, AUTO the first for small k (k <= 3 with tiles
+ * of 64, k <= 7 with tiles of 128), the second otherwise. Unknown mode:
+ * GBMC_ERR_ARG. */
 enum { GBMC_LAUNCH_AUTO = 0, GBMC_LAUNCH_GRID = 1, GBMC_LAUNCH_PERSISTENT = 2 };
 gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
 /* Kernel of the resident sweeps (checkerboard sweeps of copies held on chip,
@@ -224,9 +229,18 @@ gbmc_status metropolis_sweeps(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uin
  * the multi-hit variant). The lattice is cut into tile x tile tiles, tile
  * (a, b) holding the sites with x / tile = a, y / tile = b and having coarse
  * colour (a + b) mod 2. A round updates every tile of coarse colour 0, then
- * every tile of coarse colour 1 (one launch each); a tile gets k full
- * checkerboard sweeps (fine colour 0, then 1) from shared memory while every
- * site outside it stays fixed. The j-th sweep of round m uses sweep counter
+ * every tile of coarse colour 1; a tile gets k full checkerboard sweeps (fine
+ * colour 0, then 1) held on chip while every site outside it stays fixed.
+ * Tiles of 64 and 128 are held one bit per spin in registers, one launch per
+ * coarse colour and round; with no E/M series asked for, a cooperative-capable
+ * device and every tile pair of the call resident at once, all rounds can
+ * instead run in one launch, each tile kept on chip for the whole call and
+ * trading only its edge rows and columns with its neighbours through bounded
+ * waits (a wait that runs out raises GBMC_ERR_TIMEOUT at the next
+ * synchronising call): the choice follows gbmc_set_sweep_launch (AUTO: one
+ * launch for small k, where the per-launch loads dominate). GBMC_KERNEL_BYTES
+ * (gbmc_set_sweep_kernel) forces the byte-plane tiles, the only ones for 32.
+ * Every variant gives the same spins. The j-th sweep of round m uses sweep counter
  * t + k m + j (t = the lattice's counter on entry) for the Philox words of the
  * tile's sites, the words plain sweeps would use, and the counter advances by
  * k n_rounds; the configurations differ from plain sweeps because the order

@@ -54,14 +54,15 @@ enum ProfKind {
     PK_INIT, PK_COUPLINGS, PK_SWEEP_RES, PK_HALFSWEEP, PK_OBS, PK_PA_WEIGHTS, PK_PA_REDUCE,
     PK_PA_DRAWS, PK_PA_PLACE, PK_PA_RECORD, PK_PA_RESET, PK_SWEEP_TILES, PK_SCHEDULE, PK_PA_FUSED,
     PK_BP_HALFSWEEP, PK_SWEEP_DCB, PK_SWEEP_MSC, PK_SW, PK_BP_STRIPS, PK_SWEEP_STRIPS, PK_PT_EXCHANGE, PK_SWEEP_BITS,
-    PK_BP_PACK, PK_SWEEP_DCB_BITS, PK_COUNT
+    PK_BP_PACK, PK_SWEEP_DCB_BITS, PK_SWEEP_DCB_RES, PK_COUNT
 };
 const char* const kProfNames[PK_COUNT] = {"init_spins", "couplings", "sweep_resident", "halfsweep_global",
                                           "observables", "pa_weights", "pa_reduce", "pa_draws", "pa_place",
                                           "pa_record", "pa_reset", "sweep_tiles", "schedule", "pa_resample",
                                           "bitpack_halfsweep", "sweep_dcb", "sweep_msc", "swendsen_wang",
                                           "bitpack_strips", "sweep_strips", "pt_exchange", "sweep_bits",
-                                          "bitpack_convert", "sweep_dcb_bits"};
+                                          "bitpack_convert", "sweep_dcb_bits",
+                                          "sweep_dcb_resident"};
 
 // Device words of a context: 8 flags and counters, then the progress
 // counters of strip-resident sweeps (one per CTA, one CTA per SM).
@@ -166,6 +167,8 @@ struct gbmc_lattice {
     uint32_t* jb3;     // the same bonds as bit words of the bit-sliced 3D L = 8 sweep [inst][2][6][8]
     uint32_t* packed;  // bit-packed copy of the configuration for the strip-resident bit sweeps (int8 layout)
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
+    uint32_t* dcb_scratch;    // tile edges and progress counters of the resident double checkerboard
+    size_t dcb_scratch_bytes;
     uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags and union-find forest
     uint32_t* sw_parent;
     uint32_t t;        // sweep counter
@@ -772,6 +775,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->jsplit) cudaFree(l->jsplit);
     if (l->jb3) cudaFree(l->jb3);
     if (l->packed) cudaFree(l->packed);
+    if (l->dcb_scratch) cudaFree(l->dcb_scratch);
     if (l->alt) cudaFree(l->alt);
     if (l->sw_bonds) cudaFree(l->sw_bonds);
     if (l->sw_parent) cudaFree(l->sw_parent);
@@ -1170,6 +1174,54 @@ gbmc_status metropolis_sweeps_dcb(gbmc_ctx* ctx, gbmc_lattice* l, double beta, u
     TL.nsweeps = k;
     // bit-sliced tiles (the same spins) unless the byte-plane kernels are forced
     const bool bits = dcb_bits_supported(tile) && ctx->sweep_kernel != GBMC_KERNEL_BYTES;
+    // every round in one launch, the tiles resident in registers: worth it for
+    // small k, where loading and storing the tiles every round dominates; for
+    // larger k the per-round launches are faster (a launch ends when its SM
+    // work is done, while resident tiles that run ahead of their neighbours
+    // take issue slots from the slower ones)
+    const uint32_t k_resident = tile == 64 ? 3u : 7u;
+    const bool resident_mode = ctx->launch_mode == GBMC_LAUNCH_PERSISTENT ||
+                               (ctx->launch_mode == GBMC_LAUNCH_AUTO && k <= k_resident);
+    if (bits && !E_series && !M_series && resident_mode && ctx->coop &&
+        dcb_resident_fits(TL.L, tile, l->ncopies, ctx->sm_count)) {
+        const size_t need = dcb_resident_bytes(TL.L, tile, l->ncopies);
+        if (l->dcb_scratch_bytes < need) {
+            if (l->dcb_scratch) {
+                CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+                cudaFree(l->dcb_scratch);
+                l->dcb_scratch = nullptr;
+                l->dcb_scratch_bytes = 0;
+            }
+            cudaError_t e = cudaMalloc(&l->dcb_scratch, need);
+            if (e != cudaSuccess) return fail(GBMC_ERR_OOM, "cudaMalloc(tile edges): %s", cudaGetErrorString(e));
+            l->dcb_scratch_bytes = need;
+        }
+        const uint64_t tiles = (uint64_t)(TL.L / tile) * (TL.L / tile) * l->ncopies;
+        DcbResident D;
+        std::memset(&D, 0, sizeof(D));
+        D.spins = l->cur;
+        D.edges = l->dcb_scratch;
+        D.progress = l->dcb_scratch + tiles * (tile / 8);
+        D.err = ctx->words + 1;
+        D.budget = ctx->budget;
+        D.seed = l->d.seed;
+        D.L = TL.L;
+        D.T = tile;
+        D.R = l->d.n_replicas;
+        D.inst_base = l->d.instance_base;
+        D.t0 = l->t;
+        D.k = k;
+        D.n_rounds = n_rounds;
+        D.phantom = ctx->phantom;
+        D.thr[0] = thr[0];
+        D.thr[1] = thr[1];
+        {
+            ProfScope ps_(ctx, PK_SWEEP_DCB_RES);
+            CUDA_TRY(launch_dcb_resident(D, l->ncopies, ctx->stream));
+        }
+        l->t += n_rounds * k;
+        return GBMC_OK;
+    }
     for (uint32_t m = 0; m < n_rounds; ++m) {
         TL.t0 = l->t + m * k;
         for (uint32_t coarse = 0; coarse < 2; ++coarse) {

@@ -140,6 +140,25 @@ cudaError_t launch_sweep_dcb(const TileLaunch& P, uint64_t copies, cudaStream_t 
 // (dcb_bits.cu): T in {64, 128}, the same spins.
 bool dcb_bits_supported(uint32_t T);
 cudaError_t launch_dcb_bits(const TileLaunch& P, uint64_t copies, cudaStream_t s);
+// Every round of a call in one cooperative launch, tiles resident in
+// registers, tile edges traded through `edges` and announced by `progress`
+// (one counter per tile; both in one buffer of dcb_resident_bytes, progress
+// after the edges). Waits give up after `budget` cycles or when *err is
+// raised, raising *err; phantom: extra rounds a wait asks for (0 in
+// production; tests set 1 to make a wait run out).
+struct DcbResident {
+    int8_t* spins;
+    uint32_t* edges;
+    unsigned int* progress;
+    unsigned int* err;
+    long long budget;
+    uint64_t seed;
+    uint32_t L, T, R, inst_base, t0, k, n_rounds, phantom;
+    uint32_t thr[2];  // T(4), T(8)
+};
+size_t dcb_resident_bytes(uint32_t L, uint32_t T, uint64_t copies);
+bool dcb_resident_fits(uint32_t L, uint32_t T, uint64_t copies, int sm_count);
+cudaError_t launch_dcb_resident(const DcbResident& D, uint64_t copies, cudaStream_t s);
 // Global-memory half-sweep over one job (large lattices); colour 0 or 1.
 cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint32_t t,
                                     cudaStream_t s);

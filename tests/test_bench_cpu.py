@@ -49,6 +49,7 @@ def test_roofline_attribution_helpers():
         "bitpack_strips"
     assert bench.kernel_name(W["ising2d-L4096"], {"sweep_strips": (1, 1.0)}) == "sweep_strips"
     assert bench.kernel_name(W["ising2d-L4096-sw"], {"swendsen_wang": (3, 1.0)}) == "swendsen_wang"
+    assert bench.kernel_name(W["ising2d-L4096-dcb"], {"sweep_dcb_resident": (1, 1.0)}) == "sweep_dcb_resident"
     assert bench.kernel_name(W["ising2d-L4096-dcb"], {"sweep_dcb_bits": (2, 1.0)}) == "sweep_dcb_bits"
     assert bench.kernel_name(W["ising2d-L4096-dcb"], {"sweep_dcb": (2, 1.0)}) == "sweep_dcb"
     # every lattice of the mixed batch is one the bit-sliced kernel sweeps
@@ -64,5 +65,7 @@ def test_roofline_attribution_helpers():
     # double checkerboard, 64 x 64 tiles, k = 10: the bit-sliced tile reads a
     # one-site halo, the byte-plane window an 8-site one
     assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb_bits") - (2 + 4 / 64) / 10) < 1e-12
+    assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb_resident") -
+               (2 / 1000 + 0.75 / 640)) < 1e-12
     assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb") - (80 ** 2 + 64 ** 2) / 64 ** 2 / 10) \
         < 1e-12

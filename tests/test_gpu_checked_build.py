@@ -98,9 +98,12 @@ for dim, L in [(2, 6), (3, 4), (2, 64), (3, 16)]:
     lat = gbmc.lattice_init(ctx, dim, L, n_replicas=3, seed=9)
     gbmc.swendsen_wang(ctx, lat, 0.4, 2)
     gbmc.lattice_free(lat)
-for L, tile in [(64, 32), (128, 64), (256, 128)]:  # byte-plane tiles, then bit-sliced ones
+# byte-plane tiles, bit-sliced tiles one launch per round (an E series asked
+# for), bit-sliced tiles resident for the whole call
+for L, tile, series in [(64, 32, False), (128, 64, True), (256, 128, True), (128, 64, False), (256, 128, False)]:
     lat = gbmc.lattice_init(ctx, 2, L, n_replicas=3, seed=10)
-    gbmc.metropolis_sweeps_dcb(ctx, lat, 0.44, 2, 2, tile)
+    Es = torch.zeros(2 * 3, dtype=torch.int32, device="cuda") if series else None
+    gbmc.metropolis_sweeps_dcb(ctx, lat, 0.44, 2, 2, tile, Es, None)
     got = spins(lat)
     s = oracle.init_spins(2, L, 10, 0, 2, True)
     oracle.dcb_sweeps(L, tile, s, 0.44, 10, 0, 2, 0, 2, 2)
@@ -128,4 +131,4 @@ def test_checked_build_records_no_bounds_failure():
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    assert "checked ok 25" in r.stdout
+    assert "checked ok 27" in r.stdout
