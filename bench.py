@@ -356,25 +356,34 @@ def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
     ms_local, _, upd_local = timed(warmup, False)
     launches = gbmc.gbmc_kernel_launches() - launches0
     clocks = sampler.stop()
+    if e2e:
+        # right after the timed region, under the same conditions (clocks sampled too)
+        result["e2e"] = run_e2e(gbmc, ctx, w, lats, pa if w["kind"] == "pa" else None,
+                                pts if w["kind"] == "pt" else None, dist, ws, steps, seed0, local)
     # the same K steps again with a CUDA event pair around every launch: per-kernel times
     ms_prof, prof, upd_prof = timed(warmup + steps, True)
     ms = max_over_ranks(dist, ws, ms_local, device="cuda")
     upd_all = sum_over_ranks(dist, ws, float(upd_local), device="cuda")
     result.update(ms=ms, ms_profiled=ms_prof, prof=prof, launches=launches, clocks=clocks, upd_all=upd_all,
                   upd_local=upd_local, upd_prof=upd_prof, steps=steps, warmup=warmup)
-    if not e2e:
-        if w["kind"] == "pa":
-            gbmc.pa_free(pa)
-        if w["kind"] == "pt":
-            gbmc.pt_free(pts[0])
-        for l in lats:
-            gbmc.lattice_free(l)
-        gbmc.gbmc_destroy(ctx)
-        return result
+    if w["kind"] == "pa":
+        gbmc.pa_free(pa)
+    if w["kind"] == "pt":
+        gbmc.pt_free(pts[0])
+    for l in lats:
+        gbmc.lattice_free(l)
+    gbmc.gbmc_destroy(ctx)
+    return result
 
-    # end-to-end through the C ABI with host buffers: the population comes in
-    # from pinned host memory, and the final population and statistics go back,
-    # every step.
+
+def run_e2e(gbmc, ctx, w, lats, pa, pts, dist, ws, steps, seed0, local):
+    """End to end through the C ABI with host buffers: the population comes in
+    from pinned host memory, and the final population and statistics go back,
+    every step (up to 3 steps; clocks sampled meanwhile)."""
+    import torch
+
+    from paper_1709_04394_gb300 import inputs
+
     n_e2e = max(1, min(steps, 3))
     hosts_in, hosts_out = [], []
     for i, l in enumerate(lats):
@@ -388,6 +397,8 @@ def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
     d2h = sum(h.numel() for h in hosts_out)
     barrier(dist, ws)
     torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
     t0 = time.perf_counter()
     for k in range(n_e2e):
         for l, hin in zip(lats, hosts_in):
@@ -413,16 +424,9 @@ def run_gpu(args, w, ws, rank, local, steps=None, warmup=None, e2e=True):
         for l, hout in zip(lats, hosts_out):
             gbmc.lattice_copy_out(ctx, l, hout)
     t_e2e = time.perf_counter() - t0
+    clocks = sampler.stop()
     t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
-    result["e2e"] = dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e)
-    if w["kind"] == "pa":
-        gbmc.pa_free(pa)
-    if w["kind"] == "pt":
-        gbmc.pt_free(pts[0])
-    for l in lats:
-        gbmc.lattice_free(l)
-    gbmc.gbmc_destroy(ctx)
-    return result
+    return dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e, clocks=clocks)
 
 
 # MLP proposals are kept when their realised overlap lies in [0.80, 0.90], a band
@@ -725,7 +729,8 @@ def main():
     upd_step = res["upd_local"] / res["steps"]
     e = res["e2e"]
     line["e2e"] = {"value": ws * upd_step / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
-                   "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"]}
+                   "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"],
+                   "clocks": e["clocks"]}
     if not args.no_secondary and args.workload == "pa-ising2d-L64" and not args.graph:
         line["secondary"] = secondary
         if ws == 1:
