@@ -126,7 +126,7 @@ gbmc_status gbmc_set_sweep_launch(gbmc_ctx *ctx, int32_t mode);
  * a colour per word (the multi-spin coding of sites of Sec. 3.1 applied to the
  * copy on chip; the population stays in the int8 layout in device memory and
  * is converted on load and store), for 2D ferromagnets with L in {16, 32, 64,
- * 128, 256} and 3D lattices (ferromagnet or +-J) with L = 8; other lattices of the
+ * 128, 256} and 3D lattices (ferromagnet or +-J) with L = 8 or 16; other lattices of the
  * same call take the BYTES kernel. AUTO (default): BITS for a supported lattice
  * class unless gbmc_autotune timed BYTES faster for it. The mode also picks the
  * strip-resident sweeps of large int8 2D ferromagnets (gbmc_set_sweep_launch):

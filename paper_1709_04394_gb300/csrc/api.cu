@@ -164,7 +164,7 @@ struct gbmc_lattice {
     int8_t* cur;       // buffer holding the current configuration
     uint8_t* jbits;    // +-J bond planes [inst][3][N]
     uint8_t* jsplit;   // the same bonds per colour plane [inst][2][6][N/2] (L % 8 == 0)
-    uint32_t* jb3;     // the same bonds as bit words of the bit-sliced 3D L = 8 sweep [inst][2][6][8]
+    uint32_t* jb3;     // the same bonds as bit words of the bit-sliced 3D sweeps [inst][2][6][L^3 / 64]
     uint32_t* packed;  // bit-packed copy of the configuration for the strip-resident bit sweeps (int8 layout)
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
     uint32_t* dcb_scratch;    // tile edges and progress counters of the resident double checkerboard
@@ -743,7 +743,7 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
             CUDA_TRY(launch_split_bonds(l->jbits, l->jsplit, (uint32_t)d->L, d->n_instances, ctx->stream));
         }
         if (bits_supported(d->dim, d->L)) {
-            e = cudaMalloc(&l->jb3, 96ull * 4 * d->n_instances);
+            e = cudaMalloc(&l->jb3, bits3_bond_words((uint32_t)d->L) * 4 * d->n_instances);
             if (e != cudaSuccess) {
                 if (l->jsplit) cudaFree(l->jsplit);
                 cudaFree(l->jbits);
@@ -751,7 +751,7 @@ gbmc_status lattice_init(gbmc_ctx* ctx, const gbmc_lattice_desc* d, void* spins_
                 delete l;
                 return fail(GBMC_ERR_OOM, "cudaMalloc(bond words): %s", cudaGetErrorString(e));
             }
-            CUDA_TRY(launch_bits3_bonds(l->jbits, l->jb3, d->n_instances, ctx->stream));
+            CUDA_TRY(launch_bits3_bonds(l->jbits, l->jb3, (uint32_t)d->L, d->n_instances, ctx->stream));
         }
     }
     {

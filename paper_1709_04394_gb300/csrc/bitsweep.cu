@@ -23,6 +23,13 @@
 //    in the slab z (bit 4 y + j, x = 2 j + ((y + z + c) & 1)), i.e. colour
 //    ranks 32 z .. 32 z + 31. Neighbours along x and y are rotations of the
 //    other plane's word, along z the words of the neighbouring lanes.
+//  * k_sweep_bits3w: 3D lattices with L = 16, one warp per copy in registers:
+//    word w = 4 z + q of a plane holds rows y = 4 q .. 4 q + 3 of slab z, bit
+//    8 (y & 3) + j = the site x = 2 j + ((y + z + c) & 1) (colour ranks 32 w ..
+//    32 w + 31); lane l holds words l and l + 32 (slabs l / 4 and 8 + l / 4).
+//    Neighbours along x are rotations within a row's byte, along y byte shifts
+//    (across the words of the slab's four lanes), along z the words of the
+//    lanes l -/+ 4.
 #include "bits.cuh"
 #include "check.cuh"
 #include "device.cuh"
@@ -390,6 +397,160 @@ __global__ void __launch_bounds__(128) k_sweep_bits3(const __grid_constant__ Swe
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3D, L = 16
+// ---------------------------------------------------------------------------
+
+// Rotation of each 8-site row (byte) of a word by one site: bit j takes bit
+// j - 1 (lft) or bit j + 1 (rgt), wrapping within the row.
+__device__ __forceinline__ uint32_t rot_byte_lft(uint32_t w) {
+    return ((w << 1) & 0xFEFEFEFEu) | ((w >> 7) & 0x01010101u);
+}
+__device__ __forceinline__ uint32_t rot_byte_rgt(uint32_t w) {
+    return ((w >> 1) & 0x7F7F7F7Fu) | ((w << 7) & 0x80808080u);
+}
+
+// The six neighbour words (order of nb3) of this lane's two colour-c words,
+// from the other plane's words oth[h] (h = 0: slab l / 4, h = 1: slab 8 + l / 4).
+__device__ __forceinline__ void nb3w(const uint32_t oth[2], uint32_t lane, uint32_t colour, uint32_t nb[2][6]) {
+    const uint32_t prevl = (lane & ~3u) | ((lane - 1u) & 3u), nextl = (lane & ~3u) | ((lane + 1u) & 3u);
+#pragma unroll
+    for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t z = (lane >> 2) + 8u * h;
+        // rows (bytes) whose sites of colour c have odd x: (y + z + c) odd
+        const uint32_t odd_rows = ((z + colour) & 1u) ? 0x00FF00FFu : 0xFF00FF00u;
+        nb[h][0] = oth[h];
+        nb[h][1] = (rot_byte_lft(oth[h]) & ~odd_rows) | (rot_byte_rgt(oth[h]) & odd_rows);
+        const uint32_t prev = __shfl_sync(0xffffffffu, oth[h], prevl);  // rows y - 4 .. y - 1
+        const uint32_t next = __shfl_sync(0xffffffffu, oth[h], nextl);
+        nb[h][2] = __funnelshift_l(prev, oth[h], 8);  // row y takes row y - 1
+        nb[h][3] = __funnelshift_r(oth[h], next, 8);  // row y takes row y + 1
+    }
+    // slabs z -/+ 1: lanes l -/+ 4, the other half across the wrap
+    const uint32_t a0 = __shfl_sync(0xffffffffu, oth[0], (lane - 4u) & 31u);
+    const uint32_t a1 = __shfl_sync(0xffffffffu, oth[1], (lane - 4u) & 31u);
+    const uint32_t b0 = __shfl_sync(0xffffffffu, oth[0], (lane + 4u) & 31u);
+    const uint32_t b1 = __shfl_sync(0xffffffffu, oth[1], (lane + 4u) & 31u);
+    nb[0][4] = lane >= 4u ? a0 : a1;
+    nb[1][4] = lane >= 4u ? a1 : a0;
+    nb[0][5] = lane < 28u ? b0 : b1;
+    nb[1][5] = lane < 28u ? b1 : b0;
+}
+
+template <bool EA>
+__global__ void __launch_bounds__(128) k_sweep_bits3w(const __grid_constant__ SweepLaunch P, uint32_t wpb) {
+    __shared__ __align__(16) uint32_t stage[kBitsWarps][2][64];  // [warp][plane][word]
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const int jid = job_of(P, blockIdx.x);
+    const SweepJob& J = P.jobs[jid];
+    const uint64_t ncopies = (uint64_t)J.n_inst * J.R;
+    const uint64_t slot = (uint64_t)(blockIdx.x - P.cta_begin[jid]) * wpb + wib;
+    if (slot >= ncopies) return;  // whole warp; no block barriers follow
+    uint32_t inst = 0, r = 0;
+    split_copy(slot, J.R, inst, r);
+    if (J.nlive && r >= J.nlive[inst]) return;  // variable populations: only live slots
+    constexpr uint32_t N = 4096u;
+    uint8_t* stb = reinterpret_cast<uint8_t*>(stage[wib]);
+
+    // ---- load: chunk m of 16 bytes = row y = m & 15 of slab z = m >> 4; its 8
+    // even-x sites (colour (y + z) & 1) and 8 odd-x sites are byte m of the two planes ----
+    const uint64_t srcslot = J.parent ? (uint64_t)inst * J.R + J.parent[slot] : slot;
+    const uint4* g = reinterpret_cast<const uint4*>(J.src + GBMC_IDX(srcslot, ncopies) * N);
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k) {
+        const uint32_t m = lane + 32u * k;
+        const uint4 v = g[m];
+        uint32_t e0, o0, e1, o1;
+        pack8(v.x, v.y, e0, o0);
+        pack8(v.z, v.w, e1, o1);
+        const uint32_t ce = ((m & 15u) + (m >> 4)) & 1u;
+        stb[GBMC_IDX(ce * 256u + m, 512u)] = (uint8_t)(e0 | (e1 << 4));
+        stb[GBMC_IDX((ce ^ 1u) * 256u + m, 512u)] = (uint8_t)(o0 | (o1 << 4));
+    }
+    __syncwarp();
+    uint32_t pl[2][2] = {{stage[wib][0][lane], stage[wib][0][lane + 32u]},
+                         {stage[wib][1][lane], stage[wib][1][lane + 32u]}};  // [colour][half]
+    __syncwarp();
+
+    uint32_t jb[2][2][6];  // [colour][half][bond kind]
+#pragma unroll
+    for (uint32_t c = 0; c < 2; ++c)
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h)
+#pragma unroll
+            for (uint32_t k = 0; k < 6; ++k)
+                jb[c][h][k] = EA ? J.jb3[GBMC_IDX((((uint64_t)inst * 2u + c) * 6u + k) * 64u + lane + 32u * h,
+                                                  J.n_inst * 768ull)]
+                                 : 0u;
+
+    uint32_t T4, T8, T12;
+    copy_thresholds(J, slot, T4, T8, T12);
+    const uint32_t instance = J.inst_base + inst;
+    const uint32_t k0 = (uint32_t)J.seed, k1 = (uint32_t)(J.seed >> 32);
+    const bool want_final = J.E || J.M || J.hist;
+    const uint32_t nsw = J.nsweeps;
+    for (uint32_t s = 0; s <= nsw; ++s) {
+        if (s == nsw && nsw != 0) break;
+        const bool sweep = s < nsw;
+        if (sweep) {
+            const uint32_t t = J.t0 + s;
+#pragma unroll 1
+            for (uint32_t colour = 0; colour < 2; ++colour) {
+                const PhiloxFixed pf = philox_fix(t, r, c3_word(kPurposeMetro, colour, instance), k0, k1);
+                uint32_t nb[2][6];
+                nb3w(colour ? pl[0] : pl[1], lane, colour, nb);
+#pragma unroll
+                for (uint32_t h = 0; h < 2; ++h) {
+                    const uint32_t w = colour ? pl[1][h] : pl[0][h];
+                    uint32_t d[6];
+#pragma unroll
+                    for (uint32_t k = 0; k < 6; ++k) d[k] = w ^ nb[h][k] ^ (colour ? jb[1][h][k] : jb[0][h][k]);
+                    const uint32_t nw =
+                        bp3_word_update(w, d[0], d[1], d[2], d[3], d[4], d[5], pf, 8u * (lane + 32u * h), T4, T8, T12);
+                    if (colour) pl[1][h] = nw;
+                    else pl[0][h] = nw;
+                }
+            }
+        }
+        const bool last = sweep ? s + 1 == nsw : true;
+        if ((J.Eser && sweep) || (J.Mser && sweep) || (last && want_final)) {
+            uint32_t nb[2][6];
+            nb3w(pl[1], lane, 0u, nb);
+            int U = 0;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h)
+#pragma unroll
+                for (uint32_t k = 0; k < 6; ++k) U += __popc(pl[0][h] ^ nb[h][k] ^ jb[0][h][k]);
+            int D = __popc(pl[0][0]) + __popc(pl[0][1]) + __popc(pl[1][0]) + __popc(pl[1][1]);
+#pragma unroll
+            for (uint32_t o = 16; o > 0; o >>= 1) {
+                U += __shfl_xor_sync(0xffffffffu, U, o);
+                D += __shfl_xor_sync(0xffffffffu, D, o);
+            }
+            // E = 2 (unsatisfied bonds of the colour-0 sites) - 3 N
+            if (lane == 0) record_copy(J, slot, inst, s, sweep, last, 2 * U - 3 * (int)N, (int)N - 2 * D);
+        }
+    }
+
+    // ---- store ----
+    if (nsw > 0 || J.dst != J.src || J.parent) {
+        stage[wib][0][lane] = pl[0][0];
+        stage[wib][0][lane + 32u] = pl[0][1];
+        stage[wib][1][lane] = pl[1][0];
+        stage[wib][1][lane + 32u] = pl[1][1];
+        __syncwarp();
+        uint4* d = reinterpret_cast<uint4*>(J.dst + slot * N);
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            const uint32_t m = lane + 32u * k;
+            const uint32_t ce = ((m & 15u) + (m >> 4)) & 1u;
+            const uint32_t ev = stb[GBMC_IDX(ce * 256u + m, 512u)], od = stb[GBMC_IDX((ce ^ 1u) * 256u + m, 512u)];
+            const uint2 lo = unpack8(ev & 15u, od & 15u), hi = unpack8(ev >> 4, od >> 4);
+            d[m] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
+}
+
 // Bond words of the 3D L = 8 bit-sliced sweep: for instance i, colour c, bond
 // kind k and slab z, bit 4 y + j = 1 iff the bond between the colour-c site
 // (x = 2 j + ((y + z + c) & 1), y, z) and its k-th neighbour (order of nb3)
@@ -422,15 +583,51 @@ __global__ void k_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_in
     jb3[g] = word;
 }
 
+// The same for L = 16 (word w = 4 z + q of k_sweep_bits3w, bit 8 (y & 3) + j,
+// y = 4 q + (y & 3)): for instance i, colour c, bond kind k, word w at
+// ((i * 2 + c) * 6 + k) * 64 + w.
+__global__ void k_bits3w_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_inst * 768u) return;
+    const uint32_t inst = g / 768u, rem = g - inst * 768u;
+    const uint32_t c = rem / 384u, k = (rem / 64u) % 6u, w = rem & 63u;
+    const uint32_t z = w >> 2, q = w & 3u;
+    constexpr uint32_t L = 16u, N = 4096u;
+    const uint8_t* jb = jbits + (uint64_t)inst * 3u * N;
+    uint32_t word = 0;
+    for (uint32_t yy = 0; yy < 4; ++yy)
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t y = 4u * q + yy;
+            const uint32_t o = (y + z + c) & 1u, x = 2u * j + o;
+            const uint32_t i = (z * L + y) * L + x;
+            const uint32_t xm = (z * L + y) * L + ((x + L - 1u) & (L - 1u));  // site x - 1
+            uint32_t bond;
+            switch (k) {
+                case 0: bond = o ? jb[xm] : jb[i]; break;                                     // same-j x neighbour
+                case 1: bond = o ? jb[i] : jb[xm]; break;                                     // the other x neighbour
+                case 2: bond = jb[N + (z * L + ((y + L - 1u) & (L - 1u))) * L + x]; break;    // y - 1
+                case 3: bond = jb[N + i]; break;                                              // y + 1
+                case 4: bond = jb[2u * N + ((((z + L - 1u) & (L - 1u)) * L + y) * L + x)]; break;  // z - 1
+                default: bond = jb[2u * N + i]; break;                                        // z + 1
+            }
+            word |= (bond ? 1u : 0u) << (8u * yy + j);
+        }
+    jb3[g] = word;
+}
+
 }  // namespace
 
 bool bits_supported(int dim, int L) {
-    return (dim == 2 && (L == 16 || L == 32 || L == 64 || L == 128 || L == 256)) || (dim == 3 && L == 8);
+    return (dim == 2 && (L == 16 || L == 32 || L == 64 || L == 128 || L == 256)) || (dim == 3 && (L == 8 || L == 16));
 }
 
-cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s) {
-    const uint32_t n = n_inst * 96u;
-    k_bits3_bonds<<<(n + 255u) / 256u, 256, 0, s>>>(jbits, jb3, n_inst);
+size_t bits3_bond_words(uint32_t L) { return L == 8 ? 96u : 768u; }
+
+cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t L, uint32_t n_inst, cudaStream_t s) {
+    if (L != 8 && L != 16) return cudaErrorInvalidValue;
+    const uint32_t n = n_inst * (uint32_t)bits3_bond_words(L);
+    if (L == 8) k_bits3_bonds<<<(n + 255u) / 256u, 256, 0, s>>>(jbits, jb3, n_inst);
+    else k_bits3w_bonds<<<(n + 255u) / 256u, 256, 0, s>>>(jbits, jb3, n_inst);
     count_launch();
     return cudaGetLastError();
 }
@@ -453,7 +650,7 @@ static cudaError_t launch_bits_group(const SweepLaunch& P0, bool rows, cudaStrea
         // 2D: one copy per warp, or 32 / (N / 64) copies when a plane has fewer
         // than 32 words (L = 16: 8, L = 32: 2); 3D L = 8: 4 copies per warp
         const uint32_t pw = J.N / 64u;
-        const uint32_t per_warp = P.dim == 2 ? (pw < 32u ? 32u / pw : 1u) : 4u;
+        const uint32_t per_warp = P.dim == 2 ? (pw < 32u ? 32u / pw : 1u) : (J.L == 8 ? 4u : 1u);
         const uint64_t nb = ((uint64_t)J.n_inst * J.R + per_warp * kWarps - 1) / (per_warp * kWarps);
         if (total + nb > 0x7FFFFFFFull) return cudaErrorInvalidValue;
         total += (uint32_t)nb;
@@ -471,6 +668,9 @@ static cudaError_t launch_bits_group(const SweepLaunch& P0, bool rows, cudaStrea
             if (e != cudaSuccess) return e;
         }
         kern<<<total, 32u * kWarps, smem, s>>>(P, kWarps, words);
+    } else if (P.jobs[0].L == 16) {
+        if (P.ea) k_sweep_bits3w<true><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
+        else k_sweep_bits3w<false><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
     } else if (P.ea) {
         k_sweep_bits3<true><<<total, 32u * kWarps, 0, s>>>(P, kWarps);
     } else {
@@ -481,12 +681,12 @@ static cudaError_t launch_bits_group(const SweepLaunch& P0, bool rows, cudaStrea
 }
 
 cudaError_t launch_sweep_bits(const SweepLaunch& P0, cudaStream_t s) {
-    if (P0.dim != 2) return launch_bits_group(P0, false, s);
-    // 2D: lattices whose words hold several rows (L <= 32) in their own launch
+    // 2D: lattices whose words hold several rows (L <= 32) in their own launch;
+    // 3D: L = 8 and L = 16 in launches of their own kernels
     SweepLaunch A = P0, B = P0;
     A.njobs = B.njobs = 0;
     for (int j = 0; j < P0.njobs; ++j) {
-        if (P0.jobs[j].L <= 32) A.jobs[A.njobs++] = P0.jobs[j];
+        if (P0.dim == 2 ? P0.jobs[j].L <= 32 : P0.jobs[j].L == 16) A.jobs[A.njobs++] = P0.jobs[j];
         else B.jobs[B.njobs++] = P0.jobs[j];
     }
     cudaError_t e = cudaSuccess;

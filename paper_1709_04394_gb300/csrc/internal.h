@@ -165,13 +165,16 @@ cudaError_t launch_halfsweep_global(const SweepJob& J, int dim, int colour, uint
 
 // Bit-sliced resident sweeps (bitsweep.cu): every copy converted to one bit
 // per spin on chip, same results as launch_sweep_resident. Supported lattices:
-// 2D ferromagnets with L in {16, 32, 64, 128, 256}, 3D lattices with L = 8 (all jobs of
-// a launch of one dimension and model; 2D lattices with L <= 32 and L >= 64 go
-// to separate launches). Uses its own block layout (P.cta_begin and P.total
-// are recomputed).
+// 2D ferromagnets with L in {16, 32, 64, 128, 256}, 3D lattices with L = 8 or 16 (all
+// jobs of a launch of one dimension and model; 2D lattices with L <= 32 and L >= 64,
+// and 3D lattices with L = 8 and L = 16, go to separate launches). Uses its own
+// block layout (P.cta_begin and P.total are recomputed).
 bool bits_supported(int dim, int L);
 cudaError_t launch_sweep_bits(const SweepLaunch& P, cudaStream_t s);
-cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t n_inst, cudaStream_t s);
+// +-J bonds of 3D lattices (L = 8 or 16) as the bit-sliced sweeps' bond words:
+// bits3_bond_words(L) words per instance.
+size_t bits3_bond_words(uint32_t L);
+cudaError_t launch_bits3_bonds(const uint8_t* jbits, uint32_t* jb3, uint32_t L, uint32_t n_inst, cudaStream_t s);
 
 // Multi-spin-coded sweeps (2D ferromagnet, L % 16 == 0): jobs with rpc = 32 G
 // replicas per CTA; G in 1..4 groups of 32.

@@ -1,5 +1,6 @@
 """GPU parity of the bit-sliced resident sweep kernel (one bit per spin on
-chip; 2D ferromagnets with L = 16, 32, 64, 128, 256 and 3D lattices with L = 8)
+chip; 2D ferromagnets with L = 16, 32, 64, 128, 256 and 3D lattices with L = 8
+and 16)
 against the CPU oracle, element by element: spins, per-sweep energies and
 magnetisations, annealing runs (multinomial and nearest-integer resampling,
 mixed lattice sizes in one step), parallel tempering; and the bit-sliced and
@@ -46,6 +47,10 @@ def _kernel_ran(ctx, fn):
     (3, 8, gbmc.GBMC_ISING_FM, 1, 19, 0.22, 5),      # 19 copies: the last warp partly empty
     (3, 8, gbmc.GBMC_EA_PMJ, 3, 7, 1.1, 6),
     (3, 8, gbmc.GBMC_EA_PMJ, 2, 5, 0.0, 2),
+    (3, 16, gbmc.GBMC_ISING_FM, 1, 5, 0.22, 4),      # one warp per copy, the last block partly empty
+    (3, 16, gbmc.GBMC_EA_PMJ, 2, 3, 1.1, 4),
+    (3, 16, gbmc.GBMC_EA_PMJ, 1, 2, 0.0, 2),
+    (3, 16, gbmc.GBMC_ISING_FM, 1, 2, 20.0, 3),
 ])
 def test_bits_sweeps_match_oracle(bits, dim, L, model, I, R, beta, n):
     seed = 1000 + 10 * L + dim
@@ -82,7 +87,9 @@ def test_bits_sweeps_match_oracle(bits, dim, L, model, I, R, beta, n):
                                              (2, 128, gbmc.GBMC_ISING_FM, 3, 101),
                                              (2, 256, gbmc.GBMC_ISING_FM, 1, 33),
                                              (3, 8, gbmc.GBMC_EA_PMJ, 5, 203),
-                                             (3, 8, gbmc.GBMC_ISING_FM, 1, 1001)])
+                                             (3, 8, gbmc.GBMC_ISING_FM, 1, 1001),
+                                             (3, 16, gbmc.GBMC_EA_PMJ, 3, 37),
+                                             (3, 16, gbmc.GBMC_ISING_FM, 1, 41)])
 def test_bits_equals_bytes_kernel(ctx, dim, L, model, I, R):
     out = []
     for kernel in (BITS, BYTES):
@@ -123,20 +130,43 @@ def test_bits_pa_mixed_lattices_match_oracle(bits):
         gbmc.lattice_free(l)
 
 
-def test_bits_pa_3d_ea_instances_match_oracle(bits):
-    I, R, S, theta, seed = 3, 333, 5, 2, 31
-    lat = gbmc.lattice_init(bits, 3, 8, model=gbmc.GBMC_EA_PMJ, n_instances=I, n_replicas=R, seed=seed,
+@pytest.mark.parametrize("L,I,R", [(8, 3, 333), (16, 2, 97)])
+def test_bits_pa_3d_ea_instances_match_oracle(bits, L, I, R):
+    S, theta, seed = 5, 2, 31
+    lat = gbmc.lattice_init(bits, 3, L, model=gbmc.GBMC_EA_PMJ, n_instances=I, n_replicas=R, seed=seed,
                             instance_base=10)
     betas = oracle.linear_betas(2.0, S)
     pa = gbmc.pa_create(bits, [lat], theta, S, schedule=gbmc.GBMC_SCHED_LIST, betas=betas)
     stats, n = gbmc.pa_run(bits, pa, capacity=S + 1)
     got = spins_out(bits, lat).reshape(I, R, -1)
     for i in range(I):
-        ref = oracle.pa_run(3, 8, seed, 10 + i, R, betas, theta, J=oracle.couplings(8, seed, 10 + i))
-        _compare_run(stats, ref, i, 512)
+        ref = oracle.pa_run(3, L, seed, 10 + i, R, betas, theta, J=oracle.couplings(L, seed, 10 + i))
+        _compare_run(stats, ref, i, L ** 3)
         np.testing.assert_array_equal(got[i], ref["spins"])
     gbmc.pa_free(pa)
     gbmc.lattice_free(lat)
+
+
+def test_bits_pa_3d_mixed_sizes_match_oracle(bits):
+    # one annealing step covers 3D +-J lattices with L = 6 (byte-plane kernel), L = 8
+    # and L = 16 (bit-sliced kernels, one launch each)
+    S, theta, seed = 3, 2, 17
+    spec = [(6, 150), (8, 211), (16, 45)]
+    lats = [gbmc.lattice_init(bits, 3, L, model=gbmc.GBMC_EA_PMJ, n_replicas=R, seed=seed, instance_base=3 * k)
+            for k, (L, R) in enumerate(spec)]
+    betas = oracle.linear_betas(1.5, S)
+    pa = gbmc.pa_create(bits, lats, theta, S, schedule=gbmc.GBMC_SCHED_LIST, betas=betas)
+    prof = _kernel_ran(bits, lambda: gbmc.pa_run(bits, pa, capacity=S + 1))
+    assert "sweep_bits" in prof and "sweep_resident" in prof
+    gbmc.pa_reset(bits, pa, True, 0)
+    stats, n = gbmc.pa_run(bits, pa, capacity=S + 1)
+    for k, (L, R) in enumerate(spec):
+        ref = oracle.pa_run(3, L, seed, 3 * k, R, betas, theta, J=oracle.couplings(L, seed, 3 * k))
+        _compare_run(stats, ref, k, L ** 3)
+        np.testing.assert_array_equal(spins_out(bits, lats[k]), ref["spins"])
+    gbmc.pa_free(pa)
+    for l in lats:
+        gbmc.lattice_free(l)
 
 
 @pytest.mark.parametrize("law", [gbmc.GBMC_RESAMPLE_NEAREST, gbmc.GBMC_RESAMPLE_POISSON])
@@ -158,11 +188,12 @@ def test_bits_pa_variable_population_matches_oracle(bits, law):
     gbmc.lattice_free(lat)
 
 
-def test_bits_parallel_tempering_matches_oracle(bits):
+@pytest.mark.parametrize("L,I,T", [(8, 3, 8), (16, 2, 6)])
+def test_bits_parallel_tempering_matches_oracle(bits, L, I, T):
     # every copy at its own temperature: per-copy thresholds in the bit-sliced kernel
-    I, T, theta, steps, seed = 3, 8, 3, 12, 41
+    theta, steps, seed = 3, 12, 41
     betas = np.linspace(0.2, 1.4, T)
-    lat = gbmc.lattice_init(bits, 3, 8, model=gbmc.GBMC_EA_PMJ, n_instances=I, n_replicas=T, seed=seed,
+    lat = gbmc.lattice_init(bits, 3, L, model=gbmc.GBMC_EA_PMJ, n_instances=I, n_replicas=T, seed=seed,
                             instance_base=2)
     pt = gbmc.pt_create(bits, lat, betas, theta)
     gbmc.pt_step(bits, pt, steps)
@@ -173,7 +204,7 @@ def test_bits_parallel_tempering_matches_oracle(bits):
     gbmc.pt_free(pt)
     got = spins_out(bits, lat).reshape(I, T, -1)
     for i in range(I):
-        s, r, a, e = oracle.pt_run(3, 8, seed, 2 + i, betas, theta, steps, J=oracle.couplings(8, seed, 2 + i))
+        s, r, a, e = oracle.pt_run(3, L, seed, 2 + i, betas, theta, steps, J=oracle.couplings(L, seed, 2 + i))
         np.testing.assert_array_equal(got[i], s)
         np.testing.assert_array_equal(rep.reshape(I, T)[i], r)
         np.testing.assert_array_equal(acc.reshape(I, T - 1)[i], a)

@@ -39,7 +39,7 @@ for kernel in (gbmc.GBMC_KERNEL_BYTES, gbmc.GBMC_KERNEL_BITS):
     for dim, L, model, I, R in [(2, 4, FM, 1, 3), (2, 6, FM, 2, 5), (2, 8, FM, 1, 7), (2, 16, FM, 2, 9),
                                 (2, 32, FM, 1, 3), (2, 64, FM, 1, 5),
                                 (2, 128, FM, 1, 3), (3, 4, FM, 1, 3), (3, 6, EA, 2, 3), (3, 8, EA, 3, 5),
-                                (3, 8, FM, 1, 21)]:
+                                (3, 8, FM, 1, 21), (3, 16, EA, 2, 3)]:
         lat = gbmc.lattice_init(ctx, dim, L, model=model, n_instances=I, n_replicas=R, seed=3, instance_base=1)
         n = 3
         Es = torch.zeros(n * I * R, dtype=torch.int32, device="cuda")
@@ -131,4 +131,4 @@ def test_checked_build_records_no_bounds_failure():
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    assert "checked ok 27" in r.stdout
+    assert "checked ok 29" in r.stdout
