@@ -194,6 +194,8 @@ WORKLOADS = {
     "ising2d-L4096-sw": dict(kind="sweeps", dim=2, L=4096, sweeps=100, beta=0.4406868, layout=0, sw=True),
     # 3D +-J spin glass L=8, 32 instances x 2 10^4 replicas, beta 0->3 in 201 temperatures, theta=10
     "pa-ea3d-L8": dict(kind="pa", lattices=[(3, 8, EA, 32, 20000)], S=200, theta=10, beta_f=3.0),
+    # the same spin glass at L=16 with the same number of sites: 32 instances x 2500 replicas
+    "pa-ea3d-L16": dict(kind="pa", lattices=[(3, 16, EA, 32, 2500)], S=200, theta=10, beta_f=3.0),
     # the default workload with nearest-integer resampling and a variable population:
     # R_0 = 10^5, capacity 1.05 10^5 (Sec. 5.4, Eq. (13) with R_{i-1})
     "pa-ising2d-L64-nearest": dict(kind="pa", lattices=[(2, 64, FM, 1, 105000)], S=100, theta=10, beta_f=1.0,
