@@ -40,9 +40,10 @@ ALG_INT_OPS_PER_SITE_UPDATE = 20.0
 # Multi-spin-coded sweeps: per replica update one LCG step (multiply, add) and
 # one threshold comparison, plus an 80-op Philox call per 4 sites x 32 replicas.
 ALG_INT_OPS_PER_MSC_UPDATE = 3.0 + 80.0 / 128.0
-# Swendsen-Wang: spins read for the bonds, read and written by the flip (1 + 2 B),
-# one 4-byte forest pointer written by the tile labelling and read by the flip
-SW_BYTES_PER_SITE = 11
+# Swendsen-Wang (2D, 32 x 32 scanline tiles): spins read for the bonds, read and
+# written by the flip (1 + 2 B), each site's 2-byte tile label written by the
+# labelling and read by the flip (the forest nodes of the tile roots not counted)
+SW_BYTES_PER_SITE = 7
 
 
 def recorded_traffic(kname, replicas):

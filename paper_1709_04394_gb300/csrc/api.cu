@@ -169,8 +169,9 @@ struct gbmc_lattice {
     int8_t* alt;       // second configuration buffer of the tiled large-lattice sweeps
     uint32_t* dcb_scratch;    // tile edges and progress counters of the resident double checkerboard
     size_t dcb_scratch_bytes;
-    uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags and union-find forest
+    uint8_t* sw_bonds; // Swendsen-Wang workspace: bond flags, union-find forest, 2D tile labels
     uint32_t* sw_parent;
+    uint16_t* sw_lab;
     uint32_t t;        // sweep counter
     gbmc_pa* run;      // annealing run using this lattice
 };
@@ -779,6 +780,7 @@ gbmc_status lattice_free(gbmc_lattice* l) {
     if (l->alt) cudaFree(l->alt);
     if (l->sw_bonds) cudaFree(l->sw_bonds);
     if (l->sw_parent) cudaFree(l->sw_parent);
+    if (l->sw_lab) cudaFree(l->sw_lab);
     delete l;
     return GBMC_OK;
 }
@@ -1081,8 +1083,10 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
         const bool tiled = sw_tiled((uint32_t)l->d.dim, (uint32_t)l->d.L);
         cudaError_t e = cudaMalloc(&l->sw_parent, 4 * l->N * l->ncopies);
         if (e == cudaSuccess && !tiled) e = cudaMalloc(&l->sw_bonds, l->N * l->ncopies);
+        if (e == cudaSuccess && tiled && l->d.dim == 2) e = cudaMalloc(&l->sw_lab, 2 * l->N * l->ncopies);
         if (e != cudaSuccess) {
             cudaFree(l->sw_parent);
+            cudaFree(l->sw_bonds);
             l->sw_bonds = nullptr;
             l->sw_parent = nullptr;
             return fail(GBMC_ERR_OOM, "cudaMalloc(Swendsen-Wang workspace): %s", cudaGetErrorString(e));
@@ -1093,6 +1097,7 @@ gbmc_status swendsen_wang(gbmc_ctx* ctx, gbmc_lattice* l, double beta, uint32_t 
     P.spins = l->cur;
     P.bonds = l->sw_bonds;
     P.parent = l->sw_parent;
+    P.lab = l->sw_lab;
     P.err = ctx->words + 1;
     P.seed = l->d.seed;
     // T_bond = ceil(p 2^32) - 1, p = 1 - exp(-2 beta): "r < p" as an integer comparison

@@ -202,6 +202,7 @@ struct SwLaunch {
     uint8_t* bonds;           // [copies][N] bit mu: forward bond along mu active
     uint32_t* parent;         // [copies][N] union-find forest
     int32_t* labels;          // [copies][N] cluster name (smallest site) of every site, or null
+    uint16_t* lab;            // [copies][N] 2D tiles: tile-local index of each site's tile root
     unsigned int* err;        // raised if a hook loop ran out of its cap
     uint64_t seed;
     uint64_t copy0;

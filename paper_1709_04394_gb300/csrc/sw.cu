@@ -17,8 +17,8 @@
 // Parent pointers only ever decrease, so every find walks a strictly
 // decreasing chain and ends; the hook loops are additionally capped (error flag).
 //
-// Tiled labelling (2D L % 32 == 0: 32 x 32 tiles; 3D L % 16 == 0: 16 x 8 x 8),
-// the tile decomposition of Sec. 3.3 with the consolidation done by atomics:
+// Tiled labelling of 3D lattices (L % 16 == 0: 16 x 8 x 8 tiles), the tile
+// decomposition of Sec. 3.3 with the consolidation done by atomics:
 //  k_sw_local      : one CTA per tile computes the tile's bond flags (the same
 //                    Philox words as k_sw_bonds), labels the tile's components
 //                    in shared memory with the same lock-free union-find, and
@@ -34,7 +34,26 @@
 // Each component again ends rooted at its smallest site (a hook always puts
 // the larger root under the smaller), so the labels and coins do not depend
 // on the order of the unions.
+//
+// 2D lattices with L % 32 == 0 take 32 x 32 tiles with a scanline labelling,
+// the tile labels kept apart from the global forest:
+//  k_sw_scan2    : one warp per tile, lane x = column x, the rows in order.
+//                  Row r's x bonds cut it into runs; a run's label is the
+//                  smallest of its start and of the labels its y bonds reach in
+//                  row r - 1, and a run that reaches two components above hooks
+//                  the larger label under the smaller in the tile's label
+//                  forest (shared memory). At the end every site's label is
+//                  resolved to its component's smallest site: lab[i] = that
+//                  site's tile-local index, and parent[g] = g for each such
+//                  tile root g, the only nodes of the global forest;
+//  k_sw_cross    : unites the tile roots of the two ends of each active
+//                  tile-crossing bond in the global forest;
+//  k_sw_flip_lab : one CTA per tile finds the global root of each tile root
+//                  whose component touches the tile border (the others are
+//                  roots of whole clusters) and draws each tile root's coin
+//                  once; every site takes its tile root's.
 #include "bits.cuh"
+#include "check.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -240,18 +259,6 @@ __global__ void __launch_bounds__(256) k_sw_local(const __grid_constant__ SwLaun
     *reinterpret_cast<uint4*>(P.parent + copy * P.N + i0) = make_uint4(g[0], g[1], g[2], g[3]);
 }
 
-// First site of the run holding site x (run-start mask R of the row; bit 0 is always set).
-__device__ __forceinline__ uint32_t sw_run_start(uint32_t R, uint32_t x) {
-    return 31u - __clz(R & (0xFFFFFFFFu >> (31u - x)));
-}
-
-// 2D tiles, the labelling by runs: as k_sw_local<2> (thread t: sites 4t .. 4t+3,
-// eight lanes per tile row), with the union-find over run starts only. A row's
-// run starts and y bonds become 32-bit masks; a y bond unites the runs holding
-// its two ends, and one union per pair of overlapping runs suffices (the bond
-// at x joins the same pair as the one at x - 1 unless a run starts at x in
-// either row); the root of each run is found once, at its start, and every site
-// takes its run's root.
 // Appends the items with has = true of the warp's lanes to the warp's queue q
 // (lane order), advancing n; all 32 lanes call it together.
 __device__ __forceinline__ void sw_warp_push(uint32_t* q, uint32_t& n, bool has, uint32_t item) {
@@ -260,74 +267,84 @@ __device__ __forceinline__ void sw_warp_push(uint32_t* q, uint32_t& n, bool has,
     n += __popc(b);
 }
 
-__global__ void __launch_bounds__(256) k_sw_local_runs(const __grid_constant__ SwLaunch P) {
-    __shared__ uint32_t lp[1024];
-    __shared__ uint16_t rt[1024];    // root of each run, at its start
-    __shared__ uint32_t rmask[32];   // run starts of each tile row
-    __shared__ uint32_t queue[8][128];  // per warp: unions (a | b << 16), then run starts
+// ---- 2D scanline tiles ----
+
+constexpr uint32_t kSwScanWarps = 4;  // tiles (warps) per block of k_sw_scan2
+
+// Global index of the 32 x 32 tile-local site k (k = 32 row + column) of the
+// tile holding site i.
+__device__ __forceinline__ uint32_t sw_tile_root(uint32_t k, uint32_t i, uint32_t L) {
+    const uint32_t y = i / L, x = i - y * L;
+    return ((y & ~31u) + (k >> 5)) * L + (x & ~31u) + (k & 31u);
+}
+
+__global__ void __launch_bounds__(32 * kSwScanWarps) k_sw_scan2(const __grid_constant__ SwLaunch P) {
+    __shared__ uint32_t eq[kSwScanWarps][1024];       // label forest of each warp's tile (local indices)
+    __shared__ uint16_t rowlab[kSwScanWarps][1024];   // each site's run label, resolved at the end
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const uint32_t L = P.L, ntx = L >> 5;
+    const uint32_t tile = blockIdx.x * kSwScanWarps + wib;
+    if (tile >= ntx * ntx) return;  // whole warp; no block barriers follow
     const uint64_t copy = P.copy0 + blockIdx.y;
     const int8_t* s = P.spins + copy * P.N;
     uint32_t inst, r;
     split_copy(copy, P.R, inst, r);
-    const uint32_t c3 = c3_word(kPurposeSwBond, 0u, P.inst_base + inst);
-    const uint32_t L = P.L, ntx = L / 32u;
-    const uint32_t bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
-    const uint32_t l0 = 4 * threadIdx.x, lx = l0 & 31u, ly = l0 >> 5, row = l0 - lx;
-    const uint32_t i0 = (by * 32u + ly) * L + bx * 32u + lx;
-    uint32_t flags[4];
-    sw_bond_flags_row<2>(P, s, i0, bx * 32u + lx, by * 32u + ly, 0u, r, c3, flags);
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t left = __shfl_up_sync(0xffffffffu, flags[3] & 1u, 1);  // bond into this thread's first site
-    uint32_t R = (lx == 0 || !left) ? 1u : 0u, Y = 0u;
+    const uint32_t bx = tile % ntx, by = tile / ntx, X = bx * 32u + lane;
+    uint32_t* f = eq[wib];
+    uint16_t* rl = rowlab[wib];
+    // bond words: the forward bonds b = 2 i + mu of sites i = 2 q, 2 q + 1 are
+    // the four words of Philox call q (t, replica and c3 hoisted)
+    const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst), (uint32_t)P.seed,
+                                      (uint32_t)(P.seed >> 32));
+    const long long Tb = P.T_bond;
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
+    int s_prev = 0;
+    uint32_t w1_prev = 0u, lab_prev = 0u;
+    for (uint32_t rr = 0; rr < 32u; ++rr) {
+        const uint32_t y = by * 32u + rr;
+        if ((rr & 1u) == 0u)  // lane l: the call of sites 2 (l & 15), +1 of row rr + l / 16
+            c = philox_q_wide(pf, ((y + (lane >> 4)) * L + bx * 32u + 2u * (lane & 15u)) >> 1);
+        const uint32_t src = ((rr & 1u) << 4) | (lane >> 1);
+        const uint32_t a0 = __shfl_sync(0xffffffffu, c.x, src), a1 = __shfl_sync(0xffffffffu, c.y, src);
+        const uint32_t a2 = __shfl_sync(0xffffffffu, c.z, src), a3 = __shfl_sync(0xffffffffu, c.w, src);
+        const uint32_t w0 = (lane & 1u) ? a2 : a0;  // bond along x: word (2 i) & 3
+        const uint32_t w1 = (lane & 1u) ? a3 : a1;  // bond along y: word (2 i + 1) & 3
+        const int sc = s[GBMC_IDX((uint64_t)y * L + X, P.N)];
+        const int sr = __shfl_down_sync(0xffffffffu, sc, 1);
+        // the bond from lane 31 leaves the tile (k_sw_cross); so does the one into row 0
+        const bool xb = lane < 31u && sc == sr && (long long)w0 <= Tb;
+        const bool yb = rr > 0u && sc == s_prev && (long long)w1_prev <= Tb;
+        const uint32_t R = ~(__ballot_sync(0xffffffffu, xb) << 1);  // run starts
+        const uint32_t own = rr * 32u + lane;
+        f[own] = own;
+        const uint32_t la = yb ? sw_find<false>(f, lab_prev) : 0u;  // the component above, if reached
+        // the run's label: segmented minimum over the run (lane x - d is in x's
+        // run when no run starts at x - d + 1 .. x), then read at the run's end
+        uint32_t v = yb ? la : own;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (k > 0) R |= (flags[k - 1] & 1u) ? 0u : 1u << k;
-        Y |= (flags[k] & 2u) ? 1u << k : 0u;
-    }
-    R <<= 4 * (lane & 7u);
-    Y <<= 4 * (lane & 7u);
-#pragma unroll
-    for (uint32_t o = 1; o < 8u; o <<= 1) {
-        R |= __shfl_xor_sync(0xffffffffu, R, o);
-        Y |= __shfl_xor_sync(0xffffffffu, Y, o);
-    }
-    if ((lane & 7u) == 0) rmask[ly] = R;
-#pragma unroll
-    for (uint32_t k = 0; k < 4; ++k)
-        if ((R >> (lx + k)) & 1u) lp[l0 + k] = l0 + k;  // run starts are their own parents
-    __syncthreads();
-    // the warp's unions, then its run starts, go through a queue so that every
-    // lane works on one at a time (instead of each lane on its own few sites)
-    uint32_t* q = queue[threadIdx.x >> 5];
-    uint32_t n = 0;
-    {
-        const uint32_t Rn = ly < 31u ? rmask[ly + 1] : 0u;
-        const uint32_t U = ly < 31u ? Y & ~((Y << 1) & ~R & ~Rn) : 0u;
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t x = lx + k;
-            const bool has = (U >> x) & 1u;
-            sw_warp_push(q, n, has,
-                         has ? (row + sw_run_start(R, x)) | ((row + 32u + sw_run_start(Rn, x)) << 16) : 0u);
+        for (uint32_t d = 1; d < 32u; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d && ((R >> (lane - d + 1u)) & ((1u << d) - 1u)) == 0u) v = t < v ? t : v;
         }
+        const uint32_t nxt = R & ~((2u << lane) - 1u);  // run starts right of this lane
+        const uint32_t m = __shfl_sync(0xffffffffu, v, nxt ? (uint32_t)__ffs(nxt) - 2u : 31u);
+        if (yb && la != m) sw_unite<false>(f, la, m, P.err);  // a second component above joins the run
+        rl[own] = (uint16_t)m;
+        lab_prev = m;
+        s_prev = sc;
+        w1_prev = w1;
+        __syncwarp();
     }
-    __syncwarp();
-    for (uint32_t i = lane; i < n; i += 32u) sw_unite<false>(lp, q[i] & 0xFFFFu, q[i] >> 16, P.err);
-    __syncthreads();
-    n = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < 4; ++k) sw_warp_push(q, n, (R >> (lx + k)) & 1u, l0 + k);
-    __syncwarp();
-    for (uint32_t i = lane; i < n; i += 32u) rt[q[i]] = (uint16_t)sw_find<false>(lp, q[i]);
-    __syncthreads();
-    uint32_t g[4];
-#pragma unroll
-    for (uint32_t k = 0; k < 4; ++k) {
-        const uint32_t root = rt[row + sw_run_start(R, lx + k)];
-        g[k] = (by * 32u + (root >> 5)) * L + bx * 32u + (root & 31u);
+    // every site's label resolved to its component's smallest site: lab = its
+    // tile-local index; each tile root a node of the global forest
+    uint32_t* par = P.parent + copy * P.N;
+    uint16_t* lab = P.lab + copy * P.N;
+    for (uint32_t rr = 0; rr < 32u; ++rr) {
+        const uint32_t own = rr * 32u + lane, i = (by * 32u + rr) * L + X;
+        const uint32_t root = sw_find<false>(f, rl[own]);
+        lab[GBMC_IDX(i, P.N)] = (uint16_t)root;
+        if (root == own) par[GBMC_IDX(i, P.N)] = i;
     }
-    // i0 % 4 == 0, N % 4 == 0 and the forest is a cudaMalloc block: 16-byte aligned
-    *reinterpret_cast<uint4*>(P.parent + copy * P.N + i0) = make_uint4(g[0], g[1], g[2], g[3]);
 }
 
 // The bonds that leave their tile: e < N / tx are the sites with x % tx == tx - 1
@@ -364,8 +381,13 @@ __global__ void __launch_bounds__(256) k_sw_cross(const __grid_constant__ SwLaun
     const int8_t* s = P.spins + copy * P.N;
     uint32_t inst, r;
     split_copy(copy, P.R, inst, r);
-    if (sw_bond_active(P, s, i, j, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst)))
-        sw_unite<true>(P.parent + copy * P.N, i, j, P.err);
+    if (!sw_bond_active(P, s, i, j, mu, r, c3_word(kPurposeSwBond, 0u, P.inst_base + inst))) return;
+    if (P.lab) {  // 2D scanline tiles: the ends' tile roots
+        const uint16_t* lab = P.lab + copy * P.N;
+        i = sw_tile_root(lab[i], i, L);
+        j = sw_tile_root(lab[j], j, L);
+    }
+    sw_unite<true>(P.parent + copy * P.N, i, j, P.err);
 }
 
 __global__ void __launch_bounds__(256) k_sw_union(const __grid_constant__ SwLaunch P) {
@@ -483,6 +505,64 @@ __global__ void __launch_bounds__(256) k_sw_flip_tiled(const __grid_constant__ S
     }
 }
 
+__global__ void __launch_bounds__(256) k_sw_flip_lab(const __grid_constant__ SwLaunch P) {
+    __shared__ uint32_t troot[1024];     // global root of each tile root (by local index)
+    __shared__ uint8_t tcoin[1024];      // its coin (1: the cluster flips)
+    __shared__ uint32_t tqueue[8][128];  // per warp: its tile roots (local indices)
+    __shared__ uint32_t tedge[32];       // the tile roots whose component touches the tile border
+    const uint64_t copy = P.copy0 + blockIdx.y;
+    uint32_t inst, r;
+    split_copy(copy, P.R, inst, r);
+    const uint32_t L = P.L, ntx = L >> 5;
+    const uint32_t bx = blockIdx.x % ntx, by = blockIdx.x / ntx;
+    const uint32_t l0 = 4 * threadIdx.x, lx = l0 & 31u, ly = l0 >> 5;
+    const uint32_t i0 = (by * 32u + ly) * L + bx * 32u + lx;
+    // i0 % 4 == 0 and the label buffer is a cudaMalloc block: 8-byte aligned
+    const uint2 lv = *reinterpret_cast<const uint2*>(P.lab + copy * P.N + GBMC_IDX(i0, P.N));
+    // i0 % 4 == 0 and the spin buffer is 16-byte aligned: one word per thread, loaded early
+    uint32_t* sw = reinterpret_cast<uint32_t*>(P.spins + copy * P.N + i0);
+    uint32_t w = *sw;
+    const uint32_t k[4] = {lv.x & 0xFFFFu, lv.x >> 16, lv.y & 0xFFFFu, lv.y >> 16};
+    // the tile roots whose component has a site on the tile border: only
+    // they can have been united with other tiles' components
+    if (threadIdx.x < 32u) tedge[threadIdx.x] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j)
+        if (ly == 0u || ly == 31u || lx + j == 0u || lx + j == 31u) atomicOr(&tedge[k[j] >> 5], 1u << (k[j] & 31u));
+    __syncthreads();
+    // the tile roots: their global root and coin, through a per-warp queue so
+    // that every lane works on one at a time
+    const PhiloxFixed pf = philox_fix(P.t, r, c3_word(kPurposeSwFlip, 0u, P.inst_base + inst), (uint32_t)P.seed,
+                                      (uint32_t)(P.seed >> 32));
+    uint32_t* par = P.parent + copy * P.N;
+    uint32_t* q = tqueue[threadIdx.x >> 5];
+    uint32_t n = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) sw_warp_push(q, n, k[j] == l0 + j, l0 + j);
+    __syncwarp();
+    for (uint32_t a = threadIdx.x & 31u; a < n; a += 32u) {
+        const uint32_t l = q[a];
+        const uint32_t g = (by * 32u + (l >> 5)) * L + bx * 32u + (l & 31u);
+        // a component away from the tile border is a whole cluster, rooted at g
+        const uint32_t root = ((tedge[l >> 5] >> (l & 31u)) & 1u) ? sw_find<true>(par, g) : g;
+        troot[l] = root;
+        tcoin[l] = (uint8_t)sw_coin(pf, root);
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < 4; ++j) {
+        if (!tcoin[GBMC_IDX(k[j], 1024u)]) continue;
+        const uint32_t b = (uint32_t)(uint8_t)(-(int8_t)(w >> (8 * j)));
+        w = (w & ~(0xFFu << (8 * j))) | (b << (8 * j));
+    }
+    *sw = w;
+    if (P.labels) {
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) P.labels[copy * P.N + i0 + j] = (int32_t)troot[GBMC_IDX(k[j], 1024u)];
+    }
+}
+
 cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s) {
     if (P0.N % 4 != 0) return cudaErrorInvalidValue;
     for (uint64_t c0 = 0; c0 < copies; c0 += 65535) {
@@ -492,9 +572,23 @@ cudaError_t launch_sw_update(const SwLaunch& P0, uint64_t copies, cudaStream_t s
         const uint32_t quads = P.N / 4;
         const bool tiled = sw_tiled(P.dim, P.L);
         cudaError_t e;
+        if (tiled && P.dim == 2) {
+            if (!P.lab) return cudaErrorInvalidValue;
+            const uint32_t tiles = P.N / 1024;
+            k_sw_scan2<<<dim3((tiles + kSwScanWarps - 1) / kSwScanWarps, nc), 32 * kSwScanWarps, 0, s>>>(P);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_sw_cross<<<dim3((sw_cross_count(P.N, P.dim) + 255) / 256, nc), 256, 0, s>>>(P);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_sw_flip_lab<<<dim3(tiles, nc), 256, 0, s>>>(P);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            continue;
+        }
+        P.lab = nullptr;
         if (tiled) {
-            if (P.dim == 2) k_sw_local_runs<<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
-            else k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
+            k_sw_local<3><<<dim3(P.N / 1024, nc), 256, 0, s>>>(P);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             k_sw_cross<<<dim3((sw_cross_count(P.N, P.dim) + 255) / 256, nc), 256, 0, s>>>(P);

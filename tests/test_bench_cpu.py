@@ -61,7 +61,7 @@ def test_roofline_attribution_helpers():
     # PA: a copy read and written once per theta sweeps, plus E, M and its parent
     b = bench.alg_bytes_per_update(W["pa-ising2d-L64"], "sweep_bits")
     assert abs(b - (2 * 4096 + 12) / (4096 * 10)) < 1e-12
-    assert bench.alg_bytes_per_update(W["ising2d-L4096-sw"], "swendsen_wang") == 11.0
+    assert bench.alg_bytes_per_update(W["ising2d-L4096-sw"], "swendsen_wang") == 7.0
     # double checkerboard, 64 x 64 tiles, k = 10: the bit-sliced tile reads a
     # one-site halo, the byte-plane window an 8-site one
     assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb_bits") - (2 + 4 / 64) / 10) < 1e-12
