@@ -405,6 +405,7 @@ def run_e2e(gbmc, ctx, w, lats, pa, pts, dist, ws, steps, seed0, local):
     sampler.start()
     time.sleep(0.5)  # nvidia-smi up and sampling before the timer starts
     t0 = time.perf_counter()
+    marks = [t0]
     for k in range(n_e2e):
         for l, hin in zip(lats, hosts_in):
             gbmc.lattice_copy_in(ctx, l, hin)
@@ -428,10 +429,12 @@ def run_e2e(gbmc, ctx, w, lats, pa, pts, dist, ws, steps, seed0, local):
             d2h_stats = 0
         for l, hout in zip(lats, hosts_out):
             gbmc.lattice_copy_out(ctx, l, hout)
-    t_e2e = time.perf_counter() - t0
+        marks.append(time.perf_counter())
+    t_e2e = marks[-1] - t0
     clocks = sampler.stop()
     t_e2e = max_over_ranks(dist, ws, t_e2e, device="cuda")
-    return dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e, clocks=clocks)
+    return dict(seconds_per_step=t_e2e / n_e2e, h2d=h2d, d2h=d2h + d2h_stats, steps=n_e2e, clocks=clocks,
+                step_seconds=[b - a for a, b in zip(marks, marks[1:])])
 
 
 # MLP proposals are kept when their realised overlap lies in [0.80, 0.90], a band
@@ -735,7 +738,7 @@ def main():
     e = res["e2e"]
     line["e2e"] = {"value": ws * upd_step / (e["seconds_per_step"] * 1e9), "unit": "spin-flips/ns",
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"], "steps": e["steps"],
-                   "clocks": e["clocks"]}
+                   "step_ms": [round(1e3 * t, 2) for t in e["step_seconds"]], "clocks": e["clocks"]}
     if not args.no_secondary and args.workload == "pa-ising2d-L64" and not args.graph:
         line["secondary"] = secondary
         if ws == 1:
