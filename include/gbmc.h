@@ -282,8 +282,9 @@ gbmc_status metropolis_sweeps_msc(gbmc_ctx *ctx, gbmc_lattice *lat, double beta,
  * E_series_dev / M_series_dev: NULL or device int32 [n_updates][n_copies] (E
  * and M after each update); labels_dev: NULL or device int32 [n_copies][N],
  * the cluster name of every site in the last update. A lazily allocated
- * workspace of 4 bytes per site and copy (5 unless 2D L % 32 == 0 or 3D
- * L % 16 == 0) stays with the lattice. Requirements
+ * workspace stays with the lattice: 6 bytes per site and copy for 2D
+ * L % 32 == 0 (the union-find forest and the 32 x 32 tiles' labels), 4 for 3D
+ * L % 16 == 0, 5 otherwise. Requirements
  * (else GBMC_ERR_ARG): ferromagnet (dim 2 or 3), int8 layout. */
 gbmc_status swendsen_wang(gbmc_ctx *ctx, gbmc_lattice *lat, double beta, uint32_t n_updates,
                           int32_t *E_series_dev, int32_t *M_series_dev, int32_t *labels_dev);
