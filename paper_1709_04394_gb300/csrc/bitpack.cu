@@ -212,6 +212,25 @@ __global__ void __launch_bounds__(kBpStripThreads, 1) k_bp_strips(const __grid_c
     // only these warps wait for the neighbours, on named barrier 1; the other
     // warps go straight to the interior rows.
     const uint32_t nb = 2 * Wr, total = rs * Wr;
+    // this thread's interior words k = k0, k0 + B, ... (fixed for the whole
+    // launch: rows and columns worked out once), two updated at a time below
+    constexpr uint32_t kMaxOwn = 4;
+    uint32_t own_lr[kMaxOwn], own_w[kMaxOwn], n_own = 0;
+    bool listed = true;
+    for (uint32_t k = tid + (tid < nb ? B : 0u); k < total; k += B) {  // k >= nb: B >= nb by the launch shape
+        if (n_own == kMaxOwn) {
+            listed = false;  // more than kMaxOwn words per thread: the generic walk
+            break;
+        }
+        const uint32_t kk = k - nb, lr = 2 + kk / Wr;
+#pragma unroll
+        for (uint32_t i = 0; i < kMaxOwn; ++i)
+            if (i == n_own) {
+                own_lr[i] = lr;
+                own_w[i] = kk - (lr - 2) * Wr;
+            }
+        ++n_own;
+    }
     for (uint32_t h = 0; h < S.n_half; ++h) {
         const uint32_t c = h & 1u;
         uint32_t* own = sm + c * ps;
@@ -245,9 +264,41 @@ __global__ void __launch_bounds__(kBpStripThreads, 1) k_bp_strips(const __grid_c
                 atomicExch(S.progress + blockIdx.x, h + 1u);
             }
         }
-        for (uint32_t k = tid + (tid < nb ? B : 0u); k < total; k += B) {  // k >= nb: B >= nb by the launch shape
-            const uint32_t kk = k - nb, lr = 2 + kk / Wr;
-            update(lr, kk - (lr - 2) * Wr);
+        if (listed) {
+            // two words at a time: both loaded and updated before either is
+            // stored (they read only the other plane)
+            auto gather = [&](uint32_t lr, uint32_t w, uint32_t& up, uint32_t& dn, uint32_t& same, uint32_t& side,
+                              uint32_t& q) {
+                const uint32_t y = y0 + lr - 1, o = (y + c) & 1u;
+                const uint32_t* orow = oth + lr * Wr;
+                same = orow[w];
+                side = o ? __funnelshift_r(same, orow[w + 1 == Wr ? 0 : w + 1], 1)   // bits j+1
+                         : __funnelshift_l(orow[w == 0 ? Wr - 1 : w - 1], same, 1);  // bits j-1
+                up = oth[(lr - 1) * Wr + w];
+                dn = oth[(lr + 1) * Wr + w];
+                q = y * (L >> 3) + 8 * w;
+            };
+#pragma unroll
+            for (uint32_t i = 0; i < kMaxOwn; i += 2) {
+                if (i + 1 < n_own) {
+                    uint32_t ua, da, sa, xa, qa, ub, db, sb, xb, qb;
+                    gather(own_lr[i], own_w[i], ua, da, sa, xa, qa);
+                    gather(own_lr[i + 1], own_w[i + 1], ub, db, sb, xb, qb);
+                    uint32_t* pa = own + own_lr[i] * Wr + own_w[i];
+                    uint32_t* pb = own + own_lr[i + 1] * Wr + own_w[i + 1];
+                    const uint32_t na = bp_word_update(*pa, ua, da, sa, xa, pf, qa, S.T4, S.T8);
+                    const uint32_t nbw = bp_word_update(*pb, ub, db, sb, xb, pf, qb, S.T4, S.T8);
+                    *pa = na;
+                    *pb = nbw;
+                } else if (i < n_own) {
+                    update(own_lr[i], own_w[i]);
+                }
+            }
+        } else {
+            for (uint32_t k = tid + (tid < nb ? B : 0u); k < total; k += B) {
+                const uint32_t kk = k - nb, lr = 2 + kk / Wr;
+                update(lr, kk - (lr - 2) * Wr);
+            }
         }
         __syncthreads();
         if (!s_ok) return;
