@@ -760,8 +760,8 @@ def main():
 
 
 # Secondary records of the default run: the other configurations of the path
-# (single L = 4096 lattice, int8 and bit-packed; 3D +-J and mixed-size
-# annealing) and of its variants (multi-spin coding, nearest-integer
+# (single L = 4096 lattice, int8 and bit-packed; 3D +-J (L = 8 and 16) and
+# mixed-size annealing) and of its variants (multi-spin coding, nearest-integer
 # resampling, parallel tempering, double checkerboard, Swendsen-Wang), with
 # (timed steps, warm-up steps) each, so that the whole default run stays within
 # a few minutes.
@@ -769,6 +769,7 @@ SECONDARY = {
     "ising2d-L4096": (10, 3),
     "ising2d-L4096-bitpack": (10, 3),
     "pa-ea3d-L8": (3, 3),
+    "pa-ea3d-L16": (3, 3),
     "pa-mixed-2d": (3, 3),
     "pa-ising2d-L64-msc": (3, 3),
     "pa-ising2d-L64-nearest": (3, 3),
