@@ -69,3 +69,29 @@ def test_roofline_attribution_helpers():
                (2 / 1000 + 0.75 / 640)) < 1e-12
     assert abs(bench.alg_bytes_per_update(W["ising2d-L4096-dcb"], "sweep_dcb") - (80 ** 2 + 64 ** 2) / 64 ** 2 / 10) \
         < 1e-12
+
+
+def test_gpu_record_line_from_a_run_result():
+    # the JSON line of a GPU workload from a (synthetic) run result: contract keys,
+    # value = site updates / time, and the roofline of the dominant kernel
+    sys.path.insert(0, ROOT)
+    import bench
+
+    w = dict(bench.WORKLOADS["ising2d-L4096-dcb"])
+    upd = 4096 ** 2 * 1000
+    res = dict(ms=12.0 * 2, steps=2, warmup=3, upd_all=2.0 * upd, upd_local=2.0 * upd, upd_prof=2.0 * upd,
+               ms_profiled=24.5, prof={"sweep_dcb_bits": (400, 24.0)}, launches=400,
+               clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, sm_count=152)
+    line = bench.gpu_record(w, "ising2d-L4096-dcb", res, 1)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks"):
+        assert k in line, k
+    assert abs(line["value"] - upd / (12.0 * 1e6)) < 1e-9 and line["ms_per_step"] == 12.0
+    roof = line["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in roof, k
+    assert roof["kernel"] == "sweep_dcb_bits" and roof["bound"] == "alu"
+    # 20 algorithmic integer ops per update over the kernel's own 24 ms
+    assert abs(roof["achieved"] - 20.0 * 2 * upd / 24e-3 / 1e9) < 1e-6
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
+    assert line["config"]["workload"] == "ising2d-L4096-dcb" and line["gpu_launches"] == 400
