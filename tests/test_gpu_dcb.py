@@ -244,3 +244,26 @@ def test_dcb_resident_neighbour_wait_runs_out_and_is_reported(ctx):
         oracle.dcb_sweeps(L, tile, s, 0.44, 12, 0, r, 0, 2, 2)
         np.testing.assert_array_equal(got[r], s)
     gbmc.lattice_free(lat)
+
+
+def test_dcb_resident_falls_back_when_tiles_do_not_fit(ctx):
+    """L = 8192 with 64 x 64 tiles has 8192 tile pairs, more than the device
+    holds at once: k = 2 (a resident launch under AUTO) takes the per-round
+    launches instead, with the spins of the byte-plane tiles."""
+    L, tile, k, rounds = 8192, 64, 2, 1
+    out = []
+    for kernel in (AUTO, BYTES):
+        gbmc.gbmc_set_sweep_kernel(ctx, kernel)
+        try:
+            lat = gbmc.lattice_init(ctx, 2, L, seed=23)
+            gbmc.gbmc_profile(ctx, True)
+            gbmc.metropolis_sweeps_dcb(ctx, lat, BETA_C, rounds, k, tile)
+            prof = gbmc.gbmc_profile_read(ctx)
+            gbmc.gbmc_profile(ctx, False)
+        finally:
+            gbmc.gbmc_set_sweep_kernel(ctx, AUTO)
+        if kernel == AUTO:
+            assert prof["sweep_dcb_bits"][0] == 2 * rounds and "sweep_dcb_resident" not in prof
+        out.append(spins_out(ctx, lat))
+        gbmc.lattice_free(lat)
+    np.testing.assert_array_equal(out[0], out[1])
